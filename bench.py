@@ -1,0 +1,332 @@
+"""Benchmark: batched Smith-Waterman/Gotoh alignment on GB300.
+
+One step = one pass of the whole hot path (forward DP, end-cell selection,
+reverse DP, output) over the 100,000-pair DNA workload (query 100-300,
+reference 200-1024, 30% planted; +3/-3, gap_open -6, gap_extend -1) with the
+inputs resident in device memory.  The metric is GCUPS: forward cells
+(sum of n*m) per second, whole job.  The same line reports the plain
+one-block-per-pair launch on the same GPU, the end-to-end rate through the
+host-buffer C-ABI call, the integer-pipe roofline of the batched kernel, and
+the CPU oracle timed on this host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the full workload on its own GPU
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "bit-exact GCUPS on 1 GB300, batched vs plain, % int-pipe roofline; serve p99 ms"
+CONFIG = 1
+OPS_PER_CELL = 6
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=CONFIG)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0 = auto)")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(batch, n_pairs: int, threads: int) -> dict:
+    import oracle
+    oracle.build()
+    sub = batch.subset(np.arange(n_pairs))
+    t0 = time.perf_counter()
+    oracle.align_workload(sub, threads=threads)
+    dt = time.perf_counter() - t0
+    cells = sub.cells
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "sample": f"first {n_pairs} pairs of {batch.name} ({cells / 1e9:.3f} G forward cells), "
+                      f"{dt:.2f} s on {threads} host threads",
+            "seconds": dt}
+
+
+def auto_cpu_pairs(batch, threads: int, target_s: float = 12.0) -> int:
+    """Pairs of the workload the oracle aligns in about target_s seconds here."""
+    probe = min(2000, batch.n_pairs)
+    r = oracle_rate(batch, probe, threads)
+    per_pair = r["seconds"] / probe
+    return int(max(probe, min(batch.n_pairs, target_s / per_pair)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# -------------------------------------------------------------- reference arm
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    batch = wl.gen_config(args.config)
+    threads = cpu_cores()
+    n = args.cpu_pairs or max(500, auto_cpu_pairs(batch, threads, target_s=6.0) // 2)
+    for _ in range(args.warmup):
+        oracle_rate(batch, min(n, 500), threads)
+    vals, secs, cells = [], 0.0, 0
+    for _ in range(args.steps):
+        r = oracle_rate(batch, n, threads)
+        vals.append(r["value"])
+        secs += r["seconds"]
+        cells += batch.subset(np.arange(n)).cells
+    value = cells / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": batch.name, "pairs_per_step": n, "threads": threads},
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                             "sample": f"first {n} pairs of {batch.name} per step"},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- our arm
+
+def reverse_cells(res: np.ndarray) -> int:
+    """Cells the reverse pass needs: rows 0..qend by columns rend..rstart."""
+    ok = res[:, 0] > 0
+    q = res[ok, 1].astype(np.int64) + 1
+    c = (res[ok, 2] - res[ok, 4]).astype(np.int64) + 1
+    return int(np.sum(q * c))
+
+
+def time_plan(swgb, torch, plan, q, r, out, stream, steps, warmup, flush):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for _ in range(warmup):
+        flush.add_(1)
+        swgb.sw_plan_execute(plan, q, r, out, stream)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1)  # larger than L2: every step starts with a cold L2
+            ev[k][0].record(stream)
+            swgb.sw_plan_execute(plan, q, r, out, stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in ev]
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2208_12350_gb300 as swgb
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    swgb.load()
+    batch = wl.gen_config(args.config)
+    cells = batch.cells
+    ctx = swgb.sw_ctx_create(local)
+    sms = swgb.sw_ctx_sm_count(ctx)
+    stream = torch.cuda.Stream(device=dev)
+    q = torch.from_numpy(batch.q_seqs).to(dev)
+    r = torch.from_numpy(batch.r_seqs).to(dev)
+    out = torch.zeros((5, batch.n_pairs), dtype=torch.int32, device=dev)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                               batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
+                               swgb.SW_PLAN_GRAPH)
+    info = swgb.sw_plan_info(plan)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    times = time_plan(swgb, torch, plan, q, r, out, stream, args.steps, args.warmup, flush)
+    barrier()
+    clk = clocks.stop()
+    t_total = sum(times)
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    res = out.T.contiguous().cpu().numpy()
+    rcells = reverse_cells(res)
+    value = cells * args.steps * world / t_total / 1e9
+    per_launch = t_total / args.steps
+
+    # --- integer roofline of the batched kernel (events timed live above)
+    ops = OPS_PER_CELL * (cells + rcells)
+    achieved = ops / per_launch / 1e12
+    mb_rate, _ = swgb.sw_microbench_int("viaddmax_s32", local, 2048)
+    peak_measured = mb_rate / 1e12
+    sm_mhz = clk.get("sm_mhz")
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
+            "frac": achieved / peak_measured if peak_measured else None, "traffic": None,
+            "peak_kind": "measured __viaddmax_s32 issue rate, whole device, this run",
+            "ops_per_cell": OPS_PER_CELL, "cells_forward": cells, "cells_reverse": rcells}
+
+    # --- plain one-block-per-pair comparator
+    plain = None
+    if not args.no_plain:
+        pplan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                                    batch.gap_open, batch.gap_extend, swgb.SW_MODE_PLAIN, 0)
+        out2 = torch.zeros_like(out)
+        pt = time_plan(swgb, torch, pplan, q, r, out2, stream, max(3, args.steps // 2), 1, flush)
+        same = bool(torch.equal(out, out2))
+        swgb.sw_plan_destroy(pplan)
+        pv = cells * len(pt) / sum(pt) / 1e9
+        plain = {"value": pv, "unit": "GCUPS", "ms_per_step": sum(pt) / len(pt) * 1e3,
+                 "steps": len(pt), "identical_outputs": same}
+
+    # --- end to end through the host-buffer C-ABI call
+    qh = torch.from_numpy(batch.q_seqs).pin_memory()
+    rh = torch.from_numpy(batch.r_seqs).pin_memory()
+    oh = torch.zeros((5, batch.n_pairs), dtype=torch.int32).pin_memory()
+    eplan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                                batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
+                                swgb.SW_PLAN_GRAPH)
+    for _ in range(args.warmup):
+        swgb.sw_plan_execute_host(eplan, qh, rh, oh, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        swgb.sw_plan_execute_host(eplan, qh, rh, oh, stream)
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    e2e_same = bool(np.array_equal(oh.numpy().T, res))
+    swgb.sw_plan_destroy(eplan)
+    e2e = {"value": cells * args.steps * world / e2e_t / 1e9, "unit": "GCUPS",
+           "h2d_bytes_per_step": int(batch.q_seqs.nbytes + batch.r_seqs.nbytes),
+           "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same}
+
+    swgb.sw_plan_destroy(plan)
+    swgb.sw_ctx_destroy(ctx)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = cpu_cores()
+        n = args.cpu_pairs or auto_cpu_pairs(batch, threads)
+        cpu = oracle_rate(batch, n, threads)
+        cpu.pop("seconds")
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_launch * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": batch.name, "pairs": batch.n_pairs,
+                           "forward_cells": cells, "mode": "batched persistent + CUDA graph",
+                           "l2": "flushed between steps (512 MB write)", "sms": sms,
+                           "group_tasks": info["group_tasks"]},
+                "plain": plain,
+                "batched_over_plain": (value / world) / plain["value"] if plain else None,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": info["launches"] * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

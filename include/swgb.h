@@ -1,0 +1,205 @@
+/*
+ * swgb: batched Smith-Waterman local alignment with affine (Gotoh) gaps on
+ * NVIDIA GB300 (sm_103a).
+ *
+ * For every (query, reference) pair of a batch the library computes the best
+ * local alignment score, its end coordinates (forward pass) and its start
+ * coordinates (reverse pass), as ADEPT does with its forward and reverse
+ * kernels (paper Section II-B, Fig. 2; Section III-B).
+ *
+ * Scoring.  Query a_1..a_n indexes matrix rows, reference b_1..b_m columns.
+ *   E[i][j] = max(H[i][j-1] + gap_open, E[i][j-1] + gap_extend)
+ *   F[i][j] = max(H[i-1][j] + gap_open, F[i-1][j] + gap_extend)
+ *   H[i][j] = max(0, H[i-1][j-1] + s(a_i, b_j), E[i][j], F[i][j])
+ * with H = 0 and E = F = -infinity on the boundary (Section II-B.1; the
+ * affine E update of Fig. 8).  A gap of length k costs
+ * gap_open + (k-1) * gap_extend; both are given as signed values <= 0 and
+ * must satisfy gap_open <= gap_extend <= 0.
+ *
+ * Outputs, one int32 each per pair, 0-based inclusive residue indices:
+ *   score   S = max H
+ *   qend, rend     among cells with H = S: smallest rend, then smallest qend
+ *   qstart, rstart among score-S alignments ending at (qend, rend): largest
+ *                  rstart, then largest qstart (the reverse pass over the
+ *                  reversed prefixes, with the same end rule)
+ *   S = 0 (also n = 0 or m = 0): score 0 and all four coordinates -1.
+ * The computation is exact integer arithmetic; results are bit-identical to
+ * the definition above.
+ *
+ * Memory.  Sequences are packed residue codes (uint8, each < alphabet_size)
+ * concatenated in CSR form: pair p's query is q_seqs[q_offsets[p] ..
+ * q_offsets[p+1]) and likewise for the reference.  Unless a function says
+ * otherwise, sequence and output pointers are DEVICE pointers owned by the
+ * caller; offsets and the scoring matrix are HOST pointers.  The library
+ * owns only the context's and plans' device workspaces.
+ *
+ * Limits.  Each sequence at most SW_MAX_LEN residues; alphabet_size in
+ * [1, SW_MAX_ALPHABET]; |gap_open|, |gap_extend| <= SW_MAX_GAP.
+ *
+ * Errors.  Every entry point returns an sw_status.  Argument errors are
+ * detected on the host before anything is enqueued; CUDA failures map to
+ * SW_ECUDA.  sw_last_error() returns a message for the calling thread's most
+ * recent failure.  No exception crosses this interface.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ * default stream.  Work is enqueued asynchronously unless stated otherwise.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SW_MAX_LEN 65535
+#define SW_MAX_ALPHABET 32
+#define SW_MAX_GAP 1000000
+
+typedef enum {
+    SW_OK = 0,
+    SW_EINVAL = -1,   /* bad argument (null pointer, sign, alphabet size) */
+    SW_ERANGE = -2,   /* a length, residue or score outside the limits    */
+    SW_ENOMEM = -3,   /* device or host allocation failed                 */
+    SW_ECUDA = -4,    /* a CUDA runtime call failed                       */
+    SW_ETIMEOUT = -5, /* a bounded wait ran out                           */
+    SW_EBUDGET = -6   /* a request exceeds the serving memory budget      */
+} sw_status;
+
+typedef enum {
+    SW_MODE_AUTO = 0,    /* = SW_MODE_BATCHED                               */
+    SW_MODE_PLAIN = 1,   /* one thread block per pair, one launch           */
+    SW_MODE_BATCHED = 2  /* persistent length-bucketed kernel (+ plain for  */
+                         /* pairs beyond its score bound)                   */
+} sw_mode;
+
+/* Plan flags. */
+#define SW_PLAN_GRAPH 1u /* capture the launch sequence in a CUDA graph and */
+                         /* replay it while pointers and stream repeat       */
+
+typedef struct sw_ctx sw_ctx;
+typedef struct sw_plan sw_plan;
+
+/* Message for the calling thread's most recent failed call ("" if none).
+ * The string stays valid until the thread's next failing call. */
+const char *sw_last_error(void);
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * The context holds device properties, the kernel tuning table and a device
+ * status word.  Destroy it after every plan made from it. */
+int sw_ctx_create(int32_t device, sw_ctx **out);
+int sw_ctx_destroy(sw_ctx *ctx);
+
+/* Number of streaming multiprocessors of the context's device. */
+int sw_ctx_sm_count(const sw_ctx *ctx, int32_t *out);
+
+/* Synchronise the context's device, return its device status word in
+ * *status (0 = no inconsistency detected by any kernel; bit 0 = a reverse
+ * pass did not reproduce its forward score) and clear it. */
+int sw_ctx_status(sw_ctx *ctx, int32_t *status);
+
+/* Batched-path tuning: the longest serial sweep, in wavefront steps
+ * (passes x (m + G - 1)), a pair may be given; pairs get the narrowest
+ * lane group G in {1, 2, 4, 8, 16, 32} that stays under it.  Applies to
+ * plans created afterwards.  Default 6000. */
+int sw_ctx_set_step_cap(sw_ctx *ctx, int32_t steps);
+
+/*
+ * Plan a batch.  q_offsets and r_offsets are HOST arrays of n_pairs + 1
+ * non-decreasing int64 offsets; score_matrix is a HOST row-major
+ * alphabet_size x alphabet_size int8 table (row = query residue).  The plan
+ * sorts the pairs by cost (longest first), buckets them into warp tasks,
+ * uploads its tables and allocates the device scratch the batch needs.
+ * Blocking; nothing is enqueued on any stream.
+ * Errors: SW_EINVAL (null pointer, n_pairs < 0, bad gaps/alphabet/mode),
+ * SW_ERANGE (a length above SW_MAX_LEN or offsets decreasing), SW_ENOMEM,
+ * SW_ECUDA.
+ */
+int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                   int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                   int32_t gap_open, int32_t gap_extend, int32_t mode, uint32_t flags,
+                   sw_plan **out);
+
+/*
+ * Run a plan on `stream`.  q_seqs / r_seqs are DEVICE pointers to the
+ * residues the plan's offsets index; the five outputs are DEVICE arrays of
+ * n_pairs int32, written at each pair's position in the batch.  Residue
+ * codes are clamped to alphabet_size - 1 on the device (use
+ * sw_check_residues to validate).  Asynchronous; the plan may be executed
+ * again once this execution has been ordered before the next on the same
+ * stream.  Executions of one plan on different streams must not overlap.
+ */
+int sw_plan_execute(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_seqs,
+                    int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
+                    int32_t *out_qstart, int32_t *out_rstart, void *stream);
+
+/*
+ * Run a plan on HOST buffers: copies q_seqs[0 .. q_offsets[n_pairs]) and
+ * r_seqs[0 .. r_offsets[n_pairs]) (offsets as planned) to plan-owned device
+ * buffers on `stream`, executes, copies the results to out_host (5 x n_pairs
+ * int32: all scores, then all qend, rend, qstart, rstart) and synchronises
+ * `stream`.  Page-locked host memory makes the copies asynchronous DMA.
+ * The staging buffers are allocated on the first call and kept by the plan.
+ */
+int sw_plan_execute_host(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_seqs,
+                         int32_t *out_host, void *stream);
+
+/* Pairs, passes and kernel launches of a plan (any pointer may be NULL):
+ * n_group_tasks warp tasks in the persistent kernel, n_plain pairs in the
+ * one-block-per-pair kernel, launches = kernels one execution enqueues. */
+int sw_plan_info(const sw_plan *plan, int32_t *n_group_tasks, int32_t *n_plain,
+                 int32_t *launches, int64_t *scratch_bytes);
+
+int sw_plan_destroy(sw_plan *plan);
+
+/*
+ * One-shot alignment of a batch whose sequences AND offsets are on the
+ * DEVICE (score_matrix on the HOST).  Reads the offsets back to plan the
+ * batch, which synchronises `stream` once, then enqueues the work on
+ * `stream` and returns; the temporary plan is released when the work is
+ * done.  Uses a per-device default context.  For repeated batches of the
+ * same shape, plan once with sw_plan_create and call sw_plan_execute.
+ */
+int sw_align_batch(const uint8_t *q_seqs, const int64_t *q_offsets,
+                   const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                   const int8_t *score_matrix, int32_t alphabet_size,
+                   int32_t gap_open, int32_t gap_extend,
+                   int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
+                   int32_t *out_qstart, int32_t *out_rstart, void *stream);
+
+/*
+ * As sw_align_batch with an explicit context and mode (sw_mode).
+ */
+int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
+                      const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                      const int8_t *score_matrix, int32_t alphabet_size,
+                      int32_t gap_open, int32_t gap_extend, int32_t mode,
+                      int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
+                      int32_t *out_qstart, int32_t *out_rstart, void *stream);
+
+/*
+ * Validate residue codes on the device: counts the codes >= alphabet_size in
+ * seqs[0 .. n) into *bad_count (a DEVICE int64, overwritten).  Asynchronous.
+ */
+int sw_check_residues(const uint8_t *seqs, int64_t n, int32_t alphabet_size,
+                      int64_t *bad_count, void *stream);
+
+/*
+ * Integer issue-rate microbenchmark on `device` (made current for the call;
+ * synchronous).  op: 0 = 32-bit add, 1 = 32-bit max, 2 = __viaddmax_s32
+ * (add then max), 3 = __vimax3_s32_relu, 4 = __viaddmax_s16x2,
+ * 5 = __vimax_s32_relu.  Runs 64 warps per SM, each thread 8 independent
+ * chains of `iters` x 16 instructions, and returns whole-device
+ * instructions per second (per 32-bit lane) in *ops_per_s and the timed
+ * duration in *seconds (may be NULL).  This measures the denominator of the
+ * alignment kernels' roofline; the paper has no counterpart.
+ */
+int sw_microbench_int(int32_t op, int32_t device, int64_t iters, double *ops_per_s,
+                      double *seconds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB_H */

@@ -1,0 +1,275 @@
+"""Python binding of libswgb (batched Smith-Waterman/Gotoh on GB300).
+
+Argument marshalling only: every step of an alignment runs in the CUDA
+library behind the C ABI declared in include/swgb.h.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if libswgb.so is
+missing or cannot load, load() raises.
+
+Functions keep the C names (sw_plan_create, sw_plan_execute, sw_align_batch,
+...) and take torch tensors, numpy arrays or raw integer addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswgb.so")
+
+SW_OK, SW_EINVAL, SW_ERANGE, SW_ENOMEM, SW_ECUDA, SW_ETIMEOUT, SW_EBUDGET = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "SW_OK", -1: "SW_EINVAL", -2: "SW_ERANGE", -3: "SW_ENOMEM", -4: "SW_ECUDA",
+                -5: "SW_ETIMEOUT", -6: "SW_EBUDGET"}
+SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
+SW_PLAN_GRAPH = 1
+SW_MAX_LEN = 65535
+
+# Every function the library exports, with its ctypes signature.
+_P = ctypes.c_void_p
+_I32, _I64, _U32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+_PP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "sw_last_error": ([], ctypes.c_char_p),
+    "sw_ctx_create": ([_I32, _PP], ctypes.c_int),
+    "sw_ctx_destroy": ([_P], ctypes.c_int),
+    "sw_ctx_sm_count": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_ctx_status": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_ctx_set_step_cap": ([_P, _I32], ctypes.c_int),
+    "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
+    "sw_plan_execute": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "sw_plan_execute_host": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "sw_plan_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                      ctypes.POINTER(_I64)], ctypes.c_int),
+    "sw_plan_destroy": ([_P], ctypes.c_int),
+    "sw_align_batch": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
+                       ctypes.c_int),
+    "sw_align_batch_ex": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P,
+                           _P, _P], ctypes.c_int),
+    "sw_check_residues": ([_P, _I64, _I32, _P, _P], ctypes.c_int),
+    "sw_microbench_int": ([_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+}
+
+_lib = None
+
+
+class SwError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load():
+    """Load libswgb.so (built by build.py / __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libswgb.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, fn: str) -> None:
+    if rc != SW_OK:
+        raise SwError(fn, rc, load().sw_last_error().decode(errors="replace"))
+
+
+def _addr(x) -> int | None:
+    """Address of a torch tensor / numpy array / int (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _host_i64(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a), dtype=np.int64)
+    return a
+
+
+def _host_i8(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int8)
+
+
+# ----------------------------------------------------------------- context
+
+def sw_ctx_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().sw_ctx_create(device, ctypes.byref(h)), "sw_ctx_create")
+    return h.value
+
+
+def sw_ctx_destroy(ctx: int) -> None:
+    _check(load().sw_ctx_destroy(ctx), "sw_ctx_destroy")
+
+
+def sw_ctx_sm_count(ctx: int) -> int:
+    v = _I32()
+    _check(load().sw_ctx_sm_count(ctx, ctypes.byref(v)), "sw_ctx_sm_count")
+    return v.value
+
+
+def sw_ctx_status(ctx: int) -> int:
+    v = _I32()
+    _check(load().sw_ctx_status(ctx, ctypes.byref(v)), "sw_ctx_status")
+    return v.value
+
+
+def sw_ctx_set_step_cap(ctx: int, steps: int) -> None:
+    _check(load().sw_ctx_set_step_cap(ctx, steps), "sw_ctx_set_step_cap")
+
+
+# -------------------------------------------------------------------- plan
+
+def sw_plan_create(ctx: int, q_offsets, r_offsets, score_matrix, gap_open: int, gap_extend: int,
+                   mode: int = SW_MODE_AUTO, flags: int = 0) -> int:
+    """q_offsets / r_offsets / score_matrix are host arrays (numpy-convertible)."""
+    qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
+    mat = _host_i8(score_matrix)
+    if mat.ndim != 2 or mat.shape[0] != mat.shape[1]:
+        raise ValueError("score_matrix must be square")
+    n = len(qo) - 1
+    if len(ro) != n + 1:
+        raise ValueError("q_offsets and r_offsets differ in length")
+    h = ctypes.c_void_p()
+    _check(load().sw_plan_create(ctx, qo.ctypes.data, ro.ctypes.data, n, mat.ctypes.data,
+                                 mat.shape[0], gap_open, gap_extend, mode, flags,
+                                 ctypes.byref(h)), "sw_plan_create")
+    return h.value
+
+
+def sw_plan_execute(plan: int, q_seqs, r_seqs, out, stream=None) -> None:
+    """out: a (5, n_pairs) int32 CUDA tensor (score, qend, rend, qstart, rstart) or 5 tensors."""
+    outs = [out[k] for k in range(5)]
+    _check(load().sw_plan_execute(plan, _addr(q_seqs), _addr(r_seqs), *[_addr(o) for o in outs],
+                                  _stream(stream)), "sw_plan_execute")
+
+
+def sw_plan_execute_host(plan: int, q_seqs, r_seqs, out_host, stream=None) -> None:
+    """Host numpy/pinned-torch buffers in and out; out_host is (5, n_pairs) int32."""
+    _check(load().sw_plan_execute_host(plan, _addr(q_seqs), _addr(r_seqs), _addr(out_host),
+                                       _stream(stream)), "sw_plan_execute_host")
+
+
+def sw_plan_info(plan: int) -> dict:
+    t, p, l = _I32(), _I32(), _I32()
+    sb = _I64()
+    _check(load().sw_plan_info(plan, ctypes.byref(t), ctypes.byref(p), ctypes.byref(l),
+                               ctypes.byref(sb)), "sw_plan_info")
+    return {"group_tasks": t.value, "plain_pairs": p.value, "launches": l.value,
+            "scratch_bytes": sb.value}
+
+
+def sw_plan_destroy(plan: int) -> None:
+    _check(load().sw_plan_destroy(plan), "sw_plan_destroy")
+
+
+# ---------------------------------------------------------------- one-shot
+
+def sw_align_batch(q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, gap_open: int,
+                   gap_extend: int, out, stream=None) -> None:
+    """Sequences, offsets and out on the device; score_matrix on the host."""
+    mat = _host_i8(score_matrix)
+    n = int(q_offsets.shape[0]) - 1
+    outs = [out[k] for k in range(5)]
+    _check(load().sw_align_batch(_addr(q_seqs), _addr(q_offsets), _addr(r_seqs), _addr(r_offsets),
+                                 n, mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
+                                 *[_addr(o) for o in outs], _stream(stream)), "sw_align_batch")
+
+
+def sw_align_batch_ex(ctx: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, gap_open: int,
+                      gap_extend: int, mode: int, out, stream=None) -> None:
+    mat = _host_i8(score_matrix)
+    n = int(q_offsets.shape[0]) - 1
+    outs = [out[k] for k in range(5)]
+    _check(load().sw_align_batch_ex(ctx, _addr(q_seqs), _addr(q_offsets), _addr(r_seqs),
+                                    _addr(r_offsets), n, mat.ctypes.data, mat.shape[0], gap_open,
+                                    gap_extend, mode, *[_addr(o) for o in outs], _stream(stream)),
+           "sw_align_batch_ex")
+
+
+def sw_check_residues(seqs, n: int, alphabet_size: int, bad_count, stream=None) -> None:
+    _check(load().sw_check_residues(_addr(seqs), n, alphabet_size, _addr(bad_count),
+                                    _stream(stream)), "sw_check_residues")
+
+
+MICROBENCH_OPS = {"iadd": 0, "imax": 1, "viaddmax_s32": 2, "vimax3_s32_relu": 3,
+                  "viaddmax_s16x2": 4, "vimax_s32_relu": 5}
+
+
+def sw_microbench_int(op: str, device: int = 0, iters: int = 4096) -> tuple[float, float]:
+    """(instructions per second over the device, seconds) for one instruction kind."""
+    rate, secs = ctypes.c_double(), ctypes.c_double()
+    _check(load().sw_microbench_int(MICROBENCH_OPS[op], device, iters, ctypes.byref(rate),
+                                    ctypes.byref(secs)), "sw_microbench_int")
+    return rate.value, secs.value
+
+
+# ----------------------------------------------------------------- helpers
+
+class Aligner:
+    """A planned batch resident on one device: upload once, execute many times."""
+
+    def __init__(self, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, gap_open, gap_extend,
+                 mode=SW_MODE_AUTO, flags=0, device=0, ctx=None):
+        import torch
+        self.device = torch.device("cuda", device)
+        self._own_ctx = ctx is None
+        self.ctx = sw_ctx_create(device) if ctx is None else ctx
+        q_offsets = _host_i64(q_offsets)
+        r_offsets = _host_i64(r_offsets)
+        self.n_pairs = len(q_offsets) - 1
+        self.q = torch.from_numpy(np.ascontiguousarray(q_seqs, dtype=np.uint8)).to(self.device)
+        self.r = torch.from_numpy(np.ascontiguousarray(r_seqs, dtype=np.uint8)).to(self.device)
+        if self.q.numel() == 0:
+            self.q = torch.zeros(1, dtype=torch.uint8, device=self.device)
+        if self.r.numel() == 0:
+            self.r = torch.zeros(1, dtype=torch.uint8, device=self.device)
+        self.out = torch.full((5, max(self.n_pairs, 1)), -7, dtype=torch.int32, device=self.device)
+        self.plan = sw_plan_create(self.ctx, q_offsets, r_offsets, score_matrix, gap_open,
+                                   gap_extend, mode, flags)
+
+    def run(self, stream=None):
+        sw_plan_execute(self.plan, self.q, self.r, self.out, stream)
+        return self.out
+
+    def results(self) -> np.ndarray:
+        """(n_pairs, 5) int32 host array after the last run (synchronises)."""
+        return self.out[:, :self.n_pairs].T.contiguous().cpu().numpy()
+
+    def info(self) -> dict:
+        return sw_plan_info(self.plan)
+
+    def close(self):
+        if self.plan:
+            sw_plan_destroy(self.plan)
+            self.plan = None
+        if self._own_ctx and self.ctx:
+            sw_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

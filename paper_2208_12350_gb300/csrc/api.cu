@@ -1,0 +1,592 @@
+// C ABI of the library: argument checks, host-side planning of a batch,
+// launch sequencing and CUDA-graph replay.  Declarations and the contract
+// of each entry point are in include/swgb.h.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sw_internal.h"
+#include "swgb.h"
+
+using namespace swgb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define SW_CUDA_TRY(call)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return fail(SW_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+// Makes a device current for a scope and restores the previous one.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+int upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return SW_OK;
+    if (cudaMalloc(dst, src.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SW_ENOMEM, "cudaMalloc of %zu bytes failed", src.size() * sizeof(T));
+    }
+    SW_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SW_OK;
+}
+
+constexpr int kDefaultStepCap = 6000;
+
+}  // namespace
+
+struct sw_ctx {
+    int device = 0;
+    int sm_count = 0;
+    char name[256] = {0};
+    int32_t *d_status = nullptr;
+    int step_cap = kDefaultStepCap;  // longest serial sweep a group may get (steps)
+    std::mutex mu;
+    std::vector<std::pair<sw_plan *, cudaEvent_t>> retired;
+};
+
+struct sw_plan {
+    sw_ctx *ctx = nullptr;
+    int32_t n_pairs = 0;
+    int A = 0, go = 0, ge = 0, mode = 0;
+    uint32_t flags = 0;
+    int8_t mat[kMaxAlphabet * kMaxAlphabet] = {0};
+    ProfileKind kind = ProfileKind::kInt32;
+    // persistent group kernel
+    PairInfo *d_pairs = nullptr;
+    GroupTask *d_tasks = nullptr;
+    int32_t n_tasks = 0;
+    int32_t *d_counter = nullptr;
+    uint32_t *d_scratch = nullptr;
+    int64_t scratch_words = 0;
+    int grid = 0;
+    // one-block-per-pair kernel
+    PairInfo *d_plain = nullptr;
+    int32_t n_plain = 0;
+    int plain_threads = 32;
+    int plain_kmax = 1;
+    // host-buffer execution: staging copies of the inputs and outputs
+    int64_t q_bytes = 0, r_bytes = 0;
+    uint8_t *d_q = nullptr, *d_r = nullptr;
+    int32_t *d_out = nullptr;
+    // graph replay
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[8] = {nullptr};
+};
+
+static void plan_free(sw_plan *p) {
+    if (!p) return;
+    DeviceGuard g(p->ctx->device);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    cudaFree(p->d_pairs);
+    cudaFree(p->d_tasks);
+    cudaFree(p->d_counter);
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_plain);
+    cudaFree(p->d_q);
+    cudaFree(p->d_r);
+    cudaFree(p->d_out);
+    delete p;
+}
+
+static void reap_retired(sw_ctx *ctx, bool wait) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto &v = ctx->retired;
+    for (size_t i = 0; i < v.size();) {
+        cudaError_t q = wait ? cudaEventSynchronize(v[i].second) : cudaEventQuery(v[i].second);
+        if (q == cudaSuccess || (q != cudaErrorNotReady)) {
+            cudaEventDestroy(v[i].second);
+            plan_free(v[i].first);
+            v[i] = v.back();
+            v.pop_back();
+        } else {
+            ++i;
+        }
+    }
+    cudaGetLastError();  // clear a cudaErrorNotReady left by the query
+}
+
+extern "C" {
+
+const char *sw_last_error(void) { return g_last_error.c_str(); }
+
+int sw_ctx_create(int32_t device, sw_ctx **out) {
+    if (!out) return fail(SW_EINVAL, "sw_ctx_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    SW_CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count)
+        return fail(SW_EINVAL, "sw_ctx_create: device %d not in [0, %d)", device, count);
+    DeviceGuard g(device);
+    if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", device);
+    auto *ctx = new sw_ctx();
+    ctx->device = device;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return fail(SW_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    }
+    ctx->sm_count = prop.multiProcessorCount;
+    snprintf(ctx->name, sizeof ctx->name, "%s", prop.name);
+    if (cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ctx->d_status);
+        delete ctx;
+        return fail(SW_ENOMEM, "sw_ctx_create: status word allocation failed");
+    }
+    *out = ctx;
+    return SW_OK;
+}
+
+int sw_ctx_destroy(sw_ctx *ctx) {
+    if (!ctx) return SW_OK;
+    reap_retired(ctx, true);
+    {
+        DeviceGuard g(ctx->device);
+        cudaFree(ctx->d_status);
+    }
+    delete ctx;
+    return SW_OK;
+}
+
+int sw_ctx_sm_count(const sw_ctx *ctx, int32_t *out) {
+    if (!ctx || !out) return fail(SW_EINVAL, "sw_ctx_sm_count: NULL argument");
+    *out = ctx->sm_count;
+    return SW_OK;
+}
+
+int sw_ctx_status(sw_ctx *ctx, int32_t *status) {
+    if (!ctx || !status) return fail(SW_EINVAL, "sw_ctx_status: NULL argument");
+    DeviceGuard g(ctx->device);
+    SW_CUDA_TRY(cudaDeviceSynchronize());
+    SW_CUDA_TRY(cudaMemcpy(status, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    SW_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(int32_t)));
+    return SW_OK;
+}
+
+int sw_ctx_set_step_cap(sw_ctx *ctx, int32_t steps) {
+    if (!ctx || steps < 1) return fail(SW_EINVAL, "sw_ctx_set_step_cap: bad argument");
+    ctx->step_cap = steps;
+    return SW_OK;
+}
+
+int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                   int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                   int32_t gap_open, int32_t gap_extend, int32_t mode, uint32_t flags,
+                   sw_plan **out) {
+    if (!out) return fail(SW_EINVAL, "sw_plan_create: out is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(SW_EINVAL, "sw_plan_create: ctx is NULL");
+    if (n_pairs < 0) return fail(SW_EINVAL, "sw_plan_create: n_pairs < 0");
+    if (n_pairs > 0 && (!q_offsets || !r_offsets))
+        return fail(SW_EINVAL, "sw_plan_create: offsets are NULL");
+    if (!score_matrix) return fail(SW_EINVAL, "sw_plan_create: score_matrix is NULL");
+    if (alphabet_size < 1 || alphabet_size > SW_MAX_ALPHABET)
+        return fail(SW_EINVAL, "sw_plan_create: alphabet_size %d not in [1, %d]", alphabet_size,
+                    SW_MAX_ALPHABET);
+    if (gap_extend > 0 || gap_open > gap_extend)
+        return fail(SW_EINVAL,
+                    "sw_plan_create: need gap_open <= gap_extend <= 0 (got %d, %d)", gap_open,
+                    gap_extend);
+    if (gap_open < -SW_MAX_GAP) return fail(SW_EINVAL, "sw_plan_create: |gap_open| too large");
+    if (mode != SW_MODE_AUTO && mode != SW_MODE_PLAIN && mode != SW_MODE_BATCHED)
+        return fail(SW_EINVAL, "sw_plan_create: unknown mode %d", mode);
+    if (mode == SW_MODE_AUTO) mode = SW_MODE_BATCHED;
+
+    const int A = alphabet_size;
+    int smax = -128, smin = 127;
+    for (int i = 0; i < A * A; ++i) {
+        smax = std::max(smax, (int)score_matrix[i]);
+        smin = std::min(smin, (int)score_matrix[i]);
+    }
+    // lengths
+    std::vector<int32_t> n(n_pairs), m(n_pairs);
+    for (int32_t i = 0; i < n_pairs; ++i) {
+        const int64_t a = q_offsets[i + 1] - q_offsets[i];
+        const int64_t b = r_offsets[i + 1] - r_offsets[i];
+        if (q_offsets[i] < 0 || r_offsets[i] < 0 || a < 0 || b < 0)
+            return fail(SW_ERANGE, "sw_plan_create: offsets of pair %d negative or decreasing", i);
+        if (a > SW_MAX_LEN || b > SW_MAX_LEN)
+            return fail(SW_ERANGE, "sw_plan_create: pair %d has lengths (%lld, %lld) > %d", i,
+                        (long long)a, (long long)b, SW_MAX_LEN);
+        n[i] = (int32_t)a;
+        m[i] = (int32_t)b;
+    }
+    const bool gaps_scaled_ok = -gap_open <= kMaxScaledGap && -gap_extend <= kMaxScaledGap;
+
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    reap_retired(ctx, false);
+
+    auto *p = new sw_plan();
+    p->ctx = ctx;
+    p->n_pairs = n_pairs;
+    p->A = A;
+    p->go = gap_open;
+    p->ge = gap_extend;
+    p->mode = mode;
+    p->flags = flags;
+    std::memcpy(p->mat, score_matrix, (size_t)A * A);
+    if (A <= 4)
+        p->kind = ProfileKind::kInt32;
+    else if (smax - gap_open <= 127 && smin - gap_open >= -127)
+        p->kind = ProfileKind::kInt8;
+    else
+        p->kind = ProfileKind::kInt32;
+
+    struct Item {
+        int32_t id, n, m, log2g, passes;
+    };
+    std::vector<Item> items;
+    std::vector<PairInfo> plain;
+    items.reserve(n_pairs);
+    int plain_max_n = 0;
+    for (int32_t i = 0; i < n_pairs; ++i) {
+        const bool scaled = gaps_scaled_ok &&
+                            (smax <= 0 || (int64_t)smax * std::min(n[i], m[i]) <= kMaxScaledScore);
+        if (mode == SW_MODE_PLAIN || !scaled) {
+            PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
+            plain.push_back(pi);
+            plain_max_n = std::max(plain_max_n, n[i]);
+            continue;
+        }
+        int log2g = 5, passes = 0;
+        if (n[i] > 0 && m[i] > 0) {
+            for (int lg = 0; lg <= 5; ++lg) {
+                const int G = 1 << lg;
+                const int ps = (n[i] + G * kRows - 1) / (G * kRows);
+                if ((int64_t)ps * (m[i] + G - 1) <= ctx->step_cap || lg == 5) {
+                    log2g = lg;
+                    passes = ps;
+                    break;
+                }
+            }
+        } else {
+            log2g = 0;
+        }
+        items.push_back({i, n[i], m[i], log2g, passes});
+    }
+    // group pairs of equal (G, passes) into warp tasks, longest sweeps first
+    std::sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+        if (x.log2g != y.log2g) return x.log2g > y.log2g;
+        if (x.passes != y.passes) return x.passes > y.passes;
+        if (x.m != y.m) return x.m > y.m;
+        return x.id < y.id;
+    });
+    struct TaskTmp {
+        int64_t cost;
+        int32_t begin, count, log2g;
+    };
+    std::vector<TaskTmp> tt;
+    for (size_t k = 0; k < items.size();) {
+        const int lg = items[k].log2g, ps = items[k].passes;
+        const int cap = 32 >> lg;
+        size_t e = k;
+        while (e < items.size() && (int)(e - k) < cap && items[e].log2g == lg &&
+               items[e].passes == ps)
+            ++e;
+        const int64_t cost = (int64_t)std::max(ps, 1) * (items[k].m + (1 << lg) - 1);
+        tt.push_back({cost, (int32_t)k, (int32_t)(e - k), lg});
+        k = e;
+    }
+    std::stable_sort(tt.begin(), tt.end(),
+                     [](const TaskTmp &a, const TaskTmp &b) { return a.cost > b.cost; });
+    std::vector<PairInfo> pairs;
+    std::vector<GroupTask> tasks;
+    pairs.reserve(items.size());
+    tasks.reserve(tt.size());
+    int64_t scratch = 0;
+    for (const TaskTmp &t : tt) {
+        GroupTask gt{(int32_t)pairs.size(), t.count, t.log2g, 0};
+        tasks.push_back(gt);
+        for (int32_t u = 0; u < t.count; ++u) {
+            const Item &it = items[t.begin + u];
+            PairInfo pi{q_offsets[it.id], r_offsets[it.id], -1, it.n, it.m, it.id, 0};
+            if (it.passes >= 2) {
+                pi.scratch = scratch;
+                scratch += 2 * (int64_t)it.m;
+            }
+            pairs.push_back(pi);
+        }
+    }
+    p->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
+    p->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
+    p->n_tasks = (int32_t)tasks.size();
+    p->n_plain = (int32_t)plain.size();
+    p->scratch_words = scratch;
+    int rc;
+    if ((rc = upload(&p->d_pairs, pairs)) || (rc = upload(&p->d_tasks, tasks)) ||
+        (rc = upload(&p->d_plain, plain))) {
+        plan_free(p);
+        return rc;
+    }
+    if (cudaMalloc(&p->d_counter, sizeof(int32_t)) != cudaSuccess ||
+        (scratch > 0 && cudaMalloc(&p->d_scratch, scratch * sizeof(uint32_t)) != cudaSuccess)) {
+        cudaGetLastError();
+        plan_free(p);
+        return fail(SW_ENOMEM, "sw_plan_create: scratch allocation (%lld words) failed",
+                    (long long)scratch);
+    }
+    if (p->n_tasks > 0) {
+        int smem = 0;
+        const int bps = group_blocks_per_sm(p->kind, A, &smem);
+        if (bps <= 0) {
+            plan_free(p);
+            return fail(SW_ECUDA, "sw_plan_create: group kernel does not fit (%d B smem)", smem);
+        }
+        const int64_t want = ((int64_t)p->n_tasks + kGroupWarps - 1) / kGroupWarps;
+        p->grid = (int)std::min<int64_t>((int64_t)bps * ctx->sm_count, want);
+    }
+    if (p->n_plain > 0) {
+        int T = ((std::min(plain_max_n, 1024) + 31) / 32) * 32;
+        if (T < 32) T = 32;
+        p->plain_threads = T;
+        p->plain_kmax = (plain_max_n + T - 1) / T > 1 ? 64 : 1;
+    }
+    *out = p;
+    return SW_OK;
+}
+
+static int enqueue(sw_plan *p, const uint8_t *q, const uint8_t *r, const Outputs &o,
+                   cudaStream_t s) {
+    if (p->n_tasks > 0) {
+        SW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t), s));
+        GroupParams gp;
+        std::memset(&gp, 0, sizeof gp);
+        gp.q = q;
+        gp.r = r;
+        gp.pairs = p->d_pairs;
+        gp.tasks = p->d_tasks;
+        gp.n_tasks = p->n_tasks;
+        gp.counter = p->d_counter;
+        gp.scratch = p->d_scratch;
+        gp.status = p->ctx->d_status;
+        gp.out = o;
+        gp.alphabet = p->A;
+        gp.gap_open = p->go;
+        gp.gap_extend = p->ge;
+        std::memcpy(gp.mat, p->mat, sizeof gp.mat);
+        SW_CUDA_TRY(launch_group(gp, p->kind, p->grid, s));
+    }
+    if (p->n_plain > 0) {
+        PlainParams pp;
+        std::memset(&pp, 0, sizeof pp);
+        pp.q = q;
+        pp.r = r;
+        pp.pairs = p->d_plain;
+        pp.n_pairs = p->n_plain;
+        pp.status = p->ctx->d_status;
+        pp.out = o;
+        pp.alphabet = p->A;
+        pp.gap_open = p->go;
+        pp.gap_extend = p->ge;
+        std::memcpy(pp.mat, p->mat, sizeof pp.mat);
+        SW_CUDA_TRY(launch_plain(pp, p->plain_threads, p->plain_kmax, s));
+    }
+    return SW_OK;
+}
+
+int sw_plan_execute(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seqs,
+                    int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
+                    int32_t *out_qstart, int32_t *out_rstart, void *stream) {
+    if (!p) return fail(SW_EINVAL, "sw_plan_execute: plan is NULL");
+    if (p->n_pairs == 0) return SW_OK;
+    if (!q_seqs || !r_seqs || !out_score || !out_qend || !out_rend || !out_qstart ||
+        !out_rstart)
+        return fail(SW_EINVAL, "sw_plan_execute: NULL device pointer");
+    DeviceGuard g(p->ctx->device);
+    if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", p->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Outputs o{out_score, out_qend, out_rend, out_qstart, out_rstart};
+    const bool graph = (p->flags & SW_PLAN_GRAPH) && s != nullptr;
+    if (!graph) return enqueue(p, q_seqs, r_seqs, o, s);
+    const void *key[8] = {q_seqs, r_seqs, out_score, out_qend, out_rend, out_qstart, out_rstart,
+                          stream};
+    if (!p->gexec || std::memcmp(key, p->gkey, sizeof key) != 0) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        SW_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue(p, q_seqs, r_seqs, o, s);
+        cudaGraph_t graph_obj = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &graph_obj);
+        if (rc != SW_OK) {
+            if (graph_obj) cudaGraphDestroy(graph_obj);
+            return rc;
+        }
+        if (ec != cudaSuccess) return fail(SW_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ec));
+        const cudaError_t ei = cudaGraphInstantiate(&p->gexec, graph_obj, 0);
+        cudaGraphDestroy(graph_obj);
+        if (ei != cudaSuccess) {
+            p->gexec = nullptr;
+            return fail(SW_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+        }
+        std::memcpy(p->gkey, key, sizeof key);
+    }
+    SW_CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+    return SW_OK;
+}
+
+int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seqs,
+                         int32_t *out_host, void *stream) {
+    if (!p) return fail(SW_EINVAL, "sw_plan_execute_host: plan is NULL");
+    if (p->n_pairs == 0) return SW_OK;
+    if ((p->q_bytes > 0 && !q_seqs) || (p->r_bytes > 0 && !r_seqs) || !out_host)
+        return fail(SW_EINVAL, "sw_plan_execute_host: NULL host pointer");
+    DeviceGuard g(p->ctx->device);
+    if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", p->ctx->device);
+    if (!p->d_out) {
+        if (cudaMalloc(&p->d_q, (size_t)std::max<int64_t>(p->q_bytes, 1)) != cudaSuccess ||
+            cudaMalloc(&p->d_r, (size_t)std::max<int64_t>(p->r_bytes, 1)) != cudaSuccess ||
+            cudaMalloc(&p->d_out, (size_t)5 * p->n_pairs * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(p->d_q);
+            cudaFree(p->d_r);
+            cudaFree(p->d_out);
+            p->d_q = p->d_r = nullptr;
+            p->d_out = nullptr;
+            return fail(SW_ENOMEM, "sw_plan_execute_host: staging allocation failed");
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->q_bytes > 0)
+        SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, p->q_bytes, cudaMemcpyHostToDevice, s));
+    if (p->r_bytes > 0)
+        SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, p->r_bytes, cudaMemcpyHostToDevice, s));
+    const int64_t n = p->n_pairs;
+    int rc = sw_plan_execute(p, p->d_q, p->d_r, p->d_out, p->d_out + n, p->d_out + 2 * n,
+                             p->d_out + 3 * n, p->d_out + 4 * n, stream);
+    if (rc != SW_OK) return rc;
+    SW_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out, (size_t)5 * n * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, s));
+    SW_CUDA_TRY(cudaStreamSynchronize(s));
+    return SW_OK;
+}
+
+int sw_plan_info(const sw_plan *p, int32_t *n_group_tasks, int32_t *n_plain, int32_t *launches,
+                 int64_t *scratch_bytes) {
+    if (!p) return fail(SW_EINVAL, "sw_plan_info: plan is NULL");
+    if (n_group_tasks) *n_group_tasks = p->n_tasks;
+    if (n_plain) *n_plain = p->n_plain;
+    if (launches) *launches = (p->n_tasks > 0 ? 1 : 0) + (p->n_plain > 0 ? 1 : 0);
+    if (scratch_bytes) *scratch_bytes = p->scratch_words * (int64_t)sizeof(uint32_t);
+    return SW_OK;
+}
+
+int sw_plan_destroy(sw_plan *p) {
+    plan_free(p);
+    return SW_OK;
+}
+
+int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
+                      const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                      const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                      int32_t gap_extend, int32_t mode, int32_t *out_score, int32_t *out_qend,
+                      int32_t *out_rend, int32_t *out_qstart, int32_t *out_rstart,
+                      void *stream) {
+    if (!ctx) return fail(SW_EINVAL, "sw_align_batch_ex: ctx is NULL");
+    if (n_pairs < 0) return fail(SW_EINVAL, "sw_align_batch_ex: n_pairs < 0");
+    if (n_pairs == 0) return SW_OK;
+    if (!q_offsets || !r_offsets) return fail(SW_EINVAL, "sw_align_batch_ex: offsets are NULL");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> hq((size_t)n_pairs + 1), hr((size_t)n_pairs + 1);
+    SW_CUDA_TRY(cudaMemcpyAsync(hq.data(), q_offsets, hq.size() * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+    SW_CUDA_TRY(cudaMemcpyAsync(hr.data(), r_offsets, hr.size() * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+    SW_CUDA_TRY(cudaStreamSynchronize(s));
+    sw_plan *p = nullptr;
+    int rc = sw_plan_create(ctx, hq.data(), hr.data(), n_pairs, score_matrix, alphabet_size,
+                            gap_open, gap_extend, mode, 0u, &p);
+    if (rc != SW_OK) return rc;
+    rc = sw_plan_execute(p, q_seqs, r_seqs, out_score, out_qend, out_rend, out_qstart,
+                         out_rstart, stream);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (ev) cudaEventDestroy(ev);
+        cudaStreamSynchronize(s);
+        plan_free(p);
+        return rc != SW_OK ? rc : fail(SW_ECUDA, "sw_align_batch: event record failed");
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->retired.emplace_back(p, ev);
+    }
+    return rc;
+}
+
+static std::mutex g_default_mu;
+static std::vector<sw_ctx *> g_default_ctx;
+
+int sw_align_batch(const uint8_t *q_seqs, const int64_t *q_offsets, const uint8_t *r_seqs,
+                   const int64_t *r_offsets, int32_t n_pairs, const int8_t *score_matrix,
+                   int32_t alphabet_size, int32_t gap_open, int32_t gap_extend,
+                   int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
+                   int32_t *out_qstart, int32_t *out_rstart, void *stream) {
+    int dev = 0;
+    SW_CUDA_TRY(cudaGetDevice(&dev));
+    sw_ctx *ctx = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_default_mu);
+        if ((int)g_default_ctx.size() <= dev) g_default_ctx.resize(dev + 1, nullptr);
+        if (!g_default_ctx[dev]) {
+            const int rc = sw_ctx_create(dev, &g_default_ctx[dev]);
+            if (rc != SW_OK) return rc;
+        }
+        ctx = g_default_ctx[dev];
+    }
+    return sw_align_batch_ex(ctx, q_seqs, q_offsets, r_seqs, r_offsets, n_pairs, score_matrix,
+                             alphabet_size, gap_open, gap_extend, SW_MODE_AUTO, out_score,
+                             out_qend, out_rend, out_qstart, out_rstart, stream);
+}
+
+int sw_check_residues(const uint8_t *seqs, int64_t n, int32_t alphabet_size, int64_t *bad_count,
+                      void *stream) {
+    if (n < 0 || !bad_count || (n > 0 && !seqs))
+        return fail(SW_EINVAL, "sw_check_residues: bad argument");
+    if (alphabet_size < 1 || alphabet_size > SW_MAX_ALPHABET)
+        return fail(SW_EINVAL, "sw_check_residues: bad alphabet size");
+    SW_CUDA_TRY(launch_check_residues(seqs, n, alphabet_size,
+                                      reinterpret_cast<unsigned long long *>(bad_count),
+                                      (cudaStream_t)stream));
+    return SW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Integer issue-rate microbenchmark: the denominator of the alignment
+// kernels' roofline.  Each thread runs 8 independent dependency chains of
+// one instruction kind; the kernel reports instructions per second for the
+// whole device.  Operands come from kernel arguments and the results are
+// stored, so nothing is folded away.
+#include "sw_internal.h"
+#include "swgb.h"
+
+namespace swgb {
+namespace {
+
+template <int OP>
+__device__ __forceinline__ int step(int a, int b, int c) {
+    if constexpr (OP == 0) return a + b;                          // IADD
+    if constexpr (OP == 1) return max(a, b);                      // IMNMX
+    if constexpr (OP == 2) return __viaddmax_s32(a, b, c);        // add + max
+    if constexpr (OP == 3) return __vimax3_s32_relu(a, b, c);     // 3-way max with 0
+    if constexpr (OP == 4) return (int)__viaddmax_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
+    if constexpr (OP == 5) return __vimax_s32_relu(a, b);         // 2-way max with 0
+    return a;
+}
+
+template <int OP>
+__global__ void int_rate_kernel(int64_t iters, int b, int c, int *sink) {
+    int x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+    int x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            x0 = step<OP>(x0, b, c);
+            x1 = step<OP>(x1, b, c);
+            x2 = step<OP>(x2, b, c);
+            x3 = step<OP>(x3, b, c);
+            x4 = step<OP>(x4, b, c);
+            x5 = step<OP>(x5, b, c);
+            x6 = step<OP>(x6, b, c);
+            x7 = step<OP>(x7, b, c);
+        }
+    }
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = x0 ^ x1 ^ x2 ^ x3 ^ x4 ^ x5 ^ x6 ^ x7;
+}
+
+template <int OP>
+cudaError_t run(int blocks, int threads, int64_t iters, int *sink, cudaStream_t s) {
+    int_rate_kernel<OP><<<blocks, threads, 0, s>>>(iters, 3, -5, sink);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace swgb
+
+extern "C" int sw_microbench_int(int32_t op, int32_t device, int64_t iters, double *ops_per_s,
+                                 double *seconds) {
+    using namespace swgb;
+    if (!ops_per_s || op < 0 || op > 5 || iters < 1) return SW_EINVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return SW_ECUDA;
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, device);
+    const int threads = 512;
+    const int blocks = prop.multiProcessorCount * 4;  // 64 warps per SM
+    int *sink = nullptr;
+    cudaEvent_t e0, e1;
+    int rc = SW_OK;
+    if (cudaMalloc(&sink, (size_t)blocks * threads * sizeof(int)) != cudaSuccess) {
+        cudaSetDevice(prev);
+        return SW_ENOMEM;
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto launch = [&](int64_t it) -> cudaError_t {
+        switch (op) {
+            case 0: return run<0>(blocks, threads, it, sink, 0);
+            case 1: return run<1>(blocks, threads, it, sink, 0);
+            case 2: return run<2>(blocks, threads, it, sink, 0);
+            case 3: return run<3>(blocks, threads, it, sink, 0);
+            case 4: return run<4>(blocks, threads, it, sink, 0);
+            default: return run<5>(blocks, threads, it, sink, 0);
+        }
+    };
+    float ms = 0.f;
+    if (launch(1) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        rc = SW_ECUDA;
+    } else {
+        cudaEventRecord(e0, 0);
+        launch(iters);
+        cudaEventRecord(e1, 0);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = SW_ECUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    const double ops = (double)blocks * threads * (double)iters * 16.0 * 8.0;
+    *ops_per_s = ms > 0 ? ops / (ms * 1e-3) : 0.0;
+    if (seconds) *seconds = ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    cudaSetDevice(prev);
+    return rc;
+}

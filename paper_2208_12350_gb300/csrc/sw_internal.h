@@ -1,0 +1,91 @@
+// Internal declarations shared by the host API and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swgb {
+
+// Scores on the batched path are held scaled by 2^16 so that the low half
+// of every H value is free for the column part of the end-cell key
+// (H << 16) | (65535 - j); one max-plus instruction per cell then tracks the
+// maximal cell with the end rule (largest H, then smallest column).
+constexpr int kKeyShift = 16;
+constexpr int32_t kScaledNegInf = -(1 << 30);  // E/F "-infinity", scaled domain
+constexpr int32_t kPlainNegInf = -(1 << 30);   // E/F "-infinity", plain int32
+constexpr int32_t kScaledPad = -(1 << 29);     // profile score of rows beyond n
+constexpr int kMaxScaledScore = 32766;         // (S << 16) + 65535 < 2^31
+constexpr int kMaxScaledGap = 16383;
+constexpr int kMaxAlphabet = 32;
+constexpr int kRows = 16;                      // query rows per lane (group kernel)
+constexpr int kGroupWarps = 4;                 // warps per block (group kernel)
+
+// One pair as the device sees it (plan order).
+struct PairInfo {
+    int64_t q;        // offset of the first query residue
+    int64_t r;        // offset of the first reference residue
+    int64_t scratch;  // offset (uint32 units) of 2*m boundary words, or -1
+    int32_t n, m;     // lengths
+    int32_t id;       // output position in the caller's batch
+    int32_t pad;
+};
+
+// A warp's unit of work in the persistent kernel: `count` consecutive pairs
+// of the plan's pair array starting at `first`, each on G = 1 << log2g lanes.
+struct GroupTask {
+    int32_t first;
+    int32_t count;
+    int32_t log2g;
+    int32_t pad;
+};
+
+struct Outputs {
+    int32_t *score, *qend, *rend, *qstart, *rstart;
+};
+
+struct GroupParams {
+    const uint8_t *q;
+    const uint8_t *r;
+    const PairInfo *pairs;
+    const GroupTask *tasks;
+    int32_t n_tasks;
+    int32_t *counter;   // task queue head, zeroed before each launch
+    uint32_t *scratch;  // strip-boundary words
+    int32_t *status;    // device status word (0 = ok)
+    Outputs out;
+    int32_t alphabet;
+    int32_t gap_open, gap_extend;  // unscaled, <= 0
+    int8_t mat[kMaxAlphabet * kMaxAlphabet];
+};
+
+struct PlainParams {
+    const uint8_t *q;
+    const uint8_t *r;
+    const PairInfo *pairs;  // one block per entry
+    int32_t n_pairs;
+    int32_t *status;
+    Outputs out;
+    int32_t alphabet;
+    int32_t gap_open, gap_extend;
+    int8_t mat[kMaxAlphabet * kMaxAlphabet];
+};
+
+// Device status bits.
+constexpr int32_t kStatusReverseMismatch = 1;  // reverse pass lost the score
+
+// Profile element width of the group kernel.
+enum class ProfileKind : int { kInt32 = 0, kInt8 = 1 };
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_group(const GroupParams &p, ProfileKind kind, int grid, cudaStream_t s);
+int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes);
+size_t group_smem_bytes(ProfileKind kind, int alphabet);
+
+cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_max,
+                         cudaStream_t s);
+size_t plain_smem_bytes(int threads, int alphabet);
+
+cudaError_t launch_check_residues(const uint8_t *seqs, int64_t n, int alphabet,
+                                  unsigned long long *bad, cudaStream_t s);
+
+}  // namespace swgb

@@ -1,0 +1,246 @@
+"""GPU parity: every output of the CUDA path equals the CPU oracle, bit for bit.
+
+The path is exact integer max-plus arithmetic, so the tolerance is zero on
+all five outputs (score, qend, rend, qstart, rstart).  Inputs come from the
+seeded generators in `workloads`; expected values from `oracle` only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def run_lib(swgb, ctx, b, mode=None, flags=0, step_cap=None):
+    if step_cap is not None:
+        swgb.sw_ctx_set_step_cap(ctx, step_cap)
+    try:
+        al = swgb.Aligner(b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix, b.gap_open,
+                          b.gap_extend, mode=swgb.SW_MODE_AUTO if mode is None else mode,
+                          flags=flags, ctx=ctx)
+        al.run()
+        got = al.results()
+        info = al.info()
+        al.close()
+    finally:
+        if step_cap is not None:
+            swgb.sw_ctx_set_step_cap(ctx, 6000)
+    assert swgb.sw_ctx_status(ctx) == 0
+    return got, info
+
+
+def assert_same(got, expect, name):
+    bad = np.flatnonzero(np.any(got != expect, axis=1))
+    if len(bad):
+        i = int(bad[0])
+        raise AssertionError(f"{name}: {len(bad)} pairs differ; first pair {i}: "
+                             f"got {got[i].tolist()} expected {expect[i].tolist()}")
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    c = gpu_lib.sw_ctx_create(0)
+    yield c
+    gpu_lib.sw_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_config0_full(gpu_lib, ctx, mode):
+    b = wl.gen_config(0)
+    expect = oracle.align_workload(b)
+    m = gpu_lib.SW_MODE_BATCHED if mode == "batched" else gpu_lib.SW_MODE_PLAIN
+    got, _ = run_lib(gpu_lib, ctx, b, mode=m)
+    assert_same(got, expect, f"config0/{mode}")
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_full_configs_batched_graph(gpu_lib, ctx, k):
+    """Workloads 1-3 at full size, in the launch form the benchmark times."""
+    b = wl.gen_config(k)
+    got, info = run_lib(gpu_lib, ctx, b, flags=gpu_lib.SW_PLAN_GRAPH)
+    expect = oracle.align_workload(b)
+    assert_same(got, expect, f"config{k}")
+    assert info["plain_pairs"] == 0  # all pairs inside the scaled path's bound
+
+
+def test_config1_plain_sampled(gpu_lib, ctx):
+    """The plain one-block-per-pair form on the full 100k-pair batch, sampled."""
+    b = wl.gen_config(1)
+    got, _ = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_PLAIN)
+    idx = np.random.default_rng(0).choice(b.n_pairs, 3000, replace=False)
+    expect = oracle.align_workload(b, idx=idx)
+    assert_same(got[idx], expect, "config1/plain sample")
+
+
+EDGE = [0, 1, 2, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
+        1023, 1024, 1025]
+
+
+def edge_batch(kind, seed, lens_q, lens_r, plant=True):
+    rng = np.random.default_rng(seed)
+    A = 4 if kind == "dna" else 20
+    qs, rs = [], []
+    for n in lens_q:
+        for m in lens_r:
+            q = rng.integers(0, A, n).astype(np.uint8)
+            r = rng.integers(0, A, m).astype(np.uint8)
+            if plant and n and m and rng.random() < 0.5:
+                k = min(n, m)
+                off = int(rng.integers(0, m - k + 1))
+                r[off:off + k] = q[:k]
+            qs.append(q)
+            rs.append(r)
+    if kind == "dna":
+        return wl.make_batch("edge-dna", qs, rs, wl.dna_matrix(), -6, -1)
+    s, _ = wl.load_blosum62()
+    return wl.make_batch("edge-protein", qs, rs, s.astype(np.int8), -11, -1)
+
+
+@pytest.mark.parametrize("step_cap", [1, 2000, 6000, 10 ** 9])
+def test_edge_lengths_all_group_widths(gpu_lib, ctx, step_cap):
+    """Lengths around every tile edge; step_cap 1 forces G = 32, 10^9 forces G = 1."""
+    b = edge_batch("dna", step_cap % 97, EDGE, EDGE[::3])
+    expect = oracle.align_workload(b)
+    got, _ = run_lib(gpu_lib, ctx, b, step_cap=step_cap)
+    assert_same(got, expect, f"edge dna cap={step_cap}")
+
+
+def test_edge_lengths_protein(gpu_lib, ctx):
+    b = edge_batch("protein", 5, EDGE[::2], EDGE[1::3])
+    expect = oracle.align_workload(b)
+    for cap in (1, 6000):
+        got, _ = run_lib(gpu_lib, ctx, b, step_cap=cap)
+        assert_same(got, expect, f"edge protein cap={cap}")
+    got, _ = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_PLAIN)
+    assert_same(got, expect, "edge protein plain")
+
+
+def test_long_sequences_and_maximum_length(gpu_lib, ctx):
+    """Long tail beyond the workloads, up to the documented maximum length."""
+    rng = np.random.default_rng(23)
+    qs, rs = [], []
+    for n, m in [(4000, 65535), (65535, 300), (3000, 3000), (1, 65535), (65535, 1)]:
+        q = rng.integers(0, 4, n).astype(np.uint8)
+        r = rng.integers(0, 4, m).astype(np.uint8)
+        k = min(n, m, 2000)
+        r[m - k:] = q[n - k:]
+        qs.append(q)
+        rs.append(r)
+    b = wl.make_batch("long", qs, rs, wl.dna_matrix(), -6, -1)
+    expect = oracle.align_workload(b)
+    got, _ = run_lib(gpu_lib, ctx, b)
+    assert_same(got, expect, "long batched")
+
+
+def test_wide_scores_use_plain_path(gpu_lib, ctx):
+    """Scores beyond the scaled int32 key range go to the general int32 kernel."""
+    rng = np.random.default_rng(29)
+    mat = np.full((4, 4), -90, np.int8)
+    np.fill_diagonal(mat, 120)
+    qs, rs = [], []
+    for n, m in [(300, 400), (1200, 1300), (50, 60), (2100, 2100)]:
+        q = rng.integers(0, 4, n).astype(np.uint8)
+        r = rng.integers(0, 4, m).astype(np.uint8)
+        r[:n // 2] = q[:n // 2]
+        qs.append(q)
+        rs.append(r)
+    b = wl.make_batch("wide", qs, rs, mat, -200, -30)
+    expect = oracle.align_workload(b)
+    got, info = run_lib(gpu_lib, ctx, b)
+    assert info["plain_pairs"] == 3  # 50 x 60 stays under the bound
+    assert_same(got, expect, "wide")
+    assert expect[:, 0].max() > 32766
+
+
+@pytest.mark.parametrize("go,ge", [(-1, -1), (0, 0), (-3, 0), (-16383, -1), (-20000, -5)])
+def test_gap_settings(gpu_lib, ctx, go, ge):
+    b = wl.gen_config(0, n_pairs=200)
+    b = wl.make_batch("gaps", [b.pair(i)[0] for i in range(b.n_pairs)],
+                      [b.pair(i)[1] for i in range(b.n_pairs)], b.matrix, go, ge)
+    expect = oracle.align_workload(b)
+    for mode in (gpu_lib.SW_MODE_BATCHED, gpu_lib.SW_MODE_PLAIN):
+        got, _ = run_lib(gpu_lib, ctx, b, mode=mode)
+        assert_same(got, expect, f"gaps {go},{ge} mode {mode}")
+
+
+def test_asymmetric_matrix_and_small_alphabet(gpu_lib, ctx):
+    rng = np.random.default_rng(31)
+    mat = rng.integers(-5, 6, size=(3, 3)).astype(np.int8)
+    mat[0, 0] = 5
+    qs = [rng.integers(0, 3, int(rng.integers(0, 200))).astype(np.uint8) for _ in range(300)]
+    rs = [rng.integers(0, 3, int(rng.integers(0, 400))).astype(np.uint8) for _ in range(300)]
+    b = wl.make_batch("asym", qs, rs, mat, -4, -2)
+    expect = oracle.align_workload(b)
+    got, _ = run_lib(gpu_lib, ctx, b)
+    assert_same(got, expect, "asym")
+
+
+def test_graph_replay_and_repeat(gpu_lib, ctx):
+    import torch
+    b = wl.gen_config(0, n_pairs=500)
+    expect = oracle.align_workload(b)
+    al = gpu_lib.Aligner(b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix, b.gap_open,
+                         b.gap_extend, flags=gpu_lib.SW_PLAN_GRAPH, ctx=ctx)
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        al.out.fill_(-9)
+        with torch.cuda.stream(s):
+            al.run(stream=s)
+        s.synchronize()
+        assert_same(al.results(), expect, "graph replay")
+    al.close()
+
+
+def test_one_shot_device_offsets(gpu_lib):
+    import torch
+    b = wl.gen_config(2, n_pairs=300)
+    expect = oracle.align_workload(b)
+    dev = torch.device("cuda", 0)
+    q = torch.from_numpy(b.q_seqs).to(dev)
+    r = torch.from_numpy(b.r_seqs).to(dev)
+    qo = torch.from_numpy(b.q_offsets).to(dev)
+    ro = torch.from_numpy(b.r_offsets).to(dev)
+    out = torch.full((5, b.n_pairs), -9, dtype=torch.int32, device=dev)
+    gpu_lib.sw_align_batch(q, qo, r, ro, b.matrix, b.gap_open, b.gap_extend, out)
+    torch.cuda.synchronize()
+    assert_same(out.T.cpu().numpy(), expect, "one-shot")
+
+
+def test_self_alignment_closed_form_at_scale(gpu_lib, ctx):
+    """S = 3L, ends (L-1, L-1), starts (0, 0) for DNA self-alignment."""
+    rng = np.random.default_rng(37)
+    lens = rng.integers(1, 3000, 400)
+    qs = [rng.integers(0, 4, L).astype(np.uint8) for L in lens]
+    b = wl.make_batch("self", qs, qs, wl.dna_matrix(), -6, -1)
+    got, _ = run_lib(gpu_lib, ctx, b)
+    L = lens.astype(np.int32)
+    expect = np.stack([3 * L, L - 1, L - 1, np.zeros_like(L), np.zeros_like(L)], axis=1)
+    assert_same(got, expect, "self")
+
+
+def test_invalid_arguments_rejected(gpu_lib, ctx):
+    b = wl.gen_config(0, n_pairs=4)
+    with pytest.raises(gpu_lib.SwError) as e:
+        gpu_lib.sw_plan_create(ctx, b.q_offsets, b.r_offsets, b.matrix, 0, -1)
+    assert e.value.code == gpu_lib.SW_EINVAL
+    bad = b.q_offsets.copy()
+    bad[2] = bad[1] - 1
+    with pytest.raises(gpu_lib.SwError) as e:
+        gpu_lib.sw_plan_create(ctx, bad, b.r_offsets, b.matrix, -6, -1)
+    assert e.value.code == gpu_lib.SW_ERANGE
+    big = np.array([0, 70000], np.int64)
+    with pytest.raises(gpu_lib.SwError) as e:
+        gpu_lib.sw_plan_create(ctx, big, np.array([0, 5], np.int64), b.matrix, -6, -1)
+    assert e.value.code == gpu_lib.SW_ERANGE
+
+
+def test_check_residues(gpu_lib):
+    import torch
+    dev = torch.device("cuda", 0)
+    s = torch.tensor([0, 1, 2, 3, 4, 7, 1, 0, 200], dtype=torch.uint8, device=dev)
+    bad = torch.zeros(1, dtype=torch.int64, device=dev)
+    gpu_lib.sw_check_residues(s, s.numel(), 4, bad)
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 3
