@@ -370,10 +370,13 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
         p->grid = (int)std::min<int64_t>((int64_t)bps * ctx->sm_count, want);
     }
     if (p->n_plain > 0) {
-        int T = ((std::min(plain_max_n, 1024) + 31) / 32) * 32;
-        if (T < 32) T = 32;
-        p->plain_threads = T;
-        p->plain_kmax = (plain_max_n + T - 1) / T > 1 ? 64 : 1;
+        if (plain_max_n <= 1024) {
+            p->plain_threads = std::max(32, ((plain_max_n + 31) / 32) * 32);
+            p->plain_kmax = 1;
+        } else {
+            p->plain_threads = kPlainWideThreads;
+            p->plain_kmax = kPlainMaxRows;
+        }
     }
     *out = p;
     return SW_OK;

@@ -66,13 +66,16 @@ __device__ uint64_t plain_sweep(const uint8_t *a, int a_step, int n, const uint8
     const int nthr = (n + k - 1) / k;
     const int row0 = t * k;
     const int rows = max(0, min(k, n - row0));
+    // KMAX == 1 keeps the row in registers; the many-rows variant keeps its
+    // rows in thread-local memory (long queries only).
     int Hl[KMAX], E[KMAX], qa[KMAX];
+    const int row_loop = KMAX == 1 ? 1 : rows;  // compile-time 1 keeps registers
 #pragma unroll
-    for (int r = 0; r < KMAX; ++r) {
+    for (int r = 0; r < row_loop; ++r) {
+        if (r >= rows) break;
         Hl[r] = 0;
         E[r] = kPlainNegInf;
-        qa[r] = 0;
-        if (r < rows) qa[r] = min((int)a[(ptrdiff_t)(row0 + r) * a_step], A - 1) * A;
+        qa[r] = min((int)a[(ptrdiff_t)(row0 + r) * a_step], A - 1) * A;
     }
     for (int idx = t; idx < 2 * T; idx += T) {
         xH[idx] = 0;
@@ -97,7 +100,7 @@ __device__ uint64_t plain_sweep(const uint8_t *a, int a_step, int n, const uint8
             int F = imax(upF + ge, upH + go);
             int h = 0;
 #pragma unroll
-            for (int r = 0; r < KMAX; ++r) {
+            for (int r = 0; r < row_loop; ++r) {
                 if (r >= rows) break;
                 if (r > 0) F = imax(F + ge, h + go);
                 const int hl = Hl[r];
@@ -126,7 +129,8 @@ __device__ uint64_t plain_sweep(const uint8_t *a, int a_step, int n, const uint8
 }
 
 template <int KMAX>
-__global__ void sw_plain_kernel(const __grid_constant__ PlainParams p) {
+__global__ void __launch_bounds__(KMAX == 1 ? 1024 : kPlainWideThreads)
+    sw_plain_kernel(const __grid_constant__ PlainParams p) {
     extern __shared__ __align__(16) int smem_plain[];
     const int A = p.alphabet;
     const int T = blockDim.x;
@@ -194,7 +198,7 @@ cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_
     if (rows_per_thread_max <= 1)
         sw_plain_kernel<1><<<p.n_pairs, threads, smem, s>>>(p);
     else
-        sw_plain_kernel<64><<<p.n_pairs, threads, smem, s>>>(p);
+        sw_plain_kernel<kPlainMaxRows><<<p.n_pairs, kPlainWideThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

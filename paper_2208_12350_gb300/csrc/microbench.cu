@@ -1,8 +1,8 @@
 // Integer issue-rate microbenchmark: the denominator of the alignment
-// kernels' roofline.  Each thread runs 8 independent dependency chains of
-// one instruction kind; the kernel reports instructions per second for the
-// whole device.  Operands come from kernel arguments and the results are
-// stored, so nothing is folded away.
+// kernels' roofline.  Each thread runs 16 instructions of one kind per
+// iteration step with 8-way instruction-level parallelism; the kernel
+// reports instructions per second for the whole device.  The results are
+// stored, so nothing is dropped.
 #include "sw_internal.h"
 #include "swgb.h"
 
@@ -20,24 +20,27 @@ __device__ __forceinline__ int step(int a, int b, int c) {
     return a;
 }
 
+// Two banks of 8 values feed each other: every instruction reads three
+// different values produced by the other bank, so no chain can be folded
+// and every bank offers 8 independent instructions.
 template <int OP>
 __global__ void int_rate_kernel(int64_t iters, int b, int c, int *sink) {
-    int x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
-    int x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    int x[8], y[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (int)threadIdx.x * (k + 1) + b * k + c;
     for (int64_t i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            x0 = step<OP>(x0, b, c);
-            x1 = step<OP>(x1, b, c);
-            x2 = step<OP>(x2, b, c);
-            x3 = step<OP>(x3, b, c);
-            x4 = step<OP>(x4, b, c);
-            x5 = step<OP>(x5, b, c);
-            x6 = step<OP>(x6, b, c);
-            x7 = step<OP>(x7, b, c);
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) y[k] = step<OP>(x[k], x[(k + 1) & 7], x[(k + 3) & 7]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = step<OP>(y[k], y[(k + 2) & 7], y[(k + 5) & 7]);
         }
     }
-    sink[blockIdx.x * blockDim.x + threadIdx.x] = x0 ^ x1 ^ x2 ^ x3 ^ x4 ^ x5 ^ x6 ^ x7;
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc ^= x[k];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
 template <int OP>

@@ -19,6 +19,8 @@ constexpr int kMaxScaledGap = 16383;
 constexpr int kMaxAlphabet = 32;
 constexpr int kRows = 16;                      // query rows per lane (group kernel)
 constexpr int kGroupWarps = 4;                 // warps per block (group kernel)
+constexpr int kPlainWideThreads = 256;         // plain kernel block for queries > 1024
+constexpr int kPlainMaxRows = 256;             // rows per thread there (n <= 65536)
 
 // One pair as the device sees it (plan order).
 struct PairInfo {
