@@ -309,7 +309,7 @@ def run_ours(args, rank, world, local):
                 "config": {"workload": batch.name, "pairs": batch.n_pairs,
                            "forward_cells": cells, "mode": "batched persistent + CUDA graph",
                            "l2": "flushed between steps (512 MB write)", "sms": sms,
-                           "group_tasks": info["group_tasks"]},
+                           "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

@@ -145,10 +145,11 @@ int sw_plan_execute(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_seqs,
 int sw_plan_execute_host(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_seqs,
                          int32_t *out_host, void *stream);
 
-/* Pairs, passes and kernel launches of a plan (any pointer may be NULL):
- * n_group_tasks warp tasks in the persistent kernel, n_plain pairs in the
- * one-block-per-pair kernel, launches = kernels one execution enqueues. */
-int sw_plan_info(const sw_plan *plan, int32_t *n_group_tasks, int32_t *n_plain,
+/* Shape of a plan (any pointer may be NULL): n_group_pairs pairs on the
+ * persistent kernel, n_plain pairs on the one-block-per-pair kernel,
+ * launches = kernels one execution enqueues, scratch_bytes = device scratch
+ * for strip boundaries. */
+int sw_plan_info(const sw_plan *plan, int32_t *n_group_pairs, int32_t *n_plain,
                  int32_t *launches, int64_t *scratch_bytes);
 
 int sw_plan_destroy(sw_plan *plan);

@@ -176,7 +176,7 @@ def sw_plan_info(plan: int) -> dict:
     sb = _I64()
     _check(load().sw_plan_info(plan, ctypes.byref(t), ctypes.byref(p), ctypes.byref(l),
                                ctypes.byref(sb)), "sw_plan_info")
-    return {"group_tasks": t.value, "plain_pairs": p.value, "launches": l.value,
+    return {"group_pairs": t.value, "plain_pairs": p.value, "launches": l.value,
             "scratch_bytes": sb.value}
 
 

@@ -34,8 +34,10 @@ def nvcc() -> str:
 
 
 def _flags(extra: list[str] | None = None) -> list[str]:
+    # SWGB_NVCC_DEFINES: tuning overrides, e.g. "SWGB_GROUP_MIN_BLOCKS=3"
+    defs = [f"-D{d}" for d in os.environ.get("SWGB_NVCC_DEFINES", "").split() if d]
     return ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
-            "-I", INCLUDE, "-I", CSRC, *(extra or [])]
+            "-I", INCLUDE, "-I", CSRC, *defs, *(extra or [])]
 
 
 def _needs_rebuild(out: str, deps: list[str]) -> bool:

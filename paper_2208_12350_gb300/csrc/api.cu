@@ -84,8 +84,9 @@ struct sw_plan {
     ProfileKind kind = ProfileKind::kInt32;
     // persistent group kernel
     PairInfo *d_pairs = nullptr;
-    GroupTask *d_tasks = nullptr;
-    int32_t n_tasks = 0;
+    ClassInfo *d_classes = nullptr;
+    int32_t n_classes = 0;
+    int32_t n_group = 0;  // pairs on the persistent kernel
     int32_t *d_counter = nullptr;
     uint32_t *d_scratch = nullptr;
     int64_t scratch_words = 0;
@@ -109,7 +110,7 @@ static void plan_free(sw_plan *p) {
     DeviceGuard g(p->ctx->device);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     cudaFree(p->d_pairs);
-    cudaFree(p->d_tasks);
+    cudaFree(p->d_classes);
     cudaFree(p->d_counter);
     cudaFree(p->d_scratch);
     cudaFree(p->d_plain);
@@ -298,75 +299,58 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
         }
         items.push_back({i, n[i], m[i], log2g, passes});
     }
-    // group pairs of equal (G, passes) into warp tasks, longest sweeps first
+    // one queue per lane-group width, widest (longest sweeps) first; inside a
+    // queue, pairs by serial cost, largest first
     std::sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
         if (x.log2g != y.log2g) return x.log2g > y.log2g;
-        if (x.passes != y.passes) return x.passes > y.passes;
-        if (x.m != y.m) return x.m > y.m;
+        const int64_t cx = (int64_t)std::max(x.passes, 1) * (x.m + (1 << x.log2g) - 1);
+        const int64_t cy = (int64_t)std::max(y.passes, 1) * (y.m + (1 << y.log2g) - 1);
+        if (cx != cy) return cx > cy;
         return x.id < y.id;
     });
-    struct TaskTmp {
-        int64_t cost;
-        int32_t begin, count, log2g;
-    };
-    std::vector<TaskTmp> tt;
-    for (size_t k = 0; k < items.size();) {
-        const int lg = items[k].log2g, ps = items[k].passes;
-        const int cap = 32 >> lg;
-        size_t e = k;
-        while (e < items.size() && (int)(e - k) < cap && items[e].log2g == lg &&
-               items[e].passes == ps)
-            ++e;
-        const int64_t cost = (int64_t)std::max(ps, 1) * (items[k].m + (1 << lg) - 1);
-        tt.push_back({cost, (int32_t)k, (int32_t)(e - k), lg});
-        k = e;
-    }
-    std::stable_sort(tt.begin(), tt.end(),
-                     [](const TaskTmp &a, const TaskTmp &b) { return a.cost > b.cost; });
     std::vector<PairInfo> pairs;
-    std::vector<GroupTask> tasks;
+    std::vector<ClassInfo> classes;
     pairs.reserve(items.size());
-    tasks.reserve(tt.size());
     int64_t scratch = 0;
-    for (const TaskTmp &t : tt) {
-        GroupTask gt{(int32_t)pairs.size(), t.count, t.log2g, 0};
-        tasks.push_back(gt);
-        for (int32_t u = 0; u < t.count; ++u) {
-            const Item &it = items[t.begin + u];
-            PairInfo pi{q_offsets[it.id], r_offsets[it.id], -1, it.n, it.m, it.id, 0};
-            if (it.passes >= 2) {
-                pi.scratch = scratch;
-                scratch += 2 * (int64_t)it.m;
-            }
-            pairs.push_back(pi);
+    for (size_t k = 0; k < items.size(); ++k) {
+        const Item &it = items[k];
+        if (classes.empty() || classes.back().log2g != it.log2g)
+            classes.push_back({(int32_t)k, 0, it.log2g, 0});
+        classes.back().count++;
+        PairInfo pi{q_offsets[it.id], r_offsets[it.id], -1, it.n, it.m, it.id, 0};
+        if (it.passes >= 2) {
+            pi.scratch = scratch;
+            scratch += 2 * (int64_t)it.m;
         }
+        pairs.push_back(pi);
     }
     p->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
     p->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
-    p->n_tasks = (int32_t)tasks.size();
+    p->n_classes = (int32_t)classes.size();
+    p->n_group = (int32_t)pairs.size();
     p->n_plain = (int32_t)plain.size();
     p->scratch_words = scratch;
     int rc;
-    if ((rc = upload(&p->d_pairs, pairs)) || (rc = upload(&p->d_tasks, tasks)) ||
+    if ((rc = upload(&p->d_pairs, pairs)) || (rc = upload(&p->d_classes, classes)) ||
         (rc = upload(&p->d_plain, plain))) {
         plan_free(p);
         return rc;
     }
-    if (cudaMalloc(&p->d_counter, sizeof(int32_t)) != cudaSuccess ||
+    if (cudaMalloc(&p->d_counter, kMaxClasses * sizeof(int32_t)) != cudaSuccess ||
         (scratch > 0 && cudaMalloc(&p->d_scratch, scratch * sizeof(uint32_t)) != cudaSuccess)) {
         cudaGetLastError();
         plan_free(p);
         return fail(SW_ENOMEM, "sw_plan_create: scratch allocation (%lld words) failed",
                     (long long)scratch);
     }
-    if (p->n_tasks > 0) {
+    if (p->n_group > 0) {
         int smem = 0;
         const int bps = group_blocks_per_sm(p->kind, A, &smem);
         if (bps <= 0) {
             plan_free(p);
             return fail(SW_ECUDA, "sw_plan_create: group kernel does not fit (%d B smem)", smem);
         }
-        const int64_t want = ((int64_t)p->n_tasks + kGroupWarps - 1) / kGroupWarps;
+        const int64_t want = ((int64_t)p->n_group + kGroupWarps - 1) / kGroupWarps;
         p->grid = (int)std::min<int64_t>((int64_t)bps * ctx->sm_count, want);
     }
     if (p->n_plain > 0) {
@@ -384,16 +368,16 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
 
 static int enqueue(sw_plan *p, const uint8_t *q, const uint8_t *r, const Outputs &o,
                    cudaStream_t s) {
-    if (p->n_tasks > 0) {
-        SW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, sizeof(int32_t), s));
+    if (p->n_group > 0) {
+        SW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, kMaxClasses * sizeof(int32_t), s));
         GroupParams gp;
         std::memset(&gp, 0, sizeof gp);
         gp.q = q;
         gp.r = r;
         gp.pairs = p->d_pairs;
-        gp.tasks = p->d_tasks;
-        gp.n_tasks = p->n_tasks;
-        gp.counter = p->d_counter;
+        gp.classes = p->d_classes;
+        gp.n_classes = p->n_classes;
+        gp.counters = p->d_counter;
         gp.scratch = p->d_scratch;
         gp.status = p->ctx->d_status;
         gp.out = o;
@@ -499,12 +483,12 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
     return SW_OK;
 }
 
-int sw_plan_info(const sw_plan *p, int32_t *n_group_tasks, int32_t *n_plain, int32_t *launches,
+int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int32_t *launches,
                  int64_t *scratch_bytes) {
     if (!p) return fail(SW_EINVAL, "sw_plan_info: plan is NULL");
-    if (n_group_tasks) *n_group_tasks = p->n_tasks;
+    if (n_group_pairs) *n_group_pairs = p->n_group;
     if (n_plain) *n_plain = p->n_plain;
-    if (launches) *launches = (p->n_tasks > 0 ? 1 : 0) + (p->n_plain > 0 ? 1 : 0);
+    if (launches) *launches = (p->n_group > 0 ? 1 : 0) + (p->n_plain > 0 ? 1 : 0);
     if (scratch_bytes) *scratch_bytes = p->scratch_words * (int64_t)sizeof(uint32_t);
     return SW_OK;
 }

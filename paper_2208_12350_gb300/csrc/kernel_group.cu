@@ -1,19 +1,34 @@
 // Persistent, length-bucketed batched kernel: the hot path.
 //
-// Work split.  A warp takes a task of up to 32/G pairs from a device queue
-// (the plan orders tasks longest first); each pair gets a group of G lanes
-// (G = 1..32).  Lane t of a group holds query rows [t*R, t*R + R) of the
-// current row strip in registers and walks the reference columns, lane t
-// working on column j = step - t: the anti-diagonal wavefront of ADEPT
-// (Section II-B.2, Fig. 3) with R rows per lane instead of one.  The values
-// a lane needs from the strip above (H and F of the row above, at this and
-// the previous column) arrive by one register shuffle per value per step
-// from lane t-1, executed by every lane alike, so the exchange never
-// diverges (the lesson of GEVO's edits 5, 6, 8 and 10, Section VI-A).  Lane
-// 0 of a group takes them from the strip boundary instead: zero/-infinity
-// above the first strip (Section II-B.1's boundary row), and for later
-// strips the last row of the previous strip, which lane G-1 wrote to global
-// scratch.  Queries longer than G*R rows take several strips ("passes").
+// Work split.  The plan sorts pairs into classes by lane-group width G (32,
+// 16, ..., 1; longest sweeps first) and, inside a class, by cost.  A warp
+// takes one class at a time and splits into 32/G groups of G lanes.  Each
+// group independently pulls a pair from its class queue, runs the forward
+// sweep, then the reverse sweep of the same pair, then pulls the next pair,
+// so groups never wait for one another's pairs.
+//
+// Sweep.  Lane t of a group holds query rows [t*R, t*R + R) of the current
+// row strip in registers and walks the reference columns, lane t on column
+// j = step - t: the anti-diagonal wavefront of ADEPT (Section II-B.2,
+// Fig. 3) with R rows per lane.  The H and F values of the row above arrive
+// by one register shuffle per value per step from lane t-1, executed by
+// every lane alike, so the exchange never diverges (the lesson of GEVO's
+// edits 5, 6, 8 and 10, Section VI-A).  Lane 0 takes them from the strip
+// boundary instead: H = 0 / F = -infinity above the first strip (Section
+// II-B.1's boundary row), and for later strips the last row of the previous
+// strip, which lane G-1 wrote to global scratch.  Queries longer than G*R
+// rows take several strips ("passes").  Residue codes and boundary words
+// are loaded U steps before use.
+//
+// Every lane runs the same instruction stream on every step: columns outside
+// a lane's range, idle groups and rows past the end of the query are
+// computed with a pad residue whose scores are very negative, instead of
+// being branched around.  Such cells never beat a real cell: their values
+// come from real cells at an earlier column (or the same column and a
+// smaller row) through non-positive steps, and ties go to the smaller
+// column, then the smaller row.  Before a lane's first column the pad
+// column leaves H = 0 and E = go, which gives the same first real column as
+// the E = -infinity boundary.
 //
 // Recurrence (Section II-B.1, Fig. 8), per cell, six max-plus instructions:
 //   E  = viaddmax(E, ge, Hg_left)          E = max(E + ge, H_left + go)
@@ -31,30 +46,17 @@
 // keeps every scaled value and key inside int32.
 //
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
-// a_qend..a_0 and b_rend..b_0, run by the same group right after the
-// forward pass.  It stops as soon as the column holding the first cell of
-// score S has been completed by every lane.
-//
-// Rows past the end of the query use a pad score (<= 0 after the shift back
-// by go): such cells never beat a real cell, since their values come from
-// real cells at an earlier column or the same column and a smaller row.
-// Columns outside [0, m) are skipped by the lanes they fall on.
+// a_qend..a_0 and b_rend..b_0.  Every 2U steps the group looks for a cell of
+// score S; once found, it only finishes the columns up to that one.
 #include "sw_internal.h"
 
 namespace swgb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kU = 4;  // steps per block; loads run one block ahead
 
-struct LaneJob {
-    const uint8_t *a;  // row residues: a[i * a_step]
-    const uint8_t *b;  // column residues: b[j * b_step]
-    uint32_t *bnd;     // 2*m boundary words (used when n > G*R)
-    int a_step, b_step;
-    int n, m;
-};
-
-// Sign-extended int8 byte `sel` of `w`, moved to bits 16..31 (value << 16).
+// Sign-extended int8 byte B of w, moved to bits 16..31 (value << 16).
 template <int B>
 __device__ __forceinline__ int byte_hi(uint32_t w) {
     constexpr uint32_t sel = 0x44u | (uint32_t(B) << 8) | (uint32_t(B | 8) << 12);
@@ -63,22 +65,27 @@ __device__ __forceinline__ int byte_hi(uint32_t w) {
     return (int)d;
 }
 
+// Profile of one lane: for residue c in [0, A] (A = pad) and the lane's R
+// rows, (s(q_row, c) - go) << 16, or a pad score for rows past the query.
+// Layout [c][chunk][lane] of 16-byte chunks: conflict-free 128-bit loads
+// whatever residue each lane asks for.
 template <int R, bool P8>
-__device__ __forceinline__ void build_profile(char *prof, int lane, const LaneJob &job, int row0,
-                                              int nrows, const int8_t *smat, int A, int go) {
+__device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_t *a, int dir,
+                                              int row0, int nrows, const int8_t *smat, int A,
+                                              int go) {
     int qa[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + r;
-        qa[r] = i < nrows ? min((int)job.a[(ptrdiff_t)i * job.a_step], A - 1) * A : -1;
+        qa[r] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * A : -1;
     }
-    for (int c = 0; c < A; ++c) {
+    for (int c = 0; c <= A; ++c) {
         if constexpr (P8) {
             static_assert(R == 16, "int8 profile holds 16 rows per lane");
             uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int v = qa[r] >= 0 ? (int)smat[qa[r] + c] - go : -128;
+                const int v = (qa[r] >= 0 && c < A) ? (int)smat[qa[r] + c] - go : -128;
                 w[r >> 2] |= (uint32_t)(uint8_t)(int8_t)v << (8 * (r & 3));
             }
             *reinterpret_cast<uint4 *>(prof + ((size_t)c * 32 + lane) * 16) =
@@ -90,7 +97,8 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const LaneJo
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int r = 4 * k + u;
-                    v[u] = qa[r] >= 0 ? ((int)smat[qa[r] + c] - go) * 65536 : kScaledPad;
+                    v[u] = (qa[r] >= 0 && c < A) ? ((int)smat[qa[r] + c] - go) * 65536
+                                                 : kScaledPad;
                 }
                 *reinterpret_cast<int4 *>(prof + (((size_t)c * (R / 4) + k) * 32 + lane) * 16) =
                     make_int4(v[0], v[1], v[2], v[3]);
@@ -124,62 +132,177 @@ __device__ __forceinline__ void load_scores(const char *prof, int c, int lane, i
     }
 }
 
-// One local-alignment sweep (all row strips) of each group's job.  Every
-// lane of the warp must call it.  On return every lane of a group holds the
-// group's best key (H << 16 | 65535 - j) and the row of that cell.  With
-// REV, the sweep stops once a cell of score `target` has been found and its
-// column completed.
-template <int R, bool P8, bool REV>
-__device__ void sweep(const LaneJob &job, int G, int gl, int lane, char *prof,
-                      const int8_t *smat, int A, int go, int ge, int target,
-                      uint32_t &out_key, int &out_row) {
+// Sweep state of one group (every lane of the group holds the same values).
+struct Sweep {
+    const uint8_t *a;  // row residues at a[i * dir]
+    const uint8_t *b;  // column residues at b[j * dir]
+    uint32_t *bnd;     // 2*m strip-boundary words when passes > 1
+    int dir;           // +1 forward, -1 reverse
+    int n, m;
+    int passes, ps;    // strips and current strip
+    int s, lim;        // step within the strip and steps it needs
+    int stop;          // columns still needed (the reverse pass shrinks it)
+    int target;        // reverse pass: the forward score to find
+};
+
+}  // namespace
+
+template <int R, bool P8>
+__global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
+    sw_group_kernel(const __grid_constant__ GroupParams p) {
+    extern __shared__ __align__(16) char smem_group[];
+    const int A = p.alphabet;
+    const int go = p.gap_open, ge = p.gap_extend;
     const int goS = go * 65536, geS = ge * 65536;
-    const int rpp = G * R;
-    const int passes = (job.n > 0 && job.m > 0) ? (job.n + rpp - 1) / rpp : 0;
-    const int max_passes = (int)__reduce_max_sync(kFull, (unsigned)passes);
-    int stop = job.m;
-    uint32_t best_key = 0;
-    int best_row = 0x7fffffff;
-    for (int ps = 0; ps < max_passes; ++ps) {
-        const bool live = ps < passes;
-        const int row0 = ps * rpp + gl * R;
-        build_profile<R, P8>(prof, lane, job, row0, live ? job.n : 0, smat, A, go);
-        __syncwarp();
+    int8_t *smat = reinterpret_cast<int8_t *>(smem_group);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * 16 : (size_t)(A + 1) * (R / 4) * 32 * 16;
+    char *prof = smem_group + kMaxAlphabet * kMaxAlphabet + warp * prof_bytes;
+    for (int i = threadIdx.x; i < A * A; i += blockDim.x) smat[i] = p.mat[i];
+    __syncthreads();
+
+    for (int cls = 0; cls < p.n_classes; ++cls) {
+        const ClassInfo ci = p.classes[cls];
+        const int log2g = ci.log2g;
+        const int G = 1 << log2g;
+        const int gl = lane & (G - 1);
+        const int gbase = lane & ~(G - 1);
+        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
+
+        Sweep sw;
+        sw.a = p.q;
+        sw.b = p.r;
+        sw.bnd = p.scratch;
+        sw.dir = 1;
+        sw.n = sw.m = 0;
+        sw.passes = sw.ps = 0;
+        sw.s = sw.lim = 0;
+        sw.stop = 0;
+        sw.target = 0;
+        int id = -1;           // output slot of the group's pair, -1 when idle
+        bool rev = false;
+        bool drained = false;  // the class queue had nothing left for this group
+        int S = 0, qend = 0, rend = 0;
+        uint32_t best_key = 0;
+        int best_row = 0x7fffffff;
+        bool reload = true;    // block data must be loaded before use
+
         int Hg[R], E[R];
         uint32_t K[R];
+        int diag0 = goS, outHg = goS, outF = kScaledNegInf;
+        int cur_c[kU], nxt_c[kU];
+        uint32_t cur_b[kU], nxt_b[kU];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             Hg[r] = goS;
             E[r] = kScaledNegInf;
             K[r] = 0u;
         }
-        int diag0 = goS, outHg = goS, outF = kScaledNegInf;
-        int mcols = live ? stop : 0;
-        const uint32_t *bin = job.bnd + ((ps + 1) & 1) * job.m;
-        uint32_t *bout = job.bnd + (ps & 1) * job.m;
-        const bool write_bnd = live && (ps + 1 < passes) && gl == G - 1;
-        const bool read_bnd = live && ps > 0 && gl == 0;
-        const int lim = mcols > 0 ? mcols + G - 1 : 0;
-        const int max_steps = (int)__reduce_max_sync(kFull, (unsigned)lim);
-        for (int s = 0; s < max_steps; ++s) {
-            int inHg = __shfl_up_sync(kFull, outHg, 1, G);
-            int inF = __shfl_up_sync(kFull, outF, 1, G);
-            const int j = s - gl;
-            const bool act = j >= 0 && j < mcols;
-            if (gl == 0) {
-                inHg = goS;
-                inF = kScaledNegInf;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            cur_c[u] = nxt_c[u] = A;
+            cur_b[u] = nxt_b[u] = 0u;
+        }
+
+        // Starts strip sw.ps: profile of this lane's rows, fresh DP state.
+        auto begin_strip = [&]() {
+            const int row0 = sw.ps * G * R + gl * R;
+            build_profile<R, P8>(prof, lane, sw.a, sw.dir, row0, sw.n, smat, A, go);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Hg[r] = goS;
+                E[r] = kScaledNegInf;
+                K[r] = 0u;
             }
-            if (read_bnd && act) {
-                const uint32_t v = bin[j];
-                inHg = (int)(v << 16);
-                inF = (int)(v & 0xFFFF0000u);
+            diag0 = goS;
+            outHg = goS;
+            outF = kScaledNegInf;
+            sw.s = 0;
+            sw.lim = sw.stop + G - 1;
+            reload = true;
+        };
+        // Starts a sweep over (a, n) x (b, m) in direction dir.
+        auto begin_sweep = [&](const uint8_t *a, const uint8_t *b, int n, int m, int dir) {
+            sw.a = a;
+            sw.b = b;
+            sw.dir = dir;
+            sw.n = n;
+            sw.m = m;
+            sw.passes = (n > 0 && m > 0) ? (n + G * R - 1) / (G * R) : 0;
+            sw.ps = 0;
+            sw.stop = m;
+            best_key = 0u;
+            best_row = 0x7fffffff;
+            if (sw.passes > 0) {
+                begin_strip();
+            } else {
+                sw.s = 0;
+                sw.lim = 0;
             }
-            if (act) {
-                const int c = min((int)job.b[(ptrdiff_t)j * job.b_step], A - 1);
+        };
+
+        for (;;) {
+            // ---- idle groups take the next pair of the class
+            if (id < 0 && !drained) {
+                int idx = 0;
+                if (gl == 0) idx = atomicAdd(p.counters + cls, 1);
+                idx = __shfl_sync(gmask, idx, gbase);
+                if (idx >= ci.count) {
+                    drained = true;
+                } else {
+                    const PairInfo pi = p.pairs[ci.first + idx];
+                    id = pi.id;
+                    rev = false;
+                    sw.bnd = pi.scratch >= 0 ? p.scratch + pi.scratch : p.scratch;
+                    begin_sweep(p.q + pi.q, p.r + pi.r, pi.n, pi.m, 1);
+                }
+            }
+            if (__all_sync(kFull, id < 0)) break;  // every group drained and idle
+
+            const bool live = id >= 0;
+            const int mcols = live && sw.ps < sw.passes ? sw.stop : 0;
+            const bool has_in = sw.ps > 0;
+            const bool has_out = sw.ps + 1 < sw.passes;
+            const uint32_t *bin = sw.bnd + ((sw.ps + 1) & 1) * sw.m;
+            uint32_t *bout = sw.bnd + (sw.ps & 1) * sw.m;
+            const uint8_t *bcol = sw.b;
+            const int dir = sw.dir;
+
+            // ---- residue codes and boundary words: this block (if stale), next block
+            if (reload) {
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int j = sw.s + u - gl;
+                    const bool in = (unsigned)j < (unsigned)mcols;
+                    cur_c[u] = in ? min((int)bcol[(ptrdiff_t)j * dir], A - 1) : A;
+                    cur_b[u] = (in && gl == 0 && has_in) ? bin[j] : 0u;
+                }
+                reload = false;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int j = sw.s + kU + u - gl;
+                const bool in = (unsigned)j < (unsigned)mcols;
+                nxt_c[u] = in ? min((int)bcol[(ptrdiff_t)j * dir], A - 1) : A;
+                nxt_b[u] = (in && gl == 0 && has_in) ? bin[j] : 0u;
+            }
+
+            // ---- U wavefront steps, the same instructions on every lane
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int j = sw.s + u - gl;
+                const bool in = (unsigned)j < (unsigned)mcols;
+                int inHg = __shfl_up_sync(kFull, outHg, 1, G);
+                int inF = __shfl_up_sync(kFull, outF, 1, G);
+                if (gl == 0) {
+                    const bool from_bnd = in && has_in;
+                    inHg = from_bnd ? (int)(cur_b[u] << 16) : goS;
+                    inF = from_bnd ? (int)(cur_b[u] & 0xFFFF0000u) : kScaledNegInf;
+                }
+                const int c = in ? cur_c[u] : A;
                 int sc[R];
                 load_scores<R, P8>(prof, c, lane, sc);
-                const int cj = 65535 - j;
+                const int cj = 65535 - max(j, 0);
                 int diag = diag0;
                 int F = __viaddmax_s32(inF, geS, inHg);
 #pragma unroll
@@ -194,128 +317,102 @@ __device__ void sweep(const LaneJob &job, int G, int gl, int lane, char *prof,
                 }
                 outHg = Hg[R - 1];
                 outF = F;
-                if (write_bnd) bout[j] = ((uint32_t)outHg >> 16) | ((uint32_t)outF & 0xFFFF0000u);
+                if (in && has_out && gl == G - 1)
+                    bout[j] = ((uint32_t)outHg >> 16) | ((uint32_t)outF & 0xFFFF0000u);
                 diag0 = inHg;
             }
-            if constexpr (REV) {
-                if ((s & 7) == 7) {
-                    uint32_t lk = K[0];
 #pragma unroll
-                    for (int r = 1; r < R; ++r) lk = max(lk, K[r]);
-                    int found = live && (int)(lk >> 16) >= target ? 65535 - (int)(lk & 0xFFFFu)
-                                                                  : 0x7fffffff;
-                    for (int off = 1; off < G; off <<= 1)
-                        found = min(found, __shfl_xor_sync(kFull, found, off, G));
-                    if (found != 0x7fffffff && found + 1 < stop) stop = found + 1;
-                    mcols = live ? stop : 0;
-                    const bool done = s + 1 >= (mcols > 0 ? mcols + G - 1 : 0);
-                    if (__all_sync(kFull, done)) break;
+            for (int u = 0; u < kU; ++u) {
+                cur_c[u] = nxt_c[u];
+                cur_b[u] = nxt_b[u];
+            }
+            sw.s += kU;
+
+            // ---- reverse sweep: stop once a cell of the forward score has appeared
+            if (rev && live && ((sw.s & (2 * kU - 1)) == 0)) {
+                uint32_t lk = K[0];
+#pragma unroll
+                for (int r = 1; r < R; ++r) lk = max(lk, K[r]);
+                int found = (int)(lk >> 16) >= sw.target ? 65535 - (int)(lk & 0xFFFFu) : 0x7fffffff;
+                for (int off = 1; off < G; off <<= 1)
+                    found = min(found, __shfl_xor_sync(gmask, found, off, G));
+                if (found != 0x7fffffff && found + 1 < sw.stop) {
+                    sw.stop = found + 1;
+                    sw.lim = sw.stop + G - 1;
+                }
+            }
+
+            // ---- end of a strip / sweep
+            if (live && sw.s >= sw.lim) {
+                if (sw.ps < sw.passes) {
+                    const int row0 = sw.ps * G * R + gl * R;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (K[r] > best_key) {
+                            best_key = K[r];
+                            best_row = row0 + r;
+                        }
+                }
+                if (sw.ps + 1 < sw.passes) {
+                    __syncwarp(gmask);  // boundary words written by lane G-1 -> lane 0
+                    ++sw.ps;
+                    begin_strip();
+                } else {
+                    for (int off = 1; off < G; off <<= 1) {
+                        const uint32_t ok = __shfl_xor_sync(gmask, best_key, off, G);
+                        const int orow = __shfl_xor_sync(gmask, best_row, off, G);
+                        if (ok > best_key || (ok == best_key && orow < best_row)) {
+                            best_key = ok;
+                            best_row = orow;
+                        }
+                    }
+                    bool done = true;
+                    if (!rev) {
+                        S = (int)(best_key >> 16);
+                        qend = best_row;
+                        rend = 65535 - (int)(best_key & 0xFFFFu);
+                        if (S > 0) {
+                            rev = true;
+                            done = false;
+                            __syncwarp(gmask);
+                            begin_sweep(sw.a + qend, sw.b + rend, qend + 1, rend + 1, -1);
+                            sw.target = S;
+                        }
+                    }
+                    if (done) {
+                        if (gl == 0) {
+                            int o0 = 0, o1 = -1, o2 = -1, o3 = -1, o4 = -1;
+                            if (S > 0) {
+                                const int S2 = (int)(best_key >> 16);
+                                const int l = 65535 - (int)(best_key & 0xFFFFu);
+                                if (S2 != S) atomicOr(p.status, kStatusReverseMismatch);
+                                o0 = S;
+                                o1 = qend;
+                                o2 = rend;
+                                o3 = qend - best_row;
+                                o4 = rend - l;
+                            }
+                            p.out.score[id] = o0;
+                            p.out.qend[id] = o1;
+                            p.out.rend[id] = o2;
+                            p.out.qstart[id] = o3;
+                            p.out.rstart[id] = o4;
+                        }
+                        id = -1;
+                        S = 0;
+                        rev = false;
+                        __syncwarp(gmask);
+                    }
                 }
             }
         }
-        if (live) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (K[r] > best_key) {
-                    best_key = K[r];
-                    best_row = row0 + r;
-                }
-        }
-        __syncwarp();  // boundary words and the profile are reused next pass
-    }
-    for (int off = 1; off < G; off <<= 1) {
-        const uint32_t ok = __shfl_xor_sync(kFull, best_key, off, G);
-        const int orow = __shfl_xor_sync(kFull, best_row, off, G);
-        if (ok > best_key || (ok == best_key && orow < best_row)) {
-            best_key = ok;
-            best_row = orow;
-        }
-    }
-    out_key = best_key;
-    out_row = best_row;
-}
-
-template <bool P8>
-__host__ __device__ constexpr size_t profile_bytes_per_warp(int A) {
-    return P8 ? (size_t)A * 32 * 16 : (size_t)A * (kRows / 4) * 32 * 16;
-}
-
-template <int R, bool P8>
-__global__ void __launch_bounds__(kGroupWarps * 32)
-    sw_group_kernel(const __grid_constant__ GroupParams p) {
-    extern __shared__ __align__(16) char smem_group[];
-    const int A = p.alphabet;
-    int8_t *smat = reinterpret_cast<int8_t *>(smem_group);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    char *prof = smem_group + kMaxAlphabet * kMaxAlphabet + warp * profile_bytes_per_warp<P8>(A);
-    for (int i = threadIdx.x; i < A * A; i += blockDim.x) smat[i] = p.mat[i];
-    __syncthreads();
-
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(p.counter, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= p.n_tasks) break;
-        const GroupTask task = p.tasks[t];
-        const int log2g = task.log2g;
-        const int G = 1 << log2g;
-        const int gid = lane >> log2g, gl = lane & (G - 1);
-        const bool gv = gid < task.count;
-        PairInfo pi = {0, 0, -1, 0, 0, 0, 0};
-        if (gv) pi = p.pairs[task.first + gid];
-        LaneJob fwd;
-        fwd.a = p.q + pi.q;
-        fwd.b = p.r + pi.r;
-        fwd.bnd = pi.scratch >= 0 ? p.scratch + pi.scratch : nullptr;
-        fwd.a_step = 1;
-        fwd.b_step = 1;
-        fwd.n = pi.n;
-        fwd.m = pi.m;
-        uint32_t key;
-        int row;
-        sweep<R, P8, false>(fwd, G, gl, lane, prof, smat, A, p.gap_open, p.gap_extend, 0, key,
-                            row);
-        const int S = (int)(key >> 16);
-        const int qend = row;
-        const int rend = 65535 - (int)(key & 0xFFFFu);
-        const bool need_rev = gv && S > 0;
-        LaneJob rev = fwd;
-        rev.a = need_rev ? fwd.a + qend : fwd.a;
-        rev.b = need_rev ? fwd.b + rend : fwd.b;
-        rev.a_step = -1;
-        rev.b_step = -1;
-        rev.n = need_rev ? qend + 1 : 0;
-        rev.m = need_rev ? rend + 1 : 0;
-        uint32_t key2;
-        int row2;
-        sweep<R, P8, true>(rev, G, gl, lane, prof, smat, A, p.gap_open, p.gap_extend, S, key2,
-                           row2);
-        if (gv && gl == 0) {
-            int o0 = 0, o1 = -1, o2 = -1, o3 = -1, o4 = -1;
-            if (S > 0) {
-                const int S2 = (int)(key2 >> 16);
-                const int l = 65535 - (int)(key2 & 0xFFFFu);
-                if (S2 != S) atomicOr(p.status, kStatusReverseMismatch);
-                o0 = S;
-                o1 = qend;
-                o2 = rend;
-                o3 = qend - row2;
-                o4 = rend - l;
-            }
-            p.out.score[pi.id] = o0;
-            p.out.qend[pi.id] = o1;
-            p.out.rend[pi.id] = o2;
-            p.out.qstart[pi.id] = o3;
-            p.out.rstart[pi.id] = o4;
-        }
     }
 }
-
-}  // namespace
 
 size_t group_smem_bytes(ProfileKind kind, int alphabet) {
-    const size_t per_warp = kind == ProfileKind::kInt8 ? profile_bytes_per_warp<true>(alphabet)
-                                                       : profile_bytes_per_warp<false>(alphabet);
+    const size_t per_warp = kind == ProfileKind::kInt8
+                                ? (size_t)(alphabet + 1) * 32 * 16
+                                : (size_t)(alphabet + 1) * (kRows / 4) * 32 * 16;
     return kMaxAlphabet * kMaxAlphabet + kGroupWarps * per_warp;
 }
 
@@ -342,7 +439,7 @@ int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes) {
 }
 
 cudaError_t launch_group(const GroupParams &p, ProfileKind kind, int grid, cudaStream_t s) {
-    if (p.n_tasks <= 0 || grid <= 0) return cudaSuccess;
+    if (p.n_classes <= 0 || grid <= 0) return cudaSuccess;
     const size_t smem = group_smem_bytes(kind, p.alphabet);
     if (kind == ProfileKind::kInt8)
         sw_group_kernel<kRows, true><<<grid, kGroupWarps * 32, smem, s>>>(p);

@@ -19,6 +19,10 @@ constexpr int kMaxScaledGap = 16383;
 constexpr int kMaxAlphabet = 32;
 constexpr int kRows = 16;                      // query rows per lane (group kernel)
 constexpr int kGroupWarps = 4;                 // warps per block (group kernel)
+#ifndef SWGB_GROUP_MIN_BLOCKS
+#define SWGB_GROUP_MIN_BLOCKS 4
+#endif
+constexpr int kGroupMinBlocks = SWGB_GROUP_MIN_BLOCKS;  // resident blocks per SM (register cap)
 constexpr int kPlainWideThreads = 256;         // plain kernel block for queries > 1024
 constexpr int kPlainMaxRows = 256;             // rows per thread there (n <= 65536)
 
@@ -32,14 +36,16 @@ struct PairInfo {
     int32_t pad;
 };
 
-// A warp's unit of work in the persistent kernel: `count` consecutive pairs
-// of the plan's pair array starting at `first`, each on G = 1 << log2g lanes.
-struct GroupTask {
+// A queue of the persistent kernel: `count` consecutive pairs of the plan's
+// pair array starting at `first` (sorted by cost, largest first), each
+// aligned by a group of G = 1 << log2g lanes.
+struct ClassInfo {
     int32_t first;
     int32_t count;
     int32_t log2g;
     int32_t pad;
 };
+constexpr int kMaxClasses = 6;  // G = 32, 16, 8, 4, 2, 1
 
 struct Outputs {
     int32_t *score, *qend, *rend, *qstart, *rstart;
@@ -49,9 +55,9 @@ struct GroupParams {
     const uint8_t *q;
     const uint8_t *r;
     const PairInfo *pairs;
-    const GroupTask *tasks;
-    int32_t n_tasks;
-    int32_t *counter;   // task queue head, zeroed before each launch
+    const ClassInfo *classes;
+    int32_t n_classes;
+    int32_t *counters;  // queue heads, one per class, zeroed before each launch
     uint32_t *scratch;  // strip-boundary words
     int32_t *status;    // device status word (0 = ok)
     Outputs out;
