@@ -99,11 +99,14 @@ int sw_ctx_sm_count(const sw_ctx *ctx, int32_t *out);
  * pass did not reproduce its forward score) and clear it. */
 int sw_ctx_status(sw_ctx *ctx, int32_t *status);
 
-/* Batched-path tuning: the longest serial sweep, in wavefront steps
- * (passes x (m + G - 1)), a pair may be given; pairs get the narrowest
- * lane group G in {1, 2, 4, 8, 16, 32} that stays under it.  Applies to
- * plans created afterwards.  Default 6000. */
-int sw_ctx_set_step_cap(sw_ctx *ctx, int32_t steps);
+/* Batched-path tuning for plans created afterwards.  narrow_log2g = -1
+ * (default): the planner chooses the lane-group width of the bulk of the
+ * pairs and the long-pair cap itself, by simulating the schedule of a few
+ * candidates.  narrow_log2g in [0, 5] fixes the bulk width G = 2^narrow_log2g;
+ * pairs whose serial sweep under it exceeds cap_fraction x the mean load of
+ * a group go to wider groups (cap_fraction > 0; a huge value keeps one
+ * width for all pairs). */
+int sw_ctx_set_tuning(sw_ctx *ctx, int32_t narrow_log2g, double cap_fraction);
 
 /*
  * Plan a batch.  q_offsets and r_offsets are HOST arrays of n_pairs + 1

@@ -35,7 +35,7 @@ SIGNATURES = {
     "sw_ctx_destroy": ([_P], ctypes.c_int),
     "sw_ctx_sm_count": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_status": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
-    "sw_ctx_set_step_cap": ([_P, _I32], ctypes.c_int),
+    "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
     "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
     "sw_plan_execute": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "sw_plan_execute_host": ([_P, _P, _P, _P, _P], ctypes.c_int),
@@ -135,8 +135,8 @@ def sw_ctx_status(ctx: int) -> int:
     return v.value
 
 
-def sw_ctx_set_step_cap(ctx: int, steps: int) -> None:
-    _check(load().sw_ctx_set_step_cap(ctx, steps), "sw_ctx_set_step_cap")
+def sw_ctx_set_tuning(ctx: int, narrow_log2g: int = -1, cap_fraction: float = 0.5) -> None:
+    _check(load().sw_ctx_set_tuning(ctx, narrow_log2g, cap_fraction), "sw_ctx_set_tuning")
 
 
 # -------------------------------------------------------------------- plan

@@ -61,7 +61,6 @@ int upload(T **dst, const std::vector<T> &src) {
     return SW_OK;
 }
 
-constexpr int kDefaultStepCap = 6000;
 
 }  // namespace
 
@@ -70,7 +69,8 @@ struct sw_ctx {
     int sm_count = 0;
     char name[256] = {0};
     int32_t *d_status = nullptr;
-    int step_cap = kDefaultStepCap;  // longest serial sweep a group may get (steps)
+    int narrow_log2g = -1;      // planner override: bulk lane-group width (log2), -1 = auto
+    double cap_fraction = 0.5;  // planner override: long-pair cap (used with narrow_log2g)
     std::mutex mu;
     std::vector<std::pair<sw_plan *, cudaEvent_t>> retired;
 };
@@ -91,6 +91,7 @@ struct sw_plan {
     uint32_t *d_scratch = nullptr;
     int64_t scratch_words = 0;
     int grid = 0;
+    int n_warps = 0;
     // one-block-per-pair kernel
     PairInfo *d_plain = nullptr;
     int32_t n_plain = 0;
@@ -197,9 +198,11 @@ int sw_ctx_status(sw_ctx *ctx, int32_t *status) {
     return SW_OK;
 }
 
-int sw_ctx_set_step_cap(sw_ctx *ctx, int32_t steps) {
-    if (!ctx || steps < 1) return fail(SW_EINVAL, "sw_ctx_set_step_cap: bad argument");
-    ctx->step_cap = steps;
+int sw_ctx_set_tuning(sw_ctx *ctx, int32_t narrow_log2g, double cap_fraction) {
+    if (!ctx || narrow_log2g < -1 || narrow_log2g > 5 || !(cap_fraction > 0))
+        return fail(SW_EINVAL, "sw_ctx_set_tuning: bad argument");
+    ctx->narrow_log2g = narrow_log2g;
+    ctx->cap_fraction = cap_fraction;
     return SW_OK;
 }
 
@@ -267,12 +270,10 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     else
         p->kind = ProfileKind::kInt32;
 
-    struct Item {
-        int32_t id, n, m, log2g, passes;
-    };
-    std::vector<Item> items;
+    std::vector<PlanPair> gp_pairs;  // group-path pairs, id = index into group_ids
+    std::vector<int32_t> group_ids;
     std::vector<PairInfo> plain;
-    items.reserve(n_pairs);
+    gp_pairs.reserve(n_pairs);
     int plain_max_n = 0;
     for (int32_t i = 0; i < n_pairs; ++i) {
         const bool scaled = gaps_scaled_ok &&
@@ -283,47 +284,43 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
             plain_max_n = std::max(plain_max_n, n[i]);
             continue;
         }
-        int log2g = 5, passes = 0;
-        if (n[i] > 0 && m[i] > 0) {
-            for (int lg = 0; lg <= 5; ++lg) {
-                const int G = 1 << lg;
-                const int ps = (n[i] + G * kRows - 1) / (G * kRows);
-                if ((int64_t)ps * (m[i] + G - 1) <= ctx->step_cap || lg == 5) {
-                    log2g = lg;
-                    passes = ps;
-                    break;
-                }
-            }
-        } else {
-            log2g = 0;
-        }
-        items.push_back({i, n[i], m[i], log2g, passes});
+        gp_pairs.push_back({(int32_t)group_ids.size(), n[i], m[i]});
+        group_ids.push_back(i);
     }
-    // one queue per lane-group width, widest (longest sweeps) first; inside a
-    // queue, pairs by serial cost, largest first
-    std::sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
-        if (x.log2g != y.log2g) return x.log2g > y.log2g;
-        const int64_t cx = (int64_t)std::max(x.passes, 1) * (x.m + (1 << x.log2g) - 1);
-        const int64_t cy = (int64_t)std::max(y.passes, 1) * (y.m + (1 << y.log2g) - 1);
-        if (cx != cy) return cx > cy;
-        return x.id < y.id;
-    });
+    int n_warps = 0;
+    if (!gp_pairs.empty()) {
+        int smem = 0;
+        const int bps = group_blocks_per_sm(p->kind, A, &smem);
+        if (bps <= 0) {
+            plan_free(p);
+            return fail(SW_ECUDA, "sw_plan_create: group kernel does not fit (%d B smem)", smem);
+        }
+        const int64_t want = ((int64_t)gp_pairs.size() + kGroupWarps - 1) / kGroupWarps;
+        p->grid = (int)std::min<int64_t>((int64_t)bps * ctx->sm_count, want);
+        n_warps = p->grid * kGroupWarps;
+    }
+    const std::vector<PlannedClass> planned =
+        plan_classes(gp_pairs, n_warps, ctx->narrow_log2g, ctx->cap_fraction);
     std::vector<PairInfo> pairs;
     std::vector<ClassInfo> classes;
-    pairs.reserve(items.size());
+    pairs.reserve(gp_pairs.size());
     int64_t scratch = 0;
-    for (size_t k = 0; k < items.size(); ++k) {
-        const Item &it = items[k];
-        if (classes.empty() || classes.back().log2g != it.log2g)
-            classes.push_back({(int32_t)k, 0, it.log2g, 0});
-        classes.back().count++;
-        PairInfo pi{q_offsets[it.id], r_offsets[it.id], -1, it.n, it.m, it.id, 0};
-        if (it.passes >= 2) {
-            pi.scratch = scratch;
-            scratch += 2 * (int64_t)it.m;
+    int warp_begin = 0;
+    for (const PlannedClass &pc : planned) {
+        classes.push_back({(int32_t)pairs.size(), (int32_t)pc.pairs.size(), pc.log2g, warp_begin});
+        warp_begin += pc.warps;
+        const int G = 1 << pc.log2g;
+        for (int32_t k : pc.pairs) {
+            const int32_t i = group_ids[k];
+            PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
+            if (n[i] > G * kRows && m[i] > 0) {
+                pi.scratch = scratch;
+                scratch += 2 * (int64_t)m[i];
+            }
+            pairs.push_back(pi);
         }
-        pairs.push_back(pi);
     }
+    p->n_warps = n_warps;
     p->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
     p->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
     p->n_classes = (int32_t)classes.size();
@@ -342,16 +339,6 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
         plan_free(p);
         return fail(SW_ENOMEM, "sw_plan_create: scratch allocation (%lld words) failed",
                     (long long)scratch);
-    }
-    if (p->n_group > 0) {
-        int smem = 0;
-        const int bps = group_blocks_per_sm(p->kind, A, &smem);
-        if (bps <= 0) {
-            plan_free(p);
-            return fail(SW_ECUDA, "sw_plan_create: group kernel does not fit (%d B smem)", smem);
-        }
-        const int64_t want = ((int64_t)p->n_group + kGroupWarps - 1) / kGroupWarps;
-        p->grid = (int)std::min<int64_t>((int64_t)bps * ctx->sm_count, want);
     }
     if (p->n_plain > 0) {
         if (plain_max_n <= 1024) {
@@ -378,6 +365,7 @@ static int enqueue(sw_plan *p, const uint8_t *q, const uint8_t *r, const Outputs
         gp.classes = p->d_classes;
         gp.n_classes = p->n_classes;
         gp.counters = p->d_counter;
+        gp.n_warps = p->n_warps;
         gp.scratch = p->d_scratch;
         gp.status = p->ctx->d_status;
         gp.out = o;

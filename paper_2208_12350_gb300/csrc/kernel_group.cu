@@ -161,7 +161,14 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     for (int i = threadIdx.x; i < A * A; i += blockDim.x) smat[i] = p.mat[i];
     __syncthreads();
 
-    for (int cls = 0; cls < p.n_classes; ++cls) {
+    // this warp starts on the class whose warp range holds it, then walks
+    // the classes cyclically
+    const int wid = blockIdx.x * kGroupWarps + warp;
+    int start = 0;
+    for (int c = 1; c < p.n_classes; ++c)
+        if (wid >= p.classes[c].warp_begin) start = c;
+    for (int visit = 0; visit < p.n_classes; ++visit) {
+        const int cls = (start + visit) % p.n_classes;
         const ClassInfo ci = p.classes[cls];
         const int log2g = ci.log2g;
         const int G = 1 << log2g;

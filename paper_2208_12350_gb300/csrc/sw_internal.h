@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace swgb {
 
 // Scores on the batched path are held scaled by 2^16 so that the low half
@@ -43,7 +45,7 @@ struct ClassInfo {
     int32_t first;
     int32_t count;
     int32_t log2g;
-    int32_t pad;
+    int32_t warp_begin;  // warps [warp_begin, next class's warp_begin) start here
 };
 constexpr int kMaxClasses = 6;  // G = 32, 16, 8, 4, 2, 1
 
@@ -58,6 +60,7 @@ struct GroupParams {
     const ClassInfo *classes;
     int32_t n_classes;
     int32_t *counters;  // queue heads, one per class, zeroed before each launch
+    int32_t n_warps;    // warps of the launch (grid x warps per block)
     uint32_t *scratch;  // strip-boundary words
     int32_t *status;    // device status word (0 = ok)
     Outputs out;
@@ -80,6 +83,20 @@ struct PlainParams {
 
 // Device status bits.
 constexpr int32_t kStatusReverseMismatch = 1;  // reverse pass lost the score
+
+// Host planning of the persistent kernel (plan.cpp): which lane-group width
+// each pair gets and how many warps start on each width class.
+struct PlanPair {
+    int32_t id, n, m;
+};
+struct PlannedClass {
+    int log2g;
+    std::vector<int32_t> pairs;  // pair ids, largest estimated cost first
+    int warps;                   // warps that start on this class
+};
+std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
+                                       int narrow_log2g_hint, double cap_fraction_hint);
+int64_t sweep_steps(int n, int m, int G);
 
 // Profile element width of the group kernel.
 enum class ProfileKind : int { kInt32 = 0, kInt8 = 1 };

@@ -13,9 +13,9 @@ import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-def run_lib(swgb, ctx, b, mode=None, flags=0, step_cap=None):
-    if step_cap is not None:
-        swgb.sw_ctx_set_step_cap(ctx, step_cap)
+def run_lib(swgb, ctx, b, mode=None, flags=0, tuning=None):
+    if tuning is not None:
+        swgb.sw_ctx_set_tuning(ctx, *tuning)
     try:
         al = swgb.Aligner(b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix, b.gap_open,
                           b.gap_extend, mode=swgb.SW_MODE_AUTO if mode is None else mode,
@@ -25,8 +25,8 @@ def run_lib(swgb, ctx, b, mode=None, flags=0, step_cap=None):
         info = al.info()
         al.close()
     finally:
-        if step_cap is not None:
-            swgb.sw_ctx_set_step_cap(ctx, 6000)
+        if tuning is not None:
+            swgb.sw_ctx_set_tuning(ctx, -1, 0.5)
     assert swgb.sw_ctx_status(ctx) == 0
     return got, info
 
@@ -98,21 +98,29 @@ def edge_batch(kind, seed, lens_q, lens_r, plant=True):
     return wl.make_batch("edge-protein", qs, rs, s.astype(np.int8), -11, -1)
 
 
-@pytest.mark.parametrize("step_cap", [1, 2000, 6000, 10 ** 9])
-def test_edge_lengths_all_group_widths(gpu_lib, ctx, step_cap):
-    """Lengths around every tile edge; step_cap 1 forces G = 32, 10^9 forces G = 1."""
-    b = edge_batch("dna", step_cap % 97, EDGE, EDGE[::3])
+TUNINGS = [(lg, 1e9) for lg in range(6)] + [(0, 0.05), (1, 0.3), (-1, 0.5)]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=[f"G{1 << t[0] if t[0] >= 0 else 'auto'}-cap{t[1]:g}"
+                                                 for t in TUNINGS])
+def test_edge_lengths_all_group_widths(gpu_lib, ctx, tuning):
+    """Lengths around every tile edge, under every lane-group width.
+
+    (lg, 1e9) puts every pair on groups of 2^lg lanes; a small cap fraction
+    spreads the pairs over several width classes in one launch.
+    """
+    b = edge_batch("dna", 7 + tuning[0], EDGE, EDGE[::3])
     expect = oracle.align_workload(b)
-    got, _ = run_lib(gpu_lib, ctx, b, step_cap=step_cap)
-    assert_same(got, expect, f"edge dna cap={step_cap}")
+    got, _ = run_lib(gpu_lib, ctx, b, tuning=tuning)
+    assert_same(got, expect, f"edge dna tuning={tuning}")
 
 
 def test_edge_lengths_protein(gpu_lib, ctx):
     b = edge_batch("protein", 5, EDGE[::2], EDGE[1::3])
     expect = oracle.align_workload(b)
-    for cap in (1, 6000):
-        got, _ = run_lib(gpu_lib, ctx, b, step_cap=cap)
-        assert_same(got, expect, f"edge protein cap={cap}")
+    for tuning in ((5, 1e9), (0, 1e9), (-1, 0.5)):
+        got, _ = run_lib(gpu_lib, ctx, b, tuning=tuning)
+        assert_same(got, expect, f"edge protein tuning={tuning}")
     got, _ = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_PLAIN)
     assert_same(got, expect, "edge protein plain")
 
