@@ -69,7 +69,7 @@ def test_host_side_argument_errors(lib):
     assert rc == swgb.SW_EINVAL
     assert b"ctx is NULL" in lib.sw_last_error()
     assert lib.sw_plan_execute(None, None, None, None, None, None, None, None, None) == swgb.SW_EINVAL
-    assert lib.sw_ctx_set_step_cap(None, 10) == swgb.SW_EINVAL
+    assert lib.sw_ctx_set_tuning(None, -1, 0.5) == swgb.SW_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
