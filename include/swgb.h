@@ -190,6 +190,44 @@ int sw_check_residues(const uint8_t *seqs, int64_t n, int32_t alphabet_size,
                       int64_t *bad_count, void *stream);
 
 /*
+ * Allocation-free batched alignment.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory when they align - code
+ * running where another component (a framework's caching allocator, a
+ * fixed-size arena) already owns the device's memory budget, or a
+ * latency-critical loop that must not stall on the implicit device
+ * synchronisation of cudaMalloc/cudaFree.
+ *
+ * Same computation, outputs and kernels as sw_plan_create +
+ * sw_plan_execute in SW_MODE_AUTO, but the call allocates no device memory:
+ * its tables, queue heads and strip-boundary scratch live in one fixed
+ * module array of about 37 MiB that every GPU that loads the library keeps
+ * until the process exits.  q_seqs, r_seqs and the five outputs are DEVICE
+ * pointers owned by the caller; q_offsets, r_offsets and score_matrix are
+ * HOST arrays, as for sw_plan_create.
+ *
+ * Limits: at most SW_STATIC_MAX_PAIRS pairs per call, and the pairs whose
+ * query spans more than one row strip need 2 x (reference length) boundary
+ * words each, at most SW_STATIC_MAX_BOUNDARY_WORDS in total; a batch beyond
+ * either is rejected with SW_ERANGE before anything is enqueued (split it).
+ *
+ * The first call on a device resolves the array's device address on that
+ * device; make that first call before capturing any stream on the device.
+ * Every call uses the same array (it keeps the previous call's contents and
+ * clears what must start at zero), so calls whose GPU work overlaps - on
+ * different streams or threads - race with each other: order them, e.g. on
+ * one stream.  The work is enqueued on `stream` and the call returns;
+ * the host arrays may be reused once it has returned.
+ */
+#define SW_STATIC_MAX_PAIRS 65536
+#define SW_STATIC_MAX_BOUNDARY_WORDS (8 << 20)
+int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_offsets,
+                          const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                          const int8_t *score_matrix, int32_t alphabet_size,
+                          int32_t gap_open, int32_t gap_extend,
+                          int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
+                          int32_t *out_qstart, int32_t *out_rstart, void *stream);
+
+/*
  * Integer issue-rate microbenchmark on `device` (made current for the call;
  * synchronous).  op: 0 = 32-bit add, 1 = 32-bit max, 2 = __viaddmax_s32
  * (add then max), 3 = __vimax3_s32_relu, 4 = __viaddmax_s16x2,

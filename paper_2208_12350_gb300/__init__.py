@@ -47,6 +47,8 @@ SIGNATURES = {
     "sw_align_batch_ex": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P,
                            _P, _P], ctypes.c_int),
     "sw_check_residues": ([_P, _I64, _I32, _P, _P], ctypes.c_int),
+    "sw_align_batch_static": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
+                              ctypes.c_int),
     "sw_microbench_int": ([_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -206,6 +208,25 @@ def sw_align_batch_ex(ctx: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matr
                                     _addr(r_offsets), n, mat.ctypes.data, mat.shape[0], gap_open,
                                     gap_extend, mode, *[_addr(o) for o in outs], _stream(stream)),
            "sw_align_batch_ex")
+
+
+SW_STATIC_MAX_PAIRS = 65536
+SW_STATIC_MAX_BOUNDARY_WORDS = 8 << 20
+
+
+def sw_align_batch_static(q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, gap_open: int,
+                          gap_extend: int, out, stream=None) -> None:
+    """Allocation-free alignment: sequences and out on the device, offsets and
+    score_matrix on the host.  The library allocates no device memory for the
+    call (see include/swgb.h for the fixed limits and the ordering rule)."""
+    qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
+    mat = _host_i8(score_matrix)
+    outs = [out[k] for k in range(5)]
+    _check(load().sw_align_batch_static(_addr(q_seqs), qo.ctypes.data, _addr(r_seqs),
+                                        ro.ctypes.data, len(qo) - 1, mat.ctypes.data,
+                                        mat.shape[0], gap_open, gap_extend,
+                                        *[_addr(o) for o in outs], _stream(stream)),
+           "sw_align_batch_static")
 
 
 def sw_check_residues(seqs, n: int, alphabet_size: int, bad_count, stream=None) -> None:

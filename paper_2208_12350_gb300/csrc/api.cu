@@ -64,6 +64,14 @@ int upload(T **dst, const std::vector<T> &src) {
 
 }  // namespace
 
+namespace swgb {
+// Records a failure message for sw_last_error() from other translation units.
+int set_error(int code, const char *msg) {
+    g_last_error = msg;
+    return code;
+}
+}  // namespace swgb
+
 struct sw_ctx {
     int device = 0;
     int sm_count = 0;

@@ -110,6 +110,8 @@ cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_
                          cudaStream_t s);
 size_t plain_smem_bytes(int threads, int alphabet);
 
+int set_error(int code, const char *msg);  // message for sw_last_error()
+
 cudaError_t launch_check_residues(const uint8_t *seqs, int64_t n, int alphabet,
                                   unsigned long long *bad, cudaStream_t s);
 
