@@ -54,7 +54,10 @@ namespace swgb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kU = 4;  // steps per block; loads run one block ahead
+#ifndef SWGB_GROUP_UNROLL
+#define SWGB_GROUP_UNROLL 4
+#endif
+constexpr int kU = SWGB_GROUP_UNROLL;  // steps per block; loads run one block ahead
 
 // Sign-extended int8 byte B of w, moved to bits 16..31 (value << 16).
 template <int B>
@@ -81,15 +84,21 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
     }
     for (int c = 0; c <= A; ++c) {
         if constexpr (P8) {
-            static_assert(R == 16, "int8 profile holds 16 rows per lane");
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            static_assert(R == 16 || R == 8, "int8 profile holds 8 or 16 rows per lane");
+            uint32_t w[R / 4];
+#pragma unroll
+            for (int k = 0; k < R / 4; ++k) w[k] = 0u;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int v = (qa[r] >= 0 && c < A) ? (int)smat[qa[r] + c] - go : -128;
                 w[r >> 2] |= (uint32_t)(uint8_t)(int8_t)v << (8 * (r & 3));
             }
-            *reinterpret_cast<uint4 *>(prof + ((size_t)c * 32 + lane) * 16) =
-                make_uint4(w[0], w[1], w[2], w[3]);
+            if constexpr (R == 16)
+                *reinterpret_cast<uint4 *>(prof + ((size_t)c * 32 + lane) * 16) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            else
+                *reinterpret_cast<uint2 *>(prof + ((size_t)c * 32 + lane) * 8) =
+                    make_uint2(w[0], w[1]);
         } else {
 #pragma unroll
             for (int k = 0; k < R / 4; ++k) {
@@ -110,10 +119,20 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
 template <int R, bool P8>
 __device__ __forceinline__ void load_scores(const char *prof, int c, int lane, int (&sc)[R]) {
     if constexpr (P8) {
-        const uint4 w = *reinterpret_cast<const uint4 *>(prof + ((size_t)c * 32 + lane) * 16);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        uint32_t ws[R / 4];
+        if constexpr (R == 16) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(prof + ((size_t)c * 32 + lane) * 16);
+            ws[0] = w.x;
+            ws[1] = w.y;
+            ws[2] = w.z;
+            ws[3] = w.w;
+        } else {
+            const uint2 w = *reinterpret_cast<const uint2 *>(prof + ((size_t)c * 32 + lane) * 8);
+            ws[0] = w.x;
+            ws[1] = w.y;
+        }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < R / 4; ++k) {
             sc[4 * k + 0] = byte_hi<0>(ws[k]);
             sc[4 * k + 1] = byte_hi<1>(ws[k]);
             sc[4 * k + 2] = byte_hi<2>(ws[k]);
@@ -132,18 +151,17 @@ __device__ __forceinline__ void load_scores(const char *prof, int c, int lane, i
     }
 }
 
-// Sweep state of one group (every lane of the group holds the same values).
-struct Sweep {
-    const uint8_t *a;  // row residues at a[i * dir]
-    const uint8_t *b;  // column residues at b[j * dir]
-    uint32_t *bnd;     // 2*m strip-boundary words when passes > 1
-    int dir;           // +1 forward, -1 reverse
-    int n, m;
-    int passes, ps;    // strips and current strip
-    int s, lim;        // step within the strip and steps it needs
-    int stop;          // columns still needed (the reverse pass shrinks it)
-    int target;        // reverse pass: the forward score to find
+// Per-lane bookkeeping of a group that only the strip and sweep transitions
+// read: kept in shared memory (one array per field, indexed by thread) so
+// the step loop's registers hold the DP state alone.
+struct Cold {
+    const uint8_t **a;   // row residues of the current sweep (a[i * dir])
+    uint32_t **bnd;      // the pair's strip-boundary words
+    int *n, *m, *passes, *ps, *target, *id, *S, *qend, *rend, *best_row;
+    uint32_t *best_key;
 };
+
+constexpr int kColdWords = 2 * 2 + 11;  // 32-bit words per lane
 
 }  // namespace
 
@@ -154,11 +172,29 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     const int A = p.alphabet;
     const int go = p.gap_open, ge = p.gap_extend;
     const int goS = go * 65536, geS = ge * 65536;
+    constexpr int NT = kGroupWarps * 32;
+    const int t = threadIdx.x;
+    const int warp = t >> 5, lane = t & 31;
+    const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * R : (size_t)(A + 1) * (R / 4) * 32 * 16;
     int8_t *smat = reinterpret_cast<int8_t *>(smem_group);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * 16 : (size_t)(A + 1) * (R / 4) * 32 * 16;
-    char *prof = smem_group + kMaxAlphabet * kMaxAlphabet + warp * prof_bytes;
-    for (int i = threadIdx.x; i < A * A; i += blockDim.x) smat[i] = p.mat[i];
+    char *cold_base = smem_group + kMaxAlphabet * kMaxAlphabet;
+    char *prof = cold_base + (size_t)kColdWords * 4 * NT + warp * prof_bytes;
+    Cold cold;
+    cold.a = reinterpret_cast<const uint8_t **>(cold_base);
+    cold.bnd = reinterpret_cast<uint32_t **>(cold_base + 8 * NT);
+    int *cw = reinterpret_cast<int *>(cold_base + 16 * NT);
+    cold.n = cw;
+    cold.m = cw + NT;
+    cold.passes = cw + 2 * NT;
+    cold.ps = cw + 3 * NT;
+    cold.target = cw + 4 * NT;
+    cold.id = cw + 5 * NT;
+    cold.S = cw + 6 * NT;
+    cold.qend = cw + 7 * NT;
+    cold.rend = cw + 8 * NT;
+    cold.best_row = cw + 9 * NT;
+    cold.best_key = reinterpret_cast<uint32_t *>(cw + 10 * NT);
+    for (int i = t; i < A * A; i += blockDim.x) smat[i] = p.mat[i];
     __syncthreads();
 
     // this warp starts on the class whose warp range holds it, then walks
@@ -176,32 +212,21 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         const int gbase = lane & ~(G - 1);
         const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
 
-        Sweep sw;
-        sw.a = p.q;
-        sw.b = p.r;
-        sw.bnd = p.scratch;
-        sw.dir = 1;
-        sw.n = sw.m = 0;
-        sw.passes = sw.ps = 0;
-        sw.s = sw.lim = 0;
-        sw.stop = 0;
-        sw.target = 0;
-        int id = -1;           // output slot of the group's pair, -1 when idle
-        bool rev = false;
-        bool drained = false;  // the class queue had nothing left for this group
-        int S = 0, qend = 0, rend = 0;
-        uint32_t best_key = 0;
-        int best_row = 0x7fffffff;
-        bool reload = true;    // block data must be loaded before use
-
-        int Hg[R], E[R];
+        // hot state: DP registers, the strip's step counters and pointers
+        int H[R], E[R];
         uint32_t K[R];
-        int diag0 = goS, outHg = goS, outF = kScaledNegInf;
+        int diag0 = 0, outH = 0, outF = kScaledNegInf;
+        int s = 0, lim = 0, stop = 0, dir = 1;
+        const uint8_t *bcol = p.r;
+        const uint32_t *bin = p.scratch;
+        uint32_t *bout = p.scratch;
+        bool has_in = false, has_out = false;
+        bool live = false, rev = false, drained = false, reload = true;
         int cur_c[kU], nxt_c[kU];
         uint32_t cur_b[kU], nxt_b[kU];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            Hg[r] = goS;
+            H[r] = 0;
             E[r] = kScaledNegInf;
             K[r] = 0u;
         }
@@ -210,47 +235,58 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             cur_c[u] = nxt_c[u] = A;
             cur_b[u] = nxt_b[u] = 0u;
         }
+        cold.id[t] = -1;
 
-        // Starts strip sw.ps: profile of this lane's rows, fresh DP state.
-        auto begin_strip = [&]() {
-            const int row0 = sw.ps * G * R + gl * R;
-            build_profile<R, P8>(prof, lane, sw.a, sw.dir, row0, sw.n, smat, A, go);
+        // Starts strip ps of the current sweep: profile of this lane's rows,
+        // fresh DP state, boundary buffers of the strip.
+        auto begin_strip = [&](int ps) {
+            const int n = cold.n[t], m = cold.m[t];
+            build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n, smat, A, go);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                Hg[r] = goS;
+                H[r] = 0;
                 E[r] = kScaledNegInf;
                 K[r] = 0u;
             }
-            diag0 = goS;
-            outHg = goS;
+            diag0 = 0;
+            outH = 0;
             outF = kScaledNegInf;
-            sw.s = 0;
-            sw.lim = sw.stop + G - 1;
+            s = 0;
+            lim = stop + G - 1;
+            uint32_t *bnd = cold.bnd[t];
+            bin = bnd + ((ps + 1) & 1) * m;
+            bout = bnd + (ps & 1) * m;
+            has_in = ps > 0;
+            has_out = ps + 1 < cold.passes[t];
+            cold.ps[t] = ps;
             reload = true;
         };
-        // Starts a sweep over (a, n) x (b, m) in direction dir.
-        auto begin_sweep = [&](const uint8_t *a, const uint8_t *b, int n, int m, int dir) {
-            sw.a = a;
-            sw.b = b;
-            sw.dir = dir;
-            sw.n = n;
-            sw.m = m;
-            sw.passes = (n > 0 && m > 0) ? (n + G * R - 1) / (G * R) : 0;
-            sw.ps = 0;
-            sw.stop = m;
-            best_key = 0u;
-            best_row = 0x7fffffff;
-            if (sw.passes > 0) {
-                begin_strip();
+        // Starts a sweep over (a, n) x (b, m) in direction d.
+        auto begin_sweep = [&](const uint8_t *a, const uint8_t *b, int n, int m, int d) {
+            cold.a[t] = a;
+            bcol = b;
+            dir = d;
+            cold.n[t] = n;
+            cold.m[t] = m;
+            const int passes = (n > 0 && m > 0) ? (n + G * R - 1) / (G * R) : 0;
+            cold.passes[t] = passes;
+            cold.best_key[t] = 0u;
+            cold.best_row[t] = 0x7fffffff;
+            if (passes > 0) {
+                stop = m;
+                begin_strip(0);
             } else {
-                sw.s = 0;
-                sw.lim = 0;
+                stop = 0;
+                s = 0;
+                lim = 0;
+                has_in = has_out = false;
+                cold.ps[t] = 0;
             }
         };
 
         for (;;) {
             // ---- idle groups take the next pair of the class
-            if (id < 0 && !drained) {
+            if (!live && !drained) {
                 int idx = 0;
                 if (gl == 0) idx = atomicAdd(p.counters + cls, 1);
                 idx = __shfl_sync(gmask, idx, gbase);
@@ -258,28 +294,22 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     drained = true;
                 } else {
                     const PairInfo pi = p.pairs[ci.first + idx];
-                    id = pi.id;
+                    live = true;
                     rev = false;
-                    sw.bnd = pi.scratch >= 0 ? p.scratch + pi.scratch : p.scratch;
+                    cold.id[t] = pi.id;
+                    cold.bnd[t] = p.scratch + (pi.scratch >= 0 ? pi.scratch : 0);
                     begin_sweep(p.q + pi.q, p.r + pi.r, pi.n, pi.m, 1);
                 }
             }
-            if (__all_sync(kFull, id < 0)) break;  // every group drained and idle
+            if (__all_sync(kFull, !live)) break;  // every group drained and idle
 
-            const bool live = id >= 0;
-            const int mcols = live && sw.ps < sw.passes ? sw.stop : 0;
-            const bool has_in = sw.ps > 0;
-            const bool has_out = sw.ps + 1 < sw.passes;
-            const uint32_t *bin = sw.bnd + ((sw.ps + 1) & 1) * sw.m;
-            uint32_t *bout = sw.bnd + (sw.ps & 1) * sw.m;
-            const uint8_t *bcol = sw.b;
-            const int dir = sw.dir;
+            const int mcols = live ? stop : 0;
 
             // ---- residue codes and boundary words: this block (if stale), next block
             if (reload) {
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
-                    const int j = sw.s + u - gl;
+                    const int j = s + u - gl;
                     const bool in = (unsigned)j < (unsigned)mcols;
                     cur_c[u] = in ? min((int)bcol[(ptrdiff_t)j * dir], A - 1) : A;
                     cur_b[u] = (in && gl == 0 && has_in) ? bin[j] : 0u;
@@ -288,71 +318,84 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int j = sw.s + kU + u - gl;
+                const int j = s + kU + u - gl;
                 const bool in = (unsigned)j < (unsigned)mcols;
                 nxt_c[u] = in ? min((int)bcol[(ptrdiff_t)j * dir], A - 1) : A;
                 nxt_b[u] = (in && gl == 0 && has_in) ? bin[j] : 0u;
             }
 
-            // ---- U wavefront steps, the same instructions on every lane
+            // ---- U wavefront steps, the same instructions on every lane.  E and F
+            // are held minus go, so the row-to-row chain is two instructions:
+            //   F'_r = max(F'_{r-1} + ge, H_{r-1})        E'_r = max(E'_r + ge, H_left)
+            //   T    = max(H_diag + (s - go), E'_r) + go  H_r  = max(F'_r + go, T, 0)
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int j = sw.s + u - gl;
+                const int j = s + u - gl;
                 const bool in = (unsigned)j < (unsigned)mcols;
-                int inHg = __shfl_up_sync(kFull, outHg, 1, G);
+                int inH = __shfl_up_sync(kFull, outH, 1, G);
                 int inF = __shfl_up_sync(kFull, outF, 1, G);
                 if (gl == 0) {
                     const bool from_bnd = in && has_in;
-                    inHg = from_bnd ? (int)(cur_b[u] << 16) : goS;
+                    inH = from_bnd ? (int)(cur_b[u] << 16) : 0;
                     inF = from_bnd ? (int)(cur_b[u] & 0xFFFF0000u) : kScaledNegInf;
                 }
-                const int c = in ? cur_c[u] : A;
+                int c = in ? cur_c[u] : A;
+                // tie this step's profile loads to its shuffle result, so the
+                // compiler cannot hoist every unrolled step's loads (and their
+                // registers) to the top of the block
+                asm volatile("" : "+r"(c) : "r"(inH));
                 int sc[R];
                 load_scores<R, P8>(prof, c, lane, sc);
                 const int cj = 65535 - max(j, 0);
                 int diag = diag0;
-                int F = __viaddmax_s32(inF, geS, inHg);
+                int F = __viaddmax_s32(inF, geS, inH);
+                int hprev = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (r > 0) F = __viaddmax_s32(F, geS, Hg[r - 1]);
-                    E[r] = __viaddmax_s32(E[r], geS, Hg[r]);
-                    const int T = __viaddmax_s32(diag, sc[r], E[r]);
-                    const int h = __vimax_s32_relu(T, F);
-                    diag = Hg[r];
-                    Hg[r] = h + goS;
+                    if (r > 0) F = __viaddmax_s32(F, geS, hprev);
+                    E[r] = __viaddmax_s32(E[r], geS, H[r]);
+                    const int T = __viaddmax_s32(diag, sc[r], E[r]) + goS;
+                    const int h = __viaddmax_s32_relu(F, goS, T);
+                    diag = H[r];
+                    H[r] = h;
+                    hprev = h;
                     K[r] = (uint32_t)__viaddmax_s32(h, cj, (int)K[r]);
                 }
-                outHg = Hg[R - 1];
+                outH = hprev;
                 outF = F;
                 if (in && has_out && gl == G - 1)
-                    bout[j] = ((uint32_t)outHg >> 16) | ((uint32_t)outF & 0xFFFF0000u);
-                diag0 = inHg;
+                    bout[j] = ((uint32_t)outH >> 16) | ((uint32_t)outF & 0xFFFF0000u);
+                diag0 = inH;
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 cur_c[u] = nxt_c[u];
                 cur_b[u] = nxt_b[u];
             }
-            sw.s += kU;
+            s += kU;
 
             // ---- reverse sweep: stop once a cell of the forward score has appeared
-            if (rev && live && ((sw.s & (2 * kU - 1)) == 0)) {
+            if (rev && live && ((s & (2 * kU - 1)) == 0)) {
+                const int target = cold.target[t];
                 uint32_t lk = K[0];
 #pragma unroll
                 for (int r = 1; r < R; ++r) lk = max(lk, K[r]);
-                int found = (int)(lk >> 16) >= sw.target ? 65535 - (int)(lk & 0xFFFFu) : 0x7fffffff;
+                int found = (int)(lk >> 16) >= target ? 65535 - (int)(lk & 0xFFFFu) : 0x7fffffff;
                 for (int off = 1; off < G; off <<= 1)
                     found = min(found, __shfl_xor_sync(gmask, found, off, G));
-                if (found != 0x7fffffff && found + 1 < sw.stop) {
-                    sw.stop = found + 1;
-                    sw.lim = sw.stop + G - 1;
+                if (found != 0x7fffffff && found + 1 < stop) {
+                    stop = found + 1;
+                    lim = stop + G - 1;
                 }
             }
 
             // ---- end of a strip / sweep
-            if (live && sw.s >= sw.lim) {
-                if (sw.ps < sw.passes) {
-                    const int row0 = sw.ps * G * R + gl * R;
+            if (live && s >= lim) {
+                const int ps = cold.ps[t], passes = cold.passes[t];
+                uint32_t best_key = cold.best_key[t];
+                int best_row = cold.best_row[t];
+                if (ps < passes) {
+                    const int row0 = ps * G * R + gl * R;
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         if (K[r] > best_key) {
@@ -360,10 +403,11 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             best_row = row0 + r;
                         }
                 }
-                if (sw.ps + 1 < sw.passes) {
+                cold.best_key[t] = best_key;
+                cold.best_row[t] = best_row;
+                if (ps + 1 < passes) {
                     __syncwarp(gmask);  // boundary words written by lane G-1 -> lane 0
-                    ++sw.ps;
-                    begin_strip();
+                    begin_strip(ps + 1);
                 } else {
                     for (int off = 1; off < G; off <<= 1) {
                         const uint32_t ok = __shfl_xor_sync(gmask, best_key, off, G);
@@ -375,21 +419,27 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     }
                     bool done = true;
                     if (!rev) {
-                        S = (int)(best_key >> 16);
-                        qend = best_row;
-                        rend = 65535 - (int)(best_key & 0xFFFFu);
+                        const int S = (int)(best_key >> 16);
+                        const int qend = best_row;
+                        const int rend = 65535 - (int)(best_key & 0xFFFFu);
+                        cold.S[t] = S;
                         if (S > 0) {
+                            cold.qend[t] = qend;
+                            cold.rend[t] = rend;
+                            cold.target[t] = S;
                             rev = true;
                             done = false;
                             __syncwarp(gmask);
-                            begin_sweep(sw.a + qend, sw.b + rend, qend + 1, rend + 1, -1);
-                            sw.target = S;
+                            begin_sweep(cold.a[t] + qend, bcol + rend, qend + 1, rend + 1, -1);
                         }
                     }
                     if (done) {
                         if (gl == 0) {
+                            const int S = cold.S[t];
+                            const int id = cold.id[t];
                             int o0 = 0, o1 = -1, o2 = -1, o3 = -1, o4 = -1;
                             if (S > 0) {
+                                const int qend = cold.qend[t], rend = cold.rend[t];
                                 const int S2 = (int)(best_key >> 16);
                                 const int l = 65535 - (int)(best_key & 0xFFFFu);
                                 if (S2 != S) atomicOr(p.status, kStatusReverseMismatch);
@@ -405,9 +455,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             p.out.qstart[id] = o3;
                             p.out.rstart[id] = o4;
                         }
-                        id = -1;
-                        S = 0;
+                        live = false;
                         rev = false;
+                        stop = 0;
                         __syncwarp(gmask);
                     }
                 }
@@ -418,9 +468,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
 
 size_t group_smem_bytes(ProfileKind kind, int alphabet) {
     const size_t per_warp = kind == ProfileKind::kInt8
-                                ? (size_t)(alphabet + 1) * 32 * 16
+                                ? (size_t)(alphabet + 1) * 32 * kRows
                                 : (size_t)(alphabet + 1) * (kRows / 4) * 32 * 16;
-    return kMaxAlphabet * kMaxAlphabet + kGroupWarps * per_warp;
+    return kMaxAlphabet * kMaxAlphabet + (size_t)kColdWords * 4 * kGroupWarps * 32 +
+           kGroupWarps * per_warp;
 }
 
 int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes) {

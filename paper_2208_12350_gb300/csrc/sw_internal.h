@@ -19,10 +19,13 @@ constexpr int32_t kScaledPad = -(1 << 29);     // profile score of rows beyond n
 constexpr int kMaxScaledScore = 32766;         // (S << 16) + 65535 < 2^31
 constexpr int kMaxScaledGap = 16383;
 constexpr int kMaxAlphabet = 32;
-constexpr int kRows = 16;                      // query rows per lane (group kernel)
+#ifndef SWGB_ROWS
+#define SWGB_ROWS 16
+#endif
+constexpr int kRows = SWGB_ROWS;               // query rows per lane (group kernel): 8 or 16
 constexpr int kGroupWarps = 4;                 // warps per block (group kernel)
 #ifndef SWGB_GROUP_MIN_BLOCKS
-#define SWGB_GROUP_MIN_BLOCKS 4
+#define SWGB_GROUP_MIN_BLOCKS 3
 #endif
 constexpr int kGroupMinBlocks = SWGB_GROUP_MIN_BLOCKS;  // resident blocks per SM (register cap)
 constexpr int kPlainWideThreads = 256;         // plain kernel block for queries > 1024
