@@ -323,7 +323,7 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
             PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
             if (n[i] > G * kRows && m[i] > 0) {
                 pi.scratch = scratch;
-                scratch += 2 * (int64_t)m[i];
+                scratch += boundary_words(m[i]);
             }
             pairs.push_back(pi);
         }

@@ -1,7 +1,7 @@
 // Persistent, length-bucketed batched kernel: the hot path.
 //
 // Work split.  The plan sorts pairs into classes by lane-group width G (32,
-// 16, ..., 1; longest sweeps first) and, inside a class, by cost.  A warp
+// 16, ..., 2; longest sweeps first) and, inside a class, by cost.  A warp
 // takes one class at a time and splits into 32/G groups of G lanes.  Each
 // group independently pulls a pair from its class queue, runs the forward
 // sweep, then the reverse sweep of the same pair, then pulls the next pair,
@@ -17,8 +17,15 @@
 // boundary instead: H = 0 / F = -infinity above the first strip (Section
 // II-B.1's boundary row), and for later strips the last row of the previous
 // strip, which lane G-1 wrote to global scratch.  Queries longer than G*R
-// rows take several strips ("passes").  Residue codes and boundary words
-// are loaded U steps before use.
+// rows take several strips ("passes").
+//
+// Staging.  Global memory is touched in 16-byte pieces only.  Each group has
+// three small rings in shared memory: reference residues (128 bytes, filled
+// by its lane 0 with cp.async a few 4-step blocks ahead; each lane then
+// reads its residue with a shared-memory load), the previous strip's
+// boundary words (cp.async, same distance), and this strip's boundary words
+// (lane G-1 stores one word per step and writes each completed aligned
+// group of four to global memory with one 16-byte store).
 //
 // Every lane runs the same instruction stream on every step: columns outside
 // a lane's range, idle groups and rows past the end of the query are
@@ -30,15 +37,14 @@
 // column leaves H = 0 and E = go, which gives the same first real column as
 // the E = -infinity boundary.
 //
-// Recurrence (Section II-B.1, Fig. 8), per cell, six max-plus instructions:
-//   E  = viaddmax(E, ge, Hg_left)          E = max(E + ge, H_left + go)
-//   F  = viaddmax(F_up, ge, Hg_up)         F = max(F_up + ge, H_up + go)
-//   T  = viaddmax(Hg_diag, s - go, E)      T = max(H_diag + s, E)
-//   H  = vimax_relu(T, F)                  H = max(T, F, 0)
-//   Hg = H + go
-//   K  = viaddmax(H, 65535 - j, K)         end-cell key of the row
-// Only Hg = H + go is stored per row; the profile holds s - go so the
-// diagonal term needs no extra add.  All scores are scaled by 2^16, so
+// Recurrence (Section II-B.1, Fig. 8), per cell, six instructions, E and F
+// held minus go so that the row-to-row chain is two instructions deep:
+//   E'  = viaddmax(E', ge, H_left)               E' = max(E' + ge, H_left)
+//   T   = viaddmax(H_diag, s - go, E') + go      T  = max(H_diag + s, E)
+//   F'  = viaddmax(F'_up, ge, H_up)              F' = max(F'_up + ge, H_up)
+//   H   = viaddmax_relu(F', go, T)               H  = max(F, T, 0)
+//   K   = viaddmax(H, 65535 - j, K)              end-cell key of the row
+// The profile holds s - go.  All scores are scaled by 2^16, so
 // K = (H << 16) | (65535 - j) orders cells by larger H, then smaller column,
 // at one instruction per cell; rows are compared in ascending order with a
 // strict "greater" so the smaller row wins ties.  The plan sends a pair
@@ -57,7 +63,23 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef SWGB_GROUP_UNROLL
 #define SWGB_GROUP_UNROLL 4
 #endif
-constexpr int kU = SWGB_GROUP_UNROLL;  // steps per block; loads run one block ahead
+constexpr int kU = SWGB_GROUP_UNROLL;  // steps per block
+static_assert(kU == 4, "the staging rings move 4 columns (16 bytes of boundary) per block");
+constexpr int kAhead = 3;              // blocks between a cp.async and the first use
+constexpr int kMaxGroups = 32 >> kMinLog2G;
+constexpr int kRingBytes = 128;        // per group and ring
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Sign-extended int8 byte B of w, moved to bits 16..31 (value << 16).
 template <int B>
@@ -70,8 +92,8 @@ __device__ __forceinline__ int byte_hi(uint32_t w) {
 
 // Profile of one lane: for residue c in [0, A] (A = pad) and the lane's R
 // rows, (s(q_row, c) - go) << 16, or a pad score for rows past the query.
-// Layout [c][chunk][lane] of 16-byte chunks: conflict-free 128-bit loads
-// whatever residue each lane asks for.
+// Layout [c][chunk][lane]: conflict-free loads whatever residue each lane
+// asks for.
 template <int R, bool P8>
 __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_t *a, int dir,
                                               int row0, int nrows, const int8_t *smat, int A,
@@ -84,7 +106,7 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
     }
     for (int c = 0; c <= A; ++c) {
         if constexpr (P8) {
-            static_assert(R == 16 || R == 8, "int8 profile holds 8 or 16 rows per lane");
+            static_assert(R == 8 || R == 16 || R == 32, "int8 profile holds 8, 16 or 32 rows");
             uint32_t w[R / 4];
 #pragma unroll
             for (int k = 0; k < R / 4; ++k) w[k] = 0u;
@@ -93,12 +115,15 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
                 const int v = (qa[r] >= 0 && c < A) ? (int)smat[qa[r] + c] - go : -128;
                 w[r >> 2] |= (uint32_t)(uint8_t)(int8_t)v << (8 * (r & 3));
             }
-            if constexpr (R == 16)
-                *reinterpret_cast<uint4 *>(prof + ((size_t)c * 32 + lane) * 16) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
-            else
+            if constexpr (R == 8) {
                 *reinterpret_cast<uint2 *>(prof + ((size_t)c * 32 + lane) * 8) =
                     make_uint2(w[0], w[1]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < R / 16; ++k)
+                    *reinterpret_cast<uint4 *>(prof + (((size_t)c * (R / 16) + k) * 32 + lane) * 16) =
+                        make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < R / 4; ++k) {
@@ -120,16 +145,20 @@ template <int R, bool P8>
 __device__ __forceinline__ void load_scores(const char *prof, int c, int lane, int (&sc)[R]) {
     if constexpr (P8) {
         uint32_t ws[R / 4];
-        if constexpr (R == 16) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(prof + ((size_t)c * 32 + lane) * 16);
-            ws[0] = w.x;
-            ws[1] = w.y;
-            ws[2] = w.z;
-            ws[3] = w.w;
-        } else {
+        if constexpr (R == 8) {
             const uint2 w = *reinterpret_cast<const uint2 *>(prof + ((size_t)c * 32 + lane) * 8);
             ws[0] = w.x;
             ws[1] = w.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < R / 16; ++k) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(
+                    prof + (((size_t)c * (R / 16) + k) * 32 + lane) * 16);
+                ws[4 * k] = w.x;
+                ws[4 * k + 1] = w.y;
+                ws[4 * k + 2] = w.z;
+                ws[4 * k + 3] = w.w;
+            }
         }
 #pragma unroll
         for (int k = 0; k < R / 4; ++k) {
@@ -176,8 +205,11 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * R : (size_t)(A + 1) * (R / 4) * 32 * 16;
-    int8_t *smat = reinterpret_cast<int8_t *>(smem_group);
-    char *cold_base = smem_group + kMaxAlphabet * kMaxAlphabet;
+    // shared memory: rings (16-byte aligned) | matrix | cold state | profiles
+    char *rings = smem_group + (size_t)warp * 3 * kMaxGroups * kRingBytes;
+    int8_t *smat = reinterpret_cast<int8_t *>(smem_group + (size_t)kGroupWarps * 3 * kMaxGroups *
+                                                               kRingBytes);
+    char *cold_base = reinterpret_cast<char *>(smat) + kMaxAlphabet * kMaxAlphabet;
     char *prof = cold_base + (size_t)kColdWords * 4 * NT + warp * prof_bytes;
     Cold cold;
     cold.a = reinterpret_cast<const uint8_t **>(cold_base);
@@ -210,35 +242,68 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         const int G = 1 << log2g;
         const int gl = lane & (G - 1);
         const int gbase = lane & ~(G - 1);
+        const int gid = lane >> log2g;
         const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
+        uint8_t *res_ring = reinterpret_cast<uint8_t *>(rings) + gid * kRingBytes;
+        uint32_t *bin_ring =
+            reinterpret_cast<uint32_t *>(rings + kMaxGroups * kRingBytes + gid * kRingBytes);
+        uint32_t *bout_ring =
+            reinterpret_cast<uint32_t *>(rings + 2 * kMaxGroups * kRingBytes + gid * kRingBytes);
 
-        // hot state: DP registers, the strip's step counters and pointers
+        // hot state: DP registers, the strip's step counters and stream cursors
         int H[R], E[R];
         uint32_t K[R];
         int diag0 = 0, outH = 0, outF = kScaledNegInf;
         int s = 0, lim = 0, stop = 0, dir = 1;
-        const uint8_t *bcol = p.r;
+        const uint8_t *bcol = p.r;  // column 0 of the current sweep
+        int roff = 0;               // bcol's offset in its 16-byte chunk (mirrored if dir < 0)
+        int rc_next = 0, rc_last = -1;  // next residue chunk to fetch, last useful one
+        int bi_next = 0, bi_last = -1;  // same for boundary-in chunks (4 words each)
+        int bo_done = 0;                // boundary-out words written so far
         const uint32_t *bin = p.scratch;
         uint32_t *bout = p.scratch;
         bool has_in = false, has_out = false;
-        bool live = false, rev = false, drained = false, reload = true;
-        int cur_c[kU], nxt_c[kU];
-        uint32_t cur_b[kU], nxt_b[kU];
+        bool live = false, rev = false, drained = false;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             H[r] = 0;
             E[r] = kScaledNegInf;
             K[r] = 0u;
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            cur_c[u] = nxt_c[u] = A;
-            cur_b[u] = nxt_b[u] = 0u;
-        }
         cold.id[t] = -1;
 
+        // Issues the cp.async copies that are due: residue chunks up to the
+        // one holding column `upto`, boundary-in chunks up to column `upto`.
+        // Only lane 0 of a group copies; every lane keeps the cursors.
+        auto fetch_ahead = [&](int upto) {
+            const int rc_want = min((roff + upto) >> 4, rc_last);
+            while (rc_next <= rc_want) {
+                if (gl == 0) {
+                    const uint8_t *base =
+                        reinterpret_cast<const uint8_t *>((uintptr_t)bcol & ~(uintptr_t)15);
+                    const uint8_t *src = base + (ptrdiff_t)(dir > 0 ? rc_next : -rc_next) * 16;
+                    cp_async16(res_ring + (((uintptr_t)src >> 4) & 7) * 16, src);
+                }
+                ++rc_next;
+            }
+            const int bi_want = min(upto >> 2, bi_last);
+            while (bi_next <= bi_want) {
+                if (gl == 0) cp_async16(bin_ring + (bi_next & 7) * 4, bin + bi_next * 4);
+                ++bi_next;
+            }
+        };
+        // Writes boundary-out words [bo_done, upto) (whole 4-word groups,
+        // upto a multiple of 4) from the ring to global memory.
+        auto flush_out = [&](int upto) {
+            while (bo_done < upto) {
+                if (gl == G - 1)
+                    *reinterpret_cast<uint4 *>(bout + bo_done) =
+                        *reinterpret_cast<const uint4 *>(bout_ring + (bo_done & 31));
+                bo_done += 4;
+            }
+        };
         // Starts strip ps of the current sweep: profile of this lane's rows,
-        // fresh DP state, boundary buffers of the strip.
+        // fresh DP state, stream cursors; waits for the strip's first data.
         auto begin_strip = [&](int ps) {
             const int n = cold.n[t], m = cold.m[t];
             build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n, smat, A, go);
@@ -253,13 +318,21 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             outF = kScaledNegInf;
             s = 0;
             lim = stop + G - 1;
+            const int m4 = (m + 3) & ~3;
             uint32_t *bnd = cold.bnd[t];
-            bin = bnd + ((ps + 1) & 1) * m;
-            bout = bnd + (ps & 1) * m;
+            bin = bnd + ((ps + 1) & 1) * m4;
+            bout = bnd + (ps & 1) * m4;
             has_in = ps > 0;
             has_out = ps + 1 < cold.passes[t];
+            rc_next = 0;
+            bi_next = 0;
+            bi_last = has_in ? (stop - 1) >> 2 : -1;
+            bo_done = 0;
             cold.ps[t] = ps;
-            reload = true;
+            fetch_ahead(kAhead * kU + kU - 1);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp(gmask);
         };
         // Starts a sweep over (a, n) x (b, m) in direction d.
         auto begin_sweep = [&](const uint8_t *a, const uint8_t *b, int n, int m, int d) {
@@ -272,6 +345,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             cold.passes[t] = passes;
             cold.best_key[t] = 0u;
             cold.best_row[t] = 0x7fffffff;
+            const int b15 = (int)((uintptr_t)b & 15);
+            roff = d > 0 ? b15 : 15 - b15;
+            rc_last = m > 0 ? (roff + m - 1) >> 4 : -1;
             if (passes > 0) {
                 stop = m;
                 begin_strip(0);
@@ -280,6 +356,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 s = 0;
                 lim = 0;
                 has_in = has_out = false;
+                bi_last = -1;
                 cold.ps[t] = 0;
             }
         };
@@ -305,29 +382,26 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
 
             const int mcols = live ? stop : 0;
 
-            // ---- residue codes and boundary words: this block (if stale), next block
-            if (reload) {
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const int j = s + u - gl;
-                    const bool in = (unsigned)j < (unsigned)mcols;
-                    cur_c[u] = in ? min((int)bcol[(ptrdiff_t)j * dir], A - 1) : A;
-                    cur_b[u] = (in && gl == 0 && has_in) ? bin[j] : 0u;
-                }
-                reload = false;
-            }
+            // ---- staging: copies for kAhead blocks ahead, then wait for this block's
+            fetch_ahead(s + kAhead * kU + kU - 1);
+            cp_async_commit();
+            cp_async_wait<kAhead>();
+            __syncwarp();
+
+            int cres[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int j = s + kU + u - gl;
+                const int j = s + u - gl;
                 const bool in = (unsigned)j < (unsigned)mcols;
-                nxt_c[u] = in ? min((int)bcol[(ptrdiff_t)j * dir], A - 1) : A;
-                nxt_b[u] = (in && gl == 0 && has_in) ? bin[j] : 0u;
+                const int byte = res_ring[((uint32_t)(uintptr_t)bcol + j * dir) & (kRingBytes - 1)];
+                cres[u] = in ? min(byte, A - 1) : A;
             }
+            uint4 bw = make_uint4(0xC0000000u, 0xC0000000u, 0xC0000000u, 0xC0000000u);
+            if (gl == 0 && has_in && s < mcols)
+                bw = *reinterpret_cast<const uint4 *>(bin_ring + ((s >> 2) & 7) * 4);
+            const uint32_t bws[kU] = {bw.x, bw.y, bw.z, bw.w};
 
-            // ---- U wavefront steps, the same instructions on every lane.  E and F
-            // are held minus go, so the row-to-row chain is two instructions:
-            //   F'_r = max(F'_{r-1} + ge, H_{r-1})        E'_r = max(E'_r + ge, H_left)
-            //   T    = max(H_diag + (s - go), E'_r) + go  H_r  = max(F'_r + go, T, 0)
+            // ---- U wavefront steps, the same instructions on every lane
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int j = s + u - gl;
@@ -335,14 +409,15 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 int inH = __shfl_up_sync(kFull, outH, 1, G);
                 int inF = __shfl_up_sync(kFull, outF, 1, G);
                 if (gl == 0) {
-                    const bool from_bnd = in && has_in;
-                    inH = from_bnd ? (int)(cur_b[u] << 16) : 0;
-                    inF = from_bnd ? (int)(cur_b[u] & 0xFFFF0000u) : kScaledNegInf;
+                    // previous strip's last row, or H = 0 / F' = -inf above the
+                    // first strip and outside the columns (0xC000 = -16384 << 16)
+                    const uint32_t w = in ? bws[u] : 0xC0000000u;
+                    inH = (int)(w << 16);
+                    inF = (int)(w & 0xFFFF0000u);
                 }
-                int c = in ? cur_c[u] : A;
-                // tie this step's profile loads to its shuffle result, so the
-                // compiler cannot hoist every unrolled step's loads (and their
-                // registers) to the top of the block
+                int c = cres[u];
+                // keep this step's profile loads after its shuffle, so the
+                // compiler does not hoist every unrolled step's loads
                 asm volatile("" : "+r"(c) : "r"(inH));
                 int sc[R];
                 load_scores<R, P8>(prof, c, lane, sc);
@@ -363,16 +438,16 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 }
                 outH = hprev;
                 outF = F;
-                if (in && has_out && gl == G - 1)
-                    bout[j] = ((uint32_t)outH >> 16) | ((uint32_t)outF & 0xFFFF0000u);
+                if (gl == G - 1 && has_out && in)
+                    bout_ring[j & 31] = ((uint32_t)outH >> 16) | ((uint32_t)outF & 0xFFFF0000u);
                 diag0 = inH;
             }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                cur_c[u] = nxt_c[u];
-                cur_b[u] = nxt_b[u];
-            }
             s += kU;
+            if (has_out) {
+                // words of the columns below s - G + 1 are complete
+                const int done = (s - G + 1) & ~3;
+                flush_out(min(done, (mcols + 3) & ~3));
+            }
 
             // ---- reverse sweep: stop once a cell of the forward score has appeared
             if (rev && live && ((s & (2 * kU - 1)) == 0)) {
@@ -391,6 +466,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
 
             // ---- end of a strip / sweep
             if (live && s >= lim) {
+                if (has_out) flush_out((mcols + 3) & ~3);
                 const int ps = cold.ps[t], passes = cold.passes[t];
                 uint32_t best_key = cold.best_key[t];
                 int best_row = cold.best_row[t];
@@ -405,8 +481,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 }
                 cold.best_key[t] = best_key;
                 cold.best_row[t] = best_row;
+                // boundary words stored by lane G-1 are read by lane 0's copies
+                // of the next strip; no copy may still be in flight into a ring
+                if (has_out) __threadfence();
+                cp_async_wait<0>();
+                __syncwarp(gmask);
                 if (ps + 1 < passes) {
-                    __syncwarp(gmask);  // boundary words written by lane G-1 -> lane 0
                     begin_strip(ps + 1);
                 } else {
                     for (int off = 1; off < G; off <<= 1) {
@@ -429,7 +509,6 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             cold.target[t] = S;
                             rev = true;
                             done = false;
-                            __syncwarp(gmask);
                             begin_sweep(cold.a[t] + qend, bcol + rend, qend + 1, rend + 1, -1);
                         }
                     }
@@ -458,11 +537,16 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                         live = false;
                         rev = false;
                         stop = 0;
+                        has_in = has_out = false;
+                        rc_last = -1;
+                        bi_last = -1;
                         __syncwarp(gmask);
                     }
                 }
             }
         }
+        cp_async_wait<0>();
+        __syncwarp();
     }
 }
 
@@ -470,8 +554,8 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
     const size_t per_warp = kind == ProfileKind::kInt8
                                 ? (size_t)(alphabet + 1) * 32 * kRows
                                 : (size_t)(alphabet + 1) * (kRows / 4) * 32 * 16;
-    return kMaxAlphabet * kMaxAlphabet + (size_t)kColdWords * 4 * kGroupWarps * 32 +
-           kGroupWarps * per_warp;
+    return (size_t)kGroupWarps * 3 * kMaxGroups * kRingBytes + kMaxAlphabet * kMaxAlphabet +
+           (size_t)kColdWords * 4 * kGroupWarps * 32 + kGroupWarps * per_warp;
 }
 
 int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes) {

@@ -1,4 +1,6 @@
 // Host planning of the persistent kernel: lane-group widths and warp shares.
+// Groups have at least 2 lanes (kMinLog2G): the kernel's per-group staging
+// buffers are sized for at most 16 groups per warp.
 //
 // A pair aligned by a group of G lanes with R rows per lane takes
 // ceil(n / (G R)) strips of (m + G - 1) wavefront steps (rounded up to the
@@ -152,14 +154,15 @@ std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n
                                        int narrow_log2g_hint, double cap_fraction_hint) {
     if (pairs.empty()) return {};
     n_warps = std::max(1, n_warps);
-    if (narrow_log2g_hint >= 0) return build(pairs, n_warps, narrow_log2g_hint, cap_fraction_hint);
+    if (narrow_log2g_hint >= 0)
+        return build(pairs, n_warps, std::max(narrow_log2g_hint, kMinLog2G), cap_fraction_hint);
     // a deterministic sample for the simulation
     std::vector<int> sample;
     const size_t step = std::max<size_t>(1, pairs.size() / 8192);
     for (size_t k = 0; k < pairs.size(); k += step) sample.push_back((int)k);
     Candidate best;
     bool have = false;
-    for (int gn = 0; gn <= 3; ++gn) {
+    for (int gn = kMinLog2G; gn <= 3; ++gn) {
         for (double frac : {0.25, 0.5, 1.0}) {
             Candidate c;
             c.classes = build(pairs, n_warps, gn, frac);

@@ -174,7 +174,7 @@ extern "C" int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_off
             PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
             if (n[i] > G * kRows && m[i] > 0) {
                 pi.scratch = words;
-                words += 2 * (int64_t)m[i];
+                words += boundary_words(m[i]);
             }
             pairs.push_back(pi);
         }

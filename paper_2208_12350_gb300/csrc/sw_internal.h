@@ -50,7 +50,8 @@ struct ClassInfo {
     int32_t log2g;
     int32_t warp_begin;  // warps [warp_begin, next class's warp_begin) start here
 };
-constexpr int kMaxClasses = 6;  // G = 32, 16, 8, 4, 2, 1
+constexpr int kMaxClasses = 6;  // G = 32, 16, 8, 4, 2 (1 unused)
+constexpr int kMinLog2G = 1;    // narrowest lane group: 2 lanes, 16 groups per warp
 
 struct Outputs {
     int32_t *score, *qend, *rend, *qstart, *rstart;
@@ -83,6 +84,12 @@ struct PlainParams {
     int32_t gap_open, gap_extend;
     int8_t mat[kMaxAlphabet * kMaxAlphabet];
 };
+
+// Strip-boundary words a pair needs when its query spans more than one row
+// strip: two buffers (previous strip's last row / this strip's last row) of
+// m rounded up to a multiple of 4 words, 16-byte aligned, plus 4 words of
+// tail so that a 16-byte chunk read past the last column stays inside.
+inline int64_t boundary_words(int m) { return 2 * (int64_t)((m + 3) & ~3) + 4; }
 
 // Device status bits.
 constexpr int32_t kStatusReverseMismatch = 1;  // reverse pass lost the score
