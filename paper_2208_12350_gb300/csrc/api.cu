@@ -256,7 +256,6 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
         n[i] = (int32_t)a;
         m[i] = (int32_t)b;
     }
-    const bool gaps_scaled_ok = -gap_open <= kMaxScaledGap && -gap_extend <= kMaxScaledGap;
 
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
@@ -284,8 +283,7 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     gp_pairs.reserve(n_pairs);
     int plain_max_n = 0;
     for (int32_t i = 0; i < n_pairs; ++i) {
-        const bool scaled = gaps_scaled_ok &&
-                            (smax <= 0 || (int64_t)smax * std::min(n[i], m[i]) <= kMaxScaledScore);
+        const bool scaled = group_path_eligible(n[i], m[i], smax, gap_open, gap_extend);
         if (mode == SW_MODE_PLAIN || !scaled) {
             PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
             plain.push_back(pi);

@@ -43,13 +43,15 @@
 //   T   = viaddmax(H_diag, s - go, E') + go      T  = max(H_diag + s, E)
 //   F'  = viaddmax(F'_up, ge, H_up)              F' = max(F'_up + ge, H_up)
 //   H   = viaddmax_relu(F', go, T)               H  = max(F, T, 0)
-//   K   = viaddmax(H, 65535 - j, K)              end-cell key of the row
+//   K   = viaddmax(H, kColBase - j, K)           end-cell key of the row
 // The profile holds s - go.  All scores are scaled by 2^16, so
-// K = (H << 16) | (65535 - j) orders cells by larger H, then smaller column,
+// K = (H << 16) | (kColBase - j) orders cells by larger H, then smaller column,
 // at one instruction per cell; rows are compared in ascending order with a
 // strict "greater" so the smaller row wins ties.  The plan sends a pair
-// here only when smax * min(n, m) <= 32766 and |go|, |ge| <= 16383, which
-// keeps every scaled value and key inside int32.
+// here only when smax * min(n, m) <= 32766, |go|, |ge| <= 16383 and
+// m <= kColBase, which keeps every scaled value and key inside int32 and the
+// column part in [0, 65535) also on the pad columns a lane computes before
+// its first column (j >= -31).
 //
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
 // a_qend..a_0 and b_rend..b_0.  Every 2U steps the group looks for a cell of
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 asm volatile("" : "+r"(c) : "r"(inH));
                 int sc[R];
                 load_scores<R, P8>(prof, c, lane, sc);
-                const int cj = 65535 - max(j, 0);
+                const int cj = kColBase - j;
                 int diag = diag0;
                 int F = __viaddmax_s32(inF, geS, inH);
                 int hprev = 0;
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 outH = hprev;
                 outF = F;
                 if (gl == G - 1 && has_out && in)
-                    bout_ring[j & 31] = ((uint32_t)outH >> 16) | ((uint32_t)outF & 0xFFFF0000u);
+                    bout_ring[j & 31] = __byte_perm((uint32_t)outH, (uint32_t)outF, 0x7632);
                 diag0 = inH;
             }
             s += kU;
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 uint32_t lk = K[0];
 #pragma unroll
                 for (int r = 1; r < R; ++r) lk = max(lk, K[r]);
-                int found = (int)(lk >> 16) >= target ? 65535 - (int)(lk & 0xFFFFu) : 0x7fffffff;
+                int found = (int)(lk >> 16) >= target ? kColBase - (int)(lk & 0xFFFFu) : 0x7fffffff;
                 for (int off = 1; off < G; off <<= 1)
                     found = min(found, __shfl_xor_sync(gmask, found, off, G));
                 if (found != 0x7fffffff && found + 1 < stop) {
@@ -501,7 +503,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     if (!rev) {
                         const int S = (int)(best_key >> 16);
                         const int qend = best_row;
-                        const int rend = 65535 - (int)(best_key & 0xFFFFu);
+                        const int rend = kColBase - (int)(best_key & 0xFFFFu);
                         cold.S[t] = S;
                         if (S > 0) {
                             cold.qend[t] = qend;
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             if (S > 0) {
                                 const int qend = cold.qend[t], rend = cold.rend[t];
                                 const int S2 = (int)(best_key >> 16);
-                                const int l = 65535 - (int)(best_key & 0xFFFFu);
+                                const int l = kColBase - (int)(best_key & 0xFFFFu);
                                 if (S2 != S) atomicOr(p.status, kStatusReverseMismatch);
                                 o0 = S;
                                 o1 = qend;

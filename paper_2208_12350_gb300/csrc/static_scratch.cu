@@ -133,15 +133,13 @@ extern "C" int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_off
 
     ProfileKind kind = ProfileKind::kInt32;
     if (A > 4 && smax - gap_open <= 127 && smin - gap_open >= -127) kind = ProfileKind::kInt8;
-    const bool gaps_scaled_ok = -gap_open <= kMaxScaledGap && -gap_extend <= kMaxScaledGap;
 
     std::vector<PlanPair> gp;
     std::vector<int32_t> gid;
     std::vector<PairInfo> plain;
     int plain_max_n = 0;
     for (int32_t i = 0; i < n_pairs; ++i) {
-        const bool scaled = gaps_scaled_ok &&
-                            (smax <= 0 || (int64_t)smax * std::min(n[i], m[i]) <= kMaxScaledScore);
+        const bool scaled = group_path_eligible(n[i], m[i], smax, gap_open, gap_extend);
         if (!scaled) {
             plain.push_back({q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0});
             plain_max_n = std::max(plain_max_n, n[i]);

@@ -17,6 +17,10 @@ constexpr int32_t kScaledNegInf = -(1 << 30);  // E/F "-infinity", scaled domain
 constexpr int32_t kPlainNegInf = -(1 << 30);   // E/F "-infinity", plain int32
 constexpr int32_t kScaledPad = -(1 << 29);     // profile score of rows beyond n
 constexpr int kMaxScaledScore = 32766;         // (S << 16) + 65535 < 2^31
+// Column part of the end-cell key: kColBase - j.  Lanes start up to 31
+// columns early (pad columns, j >= -31), so references of the batched path
+// are limited to kColBase residues to keep the part in [0, 65535).
+constexpr int kColBase = 65503;
 constexpr int kMaxScaledGap = 16383;
 constexpr int kMaxAlphabet = 32;
 #ifndef SWGB_ROWS
@@ -90,6 +94,14 @@ struct PlainParams {
 // m rounded up to a multiple of 4 words, 16-byte aligned, plus 4 words of
 // tail so that a 16-byte chunk read past the last column stays inside.
 inline int64_t boundary_words(int m) { return 2 * (int64_t)((m + 3) & ~3) + 4; }
+
+// Whether a pair can take the batched kernel's scaled int32 arithmetic.
+inline bool group_path_eligible(int n, int m, int smax, int gap_open, int gap_extend) {
+    if (-gap_open > kMaxScaledGap || -gap_extend > kMaxScaledGap) return false;
+    if (m > kColBase) return false;
+    const int64_t bound = (int64_t)(smax > 0 ? smax : 0) * (n < m ? n : m);
+    return bound <= kMaxScaledScore;
+}
 
 // Device status bits.
 constexpr int32_t kStatusReverseMismatch = 1;  // reverse pass lost the score

@@ -111,14 +111,15 @@ def test_static_entry_rejects_oversize_batches(gpu_lib):
     with pytest.raises(swgb.SwError) as e:
         swgb.sw_align_batch_static(seq, offs, seq, offs, wl.dna_matrix(), -6, -1, out)
     assert e.value.code == swgb.SW_ERANGE and "split the batch" in str(e.value)
-    # 70 pairs with queries longer than any row strip and 65,535-residue
-    # references need 70 x 2 x 65,535 boundary words, above the fixed scratch
+    # 70 pairs with queries longer than any row strip and 65,000-residue
+    # references need about 70 x 2 x 65,000 boundary words, above the fixed
+    # scratch
     k = 70
     qo = np.arange(k + 1, dtype=np.int64) * 2000
-    ro = np.arange(k + 1, dtype=np.int64) * 65535
+    ro = np.arange(k + 1, dtype=np.int64) * 65000
     qs = torch.zeros(int(qo[-1]), dtype=torch.uint8, device=dev)
     rs = torch.zeros(int(ro[-1]), dtype=torch.uint8, device=dev)
-    assert 2 * 65535 * k > swgb.SW_STATIC_MAX_BOUNDARY_WORDS
+    assert 2 * 65000 * k > swgb.SW_STATIC_MAX_BOUNDARY_WORDS
     with pytest.raises(swgb.SwError) as e:
         swgb.sw_align_batch_static(qs, qo, rs, ro, wl.dna_matrix(), -6, -1,
                                    torch.zeros((5, k), dtype=torch.int32, device=dev))
