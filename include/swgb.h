@@ -158,6 +158,25 @@ int sw_plan_info(const sw_plan *plan, int32_t *n_group_pairs, int32_t *n_plain,
 int sw_plan_destroy(sw_plan *plan);
 
 /*
+ * Measured tuning of the batched path for a batch (blocking).  Runs the
+ * batch - offsets and score_matrix on the HOST as for sw_plan_create,
+ * q_seqs/r_seqs on the DEVICE, `out` a DEVICE scratch array of 5 x n_pairs
+ * int32 that receives the results - once per candidate tuning (bulk
+ * lane-group width 2, 4 or 8 with long-pair caps 0.25, 0.5, 1 or none, and
+ * the planner's own choice), keeps the fastest and sets it on ctx with
+ * sw_ctx_set_tuning.  With a non-NULL cache_path the choice is looked up
+ * first and stored after measuring in that JSON file, keyed by GPU name, SM
+ * count and a signature of the batch (pair count, length sums, maxima and
+ * histograms, scoring); a hit skips the measurement.  Outputs (may be
+ * NULL): the chosen narrow_log2g and cap_fraction and its time in ms.
+ */
+int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                int32_t gap_open, int32_t gap_extend, const uint8_t *q_seqs,
+                const uint8_t *r_seqs, int32_t *out, const char *cache_path, void *stream,
+                int32_t *chosen_log2g, double *chosen_frac, double *chosen_ms);
+
+/*
  * One-shot alignment of a batch whose sequences AND offsets are on the
  * DEVICE (score_matrix on the HOST).  Reads the offsets back to plan the
  * batch, which synchronises `stream` once, then enqueues the work on
@@ -226,6 +245,45 @@ int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_offsets,
                           int32_t gap_open, int32_t gap_extend,
                           int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
                           int32_t *out_qstart, int32_t *out_rstart, void *stream);
+
+/*
+ * Serving: continuous batching of alignment requests (one device, blocking
+ * calls are bounded by timeouts).
+ *
+ * sw_server_create: a server on ctx's device with a device-memory budget of
+ * budget_bytes (allocated once, at creation, as the arena that holds every
+ * admitted request's sequences, tables, scratch and outputs), `streams`
+ * requests at most on the GPU at a time (one stream each, 1..64), and a
+ * pinned host staging pool of staging_bytes.  A worker thread admits queued
+ * requests in arrival order whenever a stream slot is free and the
+ * request's device bytes fit in what the arena has left, launches it on its
+ * slot's stream (so requests overlap on the device) and retires it when its
+ * completion event fires.
+ *
+ * sw_server_submit: queue a request given as HOST arrays (sequences,
+ * offsets, matrix; copied into the staging pool before the call returns, so
+ * the caller may reuse them).  Waits up to timeout_ms for staging space.
+ * Errors: SW_EINVAL/SW_ERANGE as sw_plan_create; SW_EBUDGET if the request
+ * alone needs more than the whole budget or staging pool; SW_ETIMEOUT.
+ *
+ * sw_server_wait: wait up to timeout_ms for a request, copy its results to
+ * out_host (5 x n_pairs int32: scores, qend, rend, qstart, rstart) and
+ * forget it.  SW_ETIMEOUT leaves it pending (wait again later).
+ *
+ * Results equal those of sw_plan_execute on the same batch.
+ */
+typedef struct sw_server sw_server;
+int sw_server_create(sw_ctx *ctx, int64_t budget_bytes, int32_t streams, int64_t staging_bytes,
+                     sw_server **out);
+int sw_server_submit(sw_server *server, const uint8_t *q_seqs, const int64_t *q_offsets,
+                     const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                     const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                     int32_t gap_extend, int32_t timeout_ms, int64_t *request_id);
+int sw_server_poll(sw_server *server, int64_t request_id, int32_t *done);
+int sw_server_wait(sw_server *server, int64_t request_id, int32_t timeout_ms, int32_t *out_host);
+int sw_server_stats(sw_server *server, int64_t *completed, int64_t *in_flight, int64_t *queued,
+                    int64_t *device_bytes_in_use, int64_t *device_bytes_peak);
+int sw_server_destroy(sw_server *server);
 
 /*
  * Integer issue-rate microbenchmark on `device` (made current for the call;

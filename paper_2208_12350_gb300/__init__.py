@@ -49,6 +49,17 @@ SIGNATURES = {
     "sw_check_residues": ([_P, _I64, _I32, _P, _P], ctypes.c_int),
     "sw_align_batch_static": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
                               ctypes.c_int),
+    "sw_autotune": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, ctypes.c_char_p, _P,
+                     ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
+                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sw_server_create": ([_P, _I64, _I32, _I64, _PP], ctypes.c_int),
+    "sw_server_submit": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32,
+                          ctypes.POINTER(_I64)], ctypes.c_int),
+    "sw_server_poll": ([_P, _I64, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_server_wait": ([_P, _I64, _I32, _P], ctypes.c_int),
+    "sw_server_stats": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                         ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "sw_server_destroy": ([_P], ctypes.c_int),
     "sw_microbench_int": ([_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -186,6 +197,20 @@ def sw_plan_destroy(plan: int) -> None:
     _check(load().sw_plan_destroy(plan), "sw_plan_destroy")
 
 
+def sw_autotune(ctx: int, q_offsets, r_offsets, score_matrix, gap_open: int, gap_extend: int,
+                q_seqs, r_seqs, out, cache_path: str | None = None, stream=None) -> dict:
+    """Measure the candidate tunings on a resident batch; sets the best on ctx."""
+    qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
+    mat = _host_i8(score_matrix)
+    lg, frac, ms = _I32(), ctypes.c_double(), ctypes.c_double()
+    _check(load().sw_autotune(ctx, qo.ctypes.data, ro.ctypes.data, len(qo) - 1, mat.ctypes.data,
+                              mat.shape[0], gap_open, gap_extend, _addr(q_seqs), _addr(r_seqs),
+                              _addr(out), cache_path.encode() if cache_path else None,
+                              _stream(stream), ctypes.byref(lg), ctypes.byref(frac),
+                              ctypes.byref(ms)), "sw_autotune")
+    return {"narrow_log2g": lg.value, "cap_fraction": frac.value, "ms": ms.value}
+
+
 # ---------------------------------------------------------------- one-shot
 
 def sw_align_batch(q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, gap_open: int,
@@ -244,6 +269,55 @@ def sw_microbench_int(op: str, device: int = 0, iters: int = 4096) -> tuple[floa
     _check(load().sw_microbench_int(MICROBENCH_OPS[op], device, iters, ctypes.byref(rate),
                                     ctypes.byref(secs)), "sw_microbench_int")
     return rate.value, secs.value
+
+
+# ----------------------------------------------------------------- serving
+
+def sw_server_create(ctx: int, budget_bytes: int, streams: int = 8,
+                     staging_bytes: int = 1 << 30) -> int:
+    h = ctypes.c_void_p()
+    _check(load().sw_server_create(ctx, budget_bytes, streams, staging_bytes, ctypes.byref(h)),
+           "sw_server_create")
+    return h.value
+
+
+def sw_server_submit(server: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix,
+                     gap_open: int, gap_extend: int, timeout_ms: int = 60000) -> int:
+    """Host arrays in; returns the request id."""
+    q = np.ascontiguousarray(q_seqs, dtype=np.uint8)
+    r = np.ascontiguousarray(r_seqs, dtype=np.uint8)
+    qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
+    mat = _host_i8(score_matrix)
+    rid = _I64()
+    _check(load().sw_server_submit(server, q.ctypes.data if q.size else None, qo.ctypes.data,
+                                   r.ctypes.data if r.size else None, ro.ctypes.data, len(qo) - 1,
+                                   mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
+                                   timeout_ms, ctypes.byref(rid)), "sw_server_submit")
+    return rid.value
+
+
+def sw_server_poll(server: int, request_id: int) -> bool:
+    d = _I32()
+    _check(load().sw_server_poll(server, request_id, ctypes.byref(d)), "sw_server_poll")
+    return bool(d.value)
+
+
+def sw_server_wait(server: int, request_id: int, n_pairs: int, timeout_ms: int = 60000) -> np.ndarray:
+    """(n_pairs, 5) int32 results of a request."""
+    out = np.empty((5, n_pairs), dtype=np.int32)
+    _check(load().sw_server_wait(server, request_id, timeout_ms, out.ctypes.data), "sw_server_wait")
+    return out.T.copy()
+
+
+def sw_server_stats(server: int) -> dict:
+    v = [_I64() for _ in range(5)]
+    _check(load().sw_server_stats(server, *[ctypes.byref(x) for x in v]), "sw_server_stats")
+    return dict(zip(["completed", "in_flight", "queued", "device_bytes_in_use",
+                     "device_bytes_peak"], [x.value for x in v]))
+
+
+def sw_server_destroy(server: int) -> None:
+    _check(load().sw_server_destroy(server), "sw_server_destroy")
 
 
 # ----------------------------------------------------------------- helpers

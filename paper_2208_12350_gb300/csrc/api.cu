@@ -89,24 +89,13 @@ struct sw_plan {
     int A = 0, go = 0, ge = 0, mode = 0;
     uint32_t flags = 0;
     int8_t mat[kMaxAlphabet * kMaxAlphabet] = {0};
-    ProfileKind kind = ProfileKind::kInt32;
-    // persistent group kernel
-    PairInfo *d_pairs = nullptr;
+    HostPlan hp;        // tables (host copies) and launch shapes
+    DeviceTables dev;   // the same tables on the device
+    PairInfo *d_pairs = nullptr, *d_plain = nullptr;
     ClassInfo *d_classes = nullptr;
-    int32_t n_classes = 0;
-    int32_t n_group = 0;  // pairs on the persistent kernel
     int32_t *d_counter = nullptr;
     uint32_t *d_scratch = nullptr;
-    int64_t scratch_words = 0;
-    int grid = 0;
-    int n_warps = 0;
-    // one-block-per-pair kernel
-    PairInfo *d_plain = nullptr;
-    int32_t n_plain = 0;
-    int plain_threads = 32;
-    int plain_kmax = 1;
     // host-buffer execution: staging copies of the inputs and outputs
-    int64_t q_bytes = 0, r_bytes = 0;
     uint8_t *d_q = nullptr, *d_r = nullptr;
     int32_t *d_out = nullptr;
     // graph replay
@@ -221,181 +210,52 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     if (!out) return fail(SW_EINVAL, "sw_plan_create: out is NULL");
     *out = nullptr;
     if (!ctx) return fail(SW_EINVAL, "sw_plan_create: ctx is NULL");
-    if (n_pairs < 0) return fail(SW_EINVAL, "sw_plan_create: n_pairs < 0");
-    if (n_pairs > 0 && (!q_offsets || !r_offsets))
-        return fail(SW_EINVAL, "sw_plan_create: offsets are NULL");
-    if (!score_matrix) return fail(SW_EINVAL, "sw_plan_create: score_matrix is NULL");
-    if (alphabet_size < 1 || alphabet_size > SW_MAX_ALPHABET)
-        return fail(SW_EINVAL, "sw_plan_create: alphabet_size %d not in [1, %d]", alphabet_size,
-                    SW_MAX_ALPHABET);
-    if (gap_extend > 0 || gap_open > gap_extend)
-        return fail(SW_EINVAL,
-                    "sw_plan_create: need gap_open <= gap_extend <= 0 (got %d, %d)", gap_open,
-                    gap_extend);
-    if (gap_open < -SW_MAX_GAP) return fail(SW_EINVAL, "sw_plan_create: |gap_open| too large");
-    if (mode != SW_MODE_AUTO && mode != SW_MODE_PLAIN && mode != SW_MODE_BATCHED)
-        return fail(SW_EINVAL, "sw_plan_create: unknown mode %d", mode);
-    if (mode == SW_MODE_AUTO) mode = SW_MODE_BATCHED;
-
-    const int A = alphabet_size;
-    int smax = -128, smin = 127;
-    for (int i = 0; i < A * A; ++i) {
-        smax = std::max(smax, (int)score_matrix[i]);
-        smin = std::min(smin, (int)score_matrix[i]);
-    }
-    // lengths
-    std::vector<int32_t> n(n_pairs), m(n_pairs);
-    for (int32_t i = 0; i < n_pairs; ++i) {
-        const int64_t a = q_offsets[i + 1] - q_offsets[i];
-        const int64_t b = r_offsets[i + 1] - r_offsets[i];
-        if (q_offsets[i] < 0 || r_offsets[i] < 0 || a < 0 || b < 0)
-            return fail(SW_ERANGE, "sw_plan_create: offsets of pair %d negative or decreasing", i);
-        if (a > SW_MAX_LEN || b > SW_MAX_LEN)
-            return fail(SW_ERANGE, "sw_plan_create: pair %d has lengths (%lld, %lld) > %d", i,
-                        (long long)a, (long long)b, SW_MAX_LEN);
-        n[i] = (int32_t)a;
-        m[i] = (int32_t)b;
-    }
-
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
     reap_retired(ctx, false);
-
     auto *p = new sw_plan();
+    std::string msg;
+    int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
+                            gap_extend, mode, ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
+                            &p->hp, &msg);
+    if (rc != SW_OK) {
+        delete p;
+        return fail(rc, "sw_plan_create: %s", msg.c_str());
+    }
     p->ctx = ctx;
     p->n_pairs = n_pairs;
-    p->A = A;
+    p->A = alphabet_size;
     p->go = gap_open;
     p->ge = gap_extend;
-    p->mode = mode;
+    p->mode = mode == SW_MODE_AUTO ? SW_MODE_BATCHED : mode;
     p->flags = flags;
-    std::memcpy(p->mat, score_matrix, (size_t)A * A);
-    if (A <= 4)
-        p->kind = ProfileKind::kInt32;
-    else if (smax - gap_open <= 127 && smin - gap_open >= -127)
-        p->kind = ProfileKind::kInt8;
-    else
-        p->kind = ProfileKind::kInt32;
-
-    std::vector<PlanPair> gp_pairs;  // group-path pairs, id = index into group_ids
-    std::vector<int32_t> group_ids;
-    std::vector<PairInfo> plain;
-    gp_pairs.reserve(n_pairs);
-    int plain_max_n = 0;
-    for (int32_t i = 0; i < n_pairs; ++i) {
-        const bool scaled = group_path_eligible(n[i], m[i], smax, gap_open, gap_extend);
-        if (mode == SW_MODE_PLAIN || !scaled) {
-            PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
-            plain.push_back(pi);
-            plain_max_n = std::max(plain_max_n, n[i]);
-            continue;
-        }
-        gp_pairs.push_back({(int32_t)group_ids.size(), n[i], m[i]});
-        group_ids.push_back(i);
-    }
-    int n_warps = 0;
-    if (!gp_pairs.empty()) {
-        int smem = 0;
-        const int bps = group_blocks_per_sm(p->kind, A, &smem);
-        if (bps <= 0) {
-            plan_free(p);
-            return fail(SW_ECUDA, "sw_plan_create: group kernel does not fit (%d B smem)", smem);
-        }
-        const int64_t want = ((int64_t)gp_pairs.size() + kGroupWarps - 1) / kGroupWarps;
-        p->grid = (int)std::min<int64_t>((int64_t)bps * ctx->sm_count, want);
-        n_warps = p->grid * kGroupWarps;
-    }
-    const std::vector<PlannedClass> planned =
-        plan_classes(gp_pairs, n_warps, ctx->narrow_log2g, ctx->cap_fraction);
-    std::vector<PairInfo> pairs;
-    std::vector<ClassInfo> classes;
-    pairs.reserve(gp_pairs.size());
-    int64_t scratch = 0;
-    int warp_begin = 0;
-    for (const PlannedClass &pc : planned) {
-        classes.push_back({(int32_t)pairs.size(), (int32_t)pc.pairs.size(), pc.log2g, warp_begin});
-        warp_begin += pc.warps;
-        const int G = 1 << pc.log2g;
-        for (int32_t k : pc.pairs) {
-            const int32_t i = group_ids[k];
-            PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
-            if (n[i] > G * kRows && m[i] > 0) {
-                pi.scratch = scratch;
-                scratch += boundary_words(m[i]);
-            }
-            pairs.push_back(pi);
-        }
-    }
-    p->n_warps = n_warps;
-    p->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
-    p->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
-    p->n_classes = (int32_t)classes.size();
-    p->n_group = (int32_t)pairs.size();
-    p->n_plain = (int32_t)plain.size();
-    p->scratch_words = scratch;
-    int rc;
-    if ((rc = upload(&p->d_pairs, pairs)) || (rc = upload(&p->d_classes, classes)) ||
-        (rc = upload(&p->d_plain, plain))) {
+    std::memcpy(p->mat, score_matrix, (size_t)alphabet_size * alphabet_size);
+    if ((rc = upload(&p->d_pairs, p->hp.pairs)) || (rc = upload(&p->d_classes, p->hp.classes)) ||
+        (rc = upload(&p->d_plain, p->hp.plain))) {
         plan_free(p);
         return rc;
     }
     if (cudaMalloc(&p->d_counter, kMaxClasses * sizeof(int32_t)) != cudaSuccess ||
-        (scratch > 0 && cudaMalloc(&p->d_scratch, scratch * sizeof(uint32_t)) != cudaSuccess)) {
+        (p->hp.scratch_words > 0 &&
+         cudaMalloc(&p->d_scratch, p->hp.scratch_words * sizeof(uint32_t)) != cudaSuccess)) {
         cudaGetLastError();
         plan_free(p);
         return fail(SW_ENOMEM, "sw_plan_create: scratch allocation (%lld words) failed",
-                    (long long)scratch);
+                    (long long)p->hp.scratch_words);
     }
-    if (p->n_plain > 0) {
-        if (plain_max_n <= 1024) {
-            p->plain_threads = std::max(32, ((plain_max_n + 31) / 32) * 32);
-            p->plain_kmax = 1;
-        } else {
-            p->plain_threads = kPlainWideThreads;
-            p->plain_kmax = kPlainMaxRows;
-        }
-    }
+    p->dev.pairs = p->d_pairs;
+    p->dev.classes = p->d_classes;
+    p->dev.plain = p->d_plain;
+    p->dev.counters = p->d_counter;
+    p->dev.scratch = p->d_scratch;
+    p->dev.status = ctx->d_status;
     *out = p;
     return SW_OK;
 }
 
 static int enqueue(sw_plan *p, const uint8_t *q, const uint8_t *r, const Outputs &o,
                    cudaStream_t s) {
-    if (p->n_group > 0) {
-        SW_CUDA_TRY(cudaMemsetAsync(p->d_counter, 0, kMaxClasses * sizeof(int32_t), s));
-        GroupParams gp;
-        std::memset(&gp, 0, sizeof gp);
-        gp.q = q;
-        gp.r = r;
-        gp.pairs = p->d_pairs;
-        gp.classes = p->d_classes;
-        gp.n_classes = p->n_classes;
-        gp.counters = p->d_counter;
-        gp.n_warps = p->n_warps;
-        gp.scratch = p->d_scratch;
-        gp.status = p->ctx->d_status;
-        gp.out = o;
-        gp.alphabet = p->A;
-        gp.gap_open = p->go;
-        gp.gap_extend = p->ge;
-        std::memcpy(gp.mat, p->mat, sizeof gp.mat);
-        SW_CUDA_TRY(launch_group(gp, p->kind, p->grid, s));
-    }
-    if (p->n_plain > 0) {
-        PlainParams pp;
-        std::memset(&pp, 0, sizeof pp);
-        pp.q = q;
-        pp.r = r;
-        pp.pairs = p->d_plain;
-        pp.n_pairs = p->n_plain;
-        pp.status = p->ctx->d_status;
-        pp.out = o;
-        pp.alphabet = p->A;
-        pp.gap_open = p->go;
-        pp.gap_extend = p->ge;
-        std::memcpy(pp.mat, p->mat, sizeof pp.mat);
-        SW_CUDA_TRY(launch_plain(pp, p->plain_threads, p->plain_kmax, s));
-    }
+    SW_CUDA_TRY(enqueue_plan(p->hp, p->dev, q, r, o, p->mat, p->A, p->go, p->ge, s));
     return SW_OK;
 }
 
@@ -445,13 +305,13 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
                          int32_t *out_host, void *stream) {
     if (!p) return fail(SW_EINVAL, "sw_plan_execute_host: plan is NULL");
     if (p->n_pairs == 0) return SW_OK;
-    if ((p->q_bytes > 0 && !q_seqs) || (p->r_bytes > 0 && !r_seqs) || !out_host)
+    if ((p->hp.q_bytes > 0 && !q_seqs) || (p->hp.r_bytes > 0 && !r_seqs) || !out_host)
         return fail(SW_EINVAL, "sw_plan_execute_host: NULL host pointer");
     DeviceGuard g(p->ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", p->ctx->device);
     if (!p->d_out) {
-        if (cudaMalloc(&p->d_q, (size_t)std::max<int64_t>(p->q_bytes, 1)) != cudaSuccess ||
-            cudaMalloc(&p->d_r, (size_t)std::max<int64_t>(p->r_bytes, 1)) != cudaSuccess ||
+        if (cudaMalloc(&p->d_q, (size_t)std::max<int64_t>(p->hp.q_bytes, 1)) != cudaSuccess ||
+            cudaMalloc(&p->d_r, (size_t)std::max<int64_t>(p->hp.r_bytes, 1)) != cudaSuccess ||
             cudaMalloc(&p->d_out, (size_t)5 * p->n_pairs * sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(p->d_q);
@@ -463,10 +323,10 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->q_bytes > 0)
-        SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, p->q_bytes, cudaMemcpyHostToDevice, s));
-    if (p->r_bytes > 0)
-        SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, p->r_bytes, cudaMemcpyHostToDevice, s));
+    if (p->hp.q_bytes > 0)
+        SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, p->hp.q_bytes, cudaMemcpyHostToDevice, s));
+    if (p->hp.r_bytes > 0)
+        SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, p->hp.r_bytes, cudaMemcpyHostToDevice, s));
     const int64_t n = p->n_pairs;
     int rc = sw_plan_execute(p, p->d_q, p->d_r, p->d_out, p->d_out + n, p->d_out + 2 * n,
                              p->d_out + 3 * n, p->d_out + 4 * n, stream);
@@ -480,10 +340,10 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
 int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int32_t *launches,
                  int64_t *scratch_bytes) {
     if (!p) return fail(SW_EINVAL, "sw_plan_info: plan is NULL");
-    if (n_group_pairs) *n_group_pairs = p->n_group;
-    if (n_plain) *n_plain = p->n_plain;
-    if (launches) *launches = (p->n_group > 0 ? 1 : 0) + (p->n_plain > 0 ? 1 : 0);
-    if (scratch_bytes) *scratch_bytes = p->scratch_words * (int64_t)sizeof(uint32_t);
+    if (n_group_pairs) *n_group_pairs = (int32_t)p->hp.pairs.size();
+    if (n_plain) *n_plain = (int32_t)p->hp.plain.size();
+    if (launches) *launches = (p->hp.pairs.empty() ? 0 : 1) + (p->hp.plain.empty() ? 0 : 1);
+    if (scratch_bytes) *scratch_bytes = p->hp.scratch_words * (int64_t)sizeof(uint32_t);
     return SW_OK;
 }
 

@@ -1,0 +1,216 @@
+// sw_autotune: measured choice of the batched path's tuning for a batch.
+//
+// The planner (plan.cpp) picks lane-group widths from a cost model.  The
+// autotuner measures instead: it runs the batch under each candidate tuning
+// (bulk lane-group width G in {2, 4, 8} x long-pair cap in {0.25, 0.5, 1,
+// none}, plus the planner's own choice), keeps the fastest, sets it on the
+// context and records it in a JSON cache keyed by the GPU (name, SM count)
+// and a signature of the batch (pair count, length sums, maxima and length
+// histograms, scoring), so the next run of the same kind of batch skips the
+// measurement.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cinttypes>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "sw_internal.h"
+#include "swgb.h"
+
+namespace swgb {
+namespace {
+
+uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string batch_key(const char *gpu, int sms, const int64_t *qo, const int64_t *ro, int n_pairs,
+                      const int8_t *mat, int A, int go, int ge) {
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, gpu, std::strlen(gpu));
+    h = fnv1a(h, &sms, sizeof sms);
+    h = fnv1a(h, &n_pairs, sizeof n_pairs);
+    h = fnv1a(h, &A, sizeof A);
+    h = fnv1a(h, &go, sizeof go);
+    h = fnv1a(h, &ge, sizeof ge);
+    h = fnv1a(h, mat, (size_t)A * A);
+    int64_t sum_n = 0, sum_m = 0, max_n = 0, max_m = 0;
+    double sum_nm = 0;
+    int64_t hist_n[32] = {0}, hist_m[32] = {0};
+    for (int i = 0; i < n_pairs; ++i) {
+        const int64_t n = qo[i + 1] - qo[i], m = ro[i + 1] - ro[i];
+        sum_n += n;
+        sum_m += m;
+        sum_nm += (double)n * (double)m;
+        max_n = std::max(max_n, n);
+        max_m = std::max(max_m, m);
+        hist_n[std::min<int64_t>(31, n / 64)]++;
+        hist_m[std::min<int64_t>(31, m / 256)]++;
+    }
+    h = fnv1a(h, &sum_n, sizeof sum_n);
+    h = fnv1a(h, &sum_m, sizeof sum_m);
+    h = fnv1a(h, &sum_nm, sizeof sum_nm);
+    h = fnv1a(h, &max_n, sizeof max_n);
+    h = fnv1a(h, &max_m, sizeof max_m);
+    h = fnv1a(h, hist_n, sizeof hist_n);
+    h = fnv1a(h, hist_m, sizeof hist_m);
+    char buf[32];
+    snprintf(buf, sizeof buf, "%016" PRIx64, h);
+    return buf;
+}
+
+struct Entry {
+    std::string key;
+    int log2g = -1;
+    double frac = 0.5, ms = 0;
+};
+
+// The cache file is a JSON object {"entries": [ {...}, ... ]} with one
+// entry per line, as this file writes it.
+std::vector<Entry> read_cache(const char *path) {
+    std::vector<Entry> out;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        const size_t k = line.find("\"key\": \"");
+        if (k == std::string::npos) continue;
+        Entry e;
+        const size_t k0 = k + 8, k1 = line.find('"', k0);
+        if (k1 == std::string::npos) continue;
+        e.key = line.substr(k0, k1 - k0);
+        auto num = [&](const char *name, double &v) {
+            const size_t p = line.find(name);
+            if (p != std::string::npos) v = std::atof(line.c_str() + p + std::strlen(name));
+        };
+        double lg = -1;
+        num("\"narrow_log2g\": ", lg);
+        num("\"cap_fraction\": ", e.frac);
+        num("\"ms\": ", e.ms);
+        e.log2g = (int)lg;
+        out.push_back(e);
+    }
+    return out;
+}
+
+bool write_cache(const char *path, const std::vector<Entry> &entries, const char *gpu, int sms) {
+    const std::string tmp = std::string(path) + ".tmp";
+    std::ofstream f(tmp);
+    if (!f) return false;
+    f << "{\"gpu\": \"" << gpu << "\", \"sms\": " << sms << ", \"entries\": [\n";
+    for (size_t i = 0; i < entries.size(); ++i) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "  {\"key\": \"%s\", \"narrow_log2g\": %d, \"cap_fraction\": %.17g, \"ms\": %.17g}%s\n",
+                 entries[i].key.c_str(), entries[i].log2g, entries[i].frac, entries[i].ms,
+                 i + 1 < entries.size() ? "," : "");
+        f << buf;
+    }
+    f << "]}\n";
+    f.close();
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+}  // namespace swgb
+
+using namespace swgb;
+
+extern "C" int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                           int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                           int32_t gap_open, int32_t gap_extend, const uint8_t *q_seqs,
+                           const uint8_t *r_seqs, int32_t *out, const char *cache_path,
+                           void *stream, int32_t *chosen_log2g, double *chosen_frac,
+                           double *chosen_ms) {
+    if (!ctx || n_pairs <= 0 || !q_offsets || !r_offsets || !score_matrix || !q_seqs || !r_seqs ||
+        !out)
+        return set_error(SW_EINVAL, "sw_autotune: bad argument");
+    char gpu[256];
+    int32_t sms = 0;
+    sw_ctx_sm_count(ctx, &sms);
+    {
+        int dev = 0;
+        cudaDeviceProp prop;
+        cudaGetDevice(&dev);
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+            return set_error(SW_ECUDA, "sw_autotune: device properties");
+        snprintf(gpu, sizeof gpu, "%s", prop.name);
+    }
+    const std::string key = batch_key(gpu, sms, q_offsets, r_offsets, n_pairs, score_matrix,
+                                      alphabet_size, gap_open, gap_extend);
+    std::vector<Entry> cache;
+    if (cache_path && *cache_path) {
+        cache = read_cache(cache_path);
+        for (const Entry &e : cache)
+            if (e.key == key) {
+                const int rc = sw_ctx_set_tuning(ctx, e.log2g, e.frac);
+                if (rc != SW_OK) return rc;
+                if (chosen_log2g) *chosen_log2g = e.log2g;
+                if (chosen_frac) *chosen_frac = e.frac;
+                if (chosen_ms) *chosen_ms = e.ms;
+                return SW_OK;
+            }
+    }
+    struct Cand {
+        int lg;
+        double frac;
+    };
+    std::vector<Cand> cands = {{-1, 0.5}};
+    for (int lg = kMinLog2G; lg <= 3; ++lg)
+        for (double f : {0.25, 0.5, 1.0, 1e9}) cands.push_back({lg, f});
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_error(SW_ECUDA, "sw_autotune: event creation failed");
+    const int64_t n = n_pairs;
+    Cand best{-1, 0.5};
+    double best_ms = 1e30;
+    int rc = SW_OK;
+    for (const Cand &c : cands) {
+        if ((rc = sw_ctx_set_tuning(ctx, c.lg, c.frac)) != SW_OK) break;
+        sw_plan *plan = nullptr;
+        rc = sw_plan_create(ctx, q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size,
+                            gap_open, gap_extend, SW_MODE_BATCHED, 0u, &plan);
+        if (rc != SW_OK) break;
+        float total = 0.f;
+        for (int it = 0; it < 3 && rc == SW_OK; ++it) {
+            cudaEventRecord(e0, s);
+            rc = sw_plan_execute(plan, q_seqs, r_seqs, out, out + n, out + 2 * n, out + 3 * n,
+                                 out + 4 * n, stream);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(SW_ECUDA, "sw_autotune: run");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (it > 0) total += ms;  // first run warms up
+        }
+        sw_plan_destroy(plan);
+        if (rc != SW_OK) break;
+        const double ms = total / 2.0;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SW_OK) return rc;
+    if ((rc = sw_ctx_set_tuning(ctx, best.lg, best.frac)) != SW_OK) return rc;
+    if (chosen_log2g) *chosen_log2g = best.lg;
+    if (chosen_frac) *chosen_frac = best.frac;
+    if (chosen_ms) *chosen_ms = best_ms;
+    if (cache_path && *cache_path) {
+        cache.push_back({key, best.lg, best.frac, best_ms});
+        if (!write_cache(cache_path, cache, gpu, sms))
+            return set_error(SW_EINVAL, "sw_autotune: cannot write the cache file");
+    }
+    return SW_OK;
+}

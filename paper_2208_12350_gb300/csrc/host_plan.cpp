@@ -1,0 +1,166 @@
+// Host planning of a batch shared by every entry point: argument checks,
+// profile width, which kernel each pair takes, the persistent kernel's
+// class queues and grid, and the strip-boundary scratch layout.  The
+// callers differ only in where they put the resulting tables (plan-owned
+// allocations, the fixed module array, a serving arena).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sw_internal.h"
+#include "swgb.h"
+
+namespace swgb {
+
+static int plan_err(std::string *msg, int code, const char *fmt, long long a = 0, long long b = 0,
+                    long long c = 0) {
+    char buf[256];
+    snprintf(buf, sizeof buf, fmt, a, b, c);
+    if (msg) *msg = buf;
+    return code;
+}
+
+int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
+                   const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
+                   int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
+                   std::string *msg) {
+    *out = HostPlan();
+    if (n_pairs < 0) return plan_err(msg, SW_EINVAL, "n_pairs < 0");
+    if (n_pairs > 0 && (!q_offsets || !r_offsets))
+        return plan_err(msg, SW_EINVAL, "offsets are NULL");
+    if (!mat) return plan_err(msg, SW_EINVAL, "score_matrix is NULL");
+    if (A < 1 || A > SW_MAX_ALPHABET)
+        return plan_err(msg, SW_EINVAL, "alphabet_size %lld not in [1, %lld]", A, SW_MAX_ALPHABET);
+    if (ge > 0 || go > ge)
+        return plan_err(msg, SW_EINVAL, "need gap_open <= gap_extend <= 0 (got %lld, %lld)", go,
+                        ge);
+    if (go < -SW_MAX_GAP) return plan_err(msg, SW_EINVAL, "|gap_open| above %lld", SW_MAX_GAP);
+    if (mode != SW_MODE_AUTO && mode != SW_MODE_PLAIN && mode != SW_MODE_BATCHED)
+        return plan_err(msg, SW_EINVAL, "unknown mode %lld", mode);
+    if (mode == SW_MODE_AUTO) mode = SW_MODE_BATCHED;
+
+    int smax = -128, smin = 127;
+    for (int i = 0; i < A * A; ++i) {
+        smax = std::max(smax, (int)mat[i]);
+        smin = std::min(smin, (int)mat[i]);
+    }
+    std::vector<int32_t> n(n_pairs), m(n_pairs);
+    for (int32_t i = 0; i < n_pairs; ++i) {
+        const int64_t a = q_offsets[i + 1] - q_offsets[i];
+        const int64_t b = r_offsets[i + 1] - r_offsets[i];
+        if (q_offsets[i] < 0 || r_offsets[i] < 0 || a < 0 || b < 0)
+            return plan_err(msg, SW_ERANGE, "offsets of pair %lld negative or decreasing", i);
+        if (a > SW_MAX_LEN || b > SW_MAX_LEN)
+            return plan_err(msg, SW_ERANGE, "pair %lld has lengths (%lld, %lld) above SW_MAX_LEN", i,
+                            a, b);
+        n[i] = (int32_t)a;
+        m[i] = (int32_t)b;
+    }
+    out->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
+    out->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
+    if (A <= 4)
+        out->kind = ProfileKind::kInt32;
+    else if (smax - go <= 127 && smin - go >= -127)
+        out->kind = ProfileKind::kInt8;
+    else
+        out->kind = ProfileKind::kInt32;
+
+    std::vector<PlanPair> gp;  // group-path pairs, id = index into gid
+    std::vector<int32_t> gid;
+    int plain_max_n = 0;
+    for (int32_t i = 0; i < n_pairs; ++i) {
+        if (mode == SW_MODE_PLAIN || !group_path_eligible(n[i], m[i], smax, go, ge)) {
+            out->plain.push_back({q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0});
+            plain_max_n = std::max(plain_max_n, n[i]);
+        } else {
+            gp.push_back({(int32_t)gid.size(), n[i], m[i]});
+            gid.push_back(i);
+        }
+    }
+    if (!gp.empty()) {
+        int smem = 0;
+        const int bps = group_blocks_per_sm(out->kind, A, &smem);
+        if (bps <= 0)
+            return plan_err(msg, SW_ECUDA, "group kernel does not fit (%lld B shared memory)", smem);
+        const int64_t want = ((int64_t)gp.size() + kGroupWarps - 1) / kGroupWarps;
+        out->grid = (int)std::min<int64_t>((int64_t)bps * sm_count, want);
+        out->n_warps = out->grid * kGroupWarps;
+    }
+    const std::vector<PlannedClass> planned =
+        plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction);
+    out->pairs.reserve(gp.size());
+    int warp_begin = 0;
+    for (const PlannedClass &pc : planned) {
+        out->classes.push_back(
+            {(int32_t)out->pairs.size(), (int32_t)pc.pairs.size(), pc.log2g, warp_begin});
+        warp_begin += pc.warps;
+        const int G = 1 << pc.log2g;
+        for (int32_t k : pc.pairs) {
+            const int32_t i = gid[k];
+            PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
+            if (n[i] > G * kRows && m[i] > 0) {
+                pi.scratch = out->scratch_words;
+                out->scratch_words += boundary_words(m[i]);
+            }
+            out->pairs.push_back(pi);
+        }
+    }
+    if (!out->plain.empty()) {
+        if (plain_max_n <= 1024) {
+            out->plain_threads = std::max(32, ((plain_max_n + 31) / 32) * 32);
+            out->plain_kmax = 1;
+        } else {
+            out->plain_threads = kPlainWideThreads;
+            out->plain_kmax = kPlainMaxRows;
+        }
+    }
+    return SW_OK;
+}
+
+cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
+                         const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,
+                         int ge, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (!hp.pairs.empty()) {
+        e = cudaMemsetAsync(t.counters, 0, kMaxClasses * sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+        GroupParams gp;
+        std::memset(&gp, 0, sizeof gp);
+        gp.q = q;
+        gp.r = r;
+        gp.pairs = t.pairs;
+        gp.classes = t.classes;
+        gp.n_classes = (int32_t)hp.classes.size();
+        gp.counters = t.counters;
+        gp.n_warps = hp.n_warps;
+        gp.scratch = t.scratch;
+        gp.status = t.status;
+        gp.out = o;
+        gp.alphabet = A;
+        gp.gap_open = go;
+        gp.gap_extend = ge;
+        std::memcpy(gp.mat, mat, (size_t)A * A);
+        e = launch_group(gp, hp.kind, hp.grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (!hp.plain.empty()) {
+        PlainParams pp;
+        std::memset(&pp, 0, sizeof pp);
+        pp.q = q;
+        pp.r = r;
+        pp.pairs = t.plain;
+        pp.n_pairs = (int32_t)hp.plain.size();
+        pp.status = t.status;
+        pp.out = o;
+        pp.alphabet = A;
+        pp.gap_open = go;
+        pp.gap_extend = ge;
+        std::memcpy(pp.mat, mat, (size_t)A * A);
+        e = launch_plain(pp, hp.plain_threads, hp.plain_kmax, s);
+    }
+    return e;
+}
+
+}  // namespace swgb

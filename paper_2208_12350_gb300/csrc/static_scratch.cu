@@ -97,152 +97,51 @@ extern "C" int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_off
     if (!q_offsets || !r_offsets || !score_matrix || !q_seqs || !r_seqs || !out_score ||
         !out_qend || !out_rend || !out_qstart || !out_rstart)
         return err(SW_EINVAL, "sw_align_batch_static: NULL pointer argument");
-    if (alphabet_size < 1 || alphabet_size > SW_MAX_ALPHABET)
-        return err(SW_EINVAL, "sw_align_batch_static: alphabet_size %d not in [1, %d]",
-                   alphabet_size, SW_MAX_ALPHABET);
-    if (gap_extend > 0 || gap_open > gap_extend || gap_open < -SW_MAX_GAP)
-        return err(SW_EINVAL, "sw_align_batch_static: need -%d <= gap_open <= gap_extend <= 0",
-                   SW_MAX_GAP);
-    const int A = alphabet_size;
-    int smax = -128, smin = 127;
-    for (int i = 0; i < A * A; ++i) {
-        smax = std::max(smax, (int)score_matrix[i]);
-        smin = std::min(smin, (int)score_matrix[i]);
-    }
-    std::vector<int32_t> n(n_pairs), m(n_pairs);
-    for (int32_t i = 0; i < n_pairs; ++i) {
-        const int64_t a = q_offsets[i + 1] - q_offsets[i];
-        const int64_t b = r_offsets[i + 1] - r_offsets[i];
-        if (q_offsets[i] < 0 || r_offsets[i] < 0 || a < 0 || b < 0)
-            return err(SW_ERANGE, "sw_align_batch_static: offsets of pair %d negative or decreasing",
-                       i);
-        if (a > SW_MAX_LEN || b > SW_MAX_LEN)
-            return err(SW_ERANGE, "sw_align_batch_static: pair %d has lengths (%lld, %lld) > %d", i,
-                       (long long)a, (long long)b, SW_MAX_LEN);
-        n[i] = (int32_t)a;
-        m[i] = (int32_t)b;
-    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return err(SW_ECUDA, "sw_align_batch_static: no device");
-    unsigned char *base = nullptr;
-    int rc = static_address(dev, &base);
-    if (rc != SW_OK) return rc;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return err(SW_ECUDA, "sw_align_batch_static: cannot read the SM count");
-
-    ProfileKind kind = ProfileKind::kInt32;
-    if (A > 4 && smax - gap_open <= 127 && smin - gap_open >= -127) kind = ProfileKind::kInt8;
-
-    std::vector<PlanPair> gp;
-    std::vector<int32_t> gid;
-    std::vector<PairInfo> plain;
-    int plain_max_n = 0;
-    for (int32_t i = 0; i < n_pairs; ++i) {
-        const bool scaled = group_path_eligible(n[i], m[i], smax, gap_open, gap_extend);
-        if (!scaled) {
-            plain.push_back({q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0});
-            plain_max_n = std::max(plain_max_n, n[i]);
-        } else {
-            gp.push_back({(int32_t)gid.size(), n[i], m[i]});
-            gid.push_back(i);
-        }
-    }
-    int grid = 0, n_warps = 0;
-    if (!gp.empty()) {
-        int smem = 0;
-        const int bps = group_blocks_per_sm(kind, A, &smem);
-        if (bps <= 0) return err(SW_ECUDA, "sw_align_batch_static: group kernel does not fit");
-        const int64_t want = ((int64_t)gp.size() + kGroupWarps - 1) / kGroupWarps;
-        grid = (int)std::min<int64_t>((int64_t)bps * sms, want);
-        n_warps = grid * kGroupWarps;
-    }
-    const std::vector<PlannedClass> planned = plan_classes(gp, n_warps, -1, 0.5);
-    std::vector<PairInfo> pairs;
-    std::vector<ClassInfo> classes;
-    pairs.reserve(gp.size());
-    int64_t words = 0;
-    int warp_begin = 0;
-    for (const PlannedClass &pc : planned) {
-        classes.push_back({(int32_t)pairs.size(), (int32_t)pc.pairs.size(), pc.log2g, warp_begin});
-        warp_begin += pc.warps;
-        const int G = 1 << pc.log2g;
-        for (int32_t k : pc.pairs) {
-            const int32_t i = gid[k];
-            PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
-            if (n[i] > G * kRows && m[i] > 0) {
-                pi.scratch = words;
-                words += boundary_words(m[i]);
-            }
-            pairs.push_back(pi);
-        }
-    }
-    if (words > kStaticMaxBoundaryWords)
+    HostPlan hp;
+    std::string msg;
+    int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
+                            gap_extend, SW_MODE_AUTO, sms, -1, 0.5, &hp, &msg);
+    if (rc != SW_OK) return err(rc, "sw_align_batch_static: %s", msg.c_str());
+    if (hp.scratch_words > kStaticMaxBoundaryWords)
         return err(SW_ERANGE,
                    "sw_align_batch_static: the batch needs %lld strip-boundary words, above the "
                    "fixed limit of %lld; split the batch",
-                   (long long)words, (long long)kStaticMaxBoundaryWords);
+                   (long long)hp.scratch_words, (long long)kStaticMaxBoundaryWords);
+    unsigned char *base = nullptr;
+    rc = static_address(dev, &base);
+    if (rc != SW_OK) return rc;
 
     cudaStream_t s = (cudaStream_t)stream;
-    int32_t *counters = reinterpret_cast<int32_t *>(base + kOffCounters);
-    int32_t *status = reinterpret_cast<int32_t *>(base + kOffStatus);
-    ClassInfo *d_classes = reinterpret_cast<ClassInfo *>(base + kOffClasses);
-    PairInfo *d_pairs = reinterpret_cast<PairInfo *>(base + kOffPairs);
-    PairInfo *d_plain = reinterpret_cast<PairInfo *>(base + kOffPlain);
-    uint32_t *d_bnd = reinterpret_cast<uint32_t *>(base + kOffBoundary);
-    // queue heads and the status word must start at zero on every call
-    cudaError_t e = cudaMemsetAsync(base + kOffCounters, 0, kOffClasses - kOffCounters, s);
-    if (e == cudaSuccess && !classes.empty())
-        e = cudaMemcpyAsync(d_classes, classes.data(), classes.size() * sizeof(ClassInfo),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !pairs.empty())
-        e = cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(PairInfo),
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !plain.empty())
-        e = cudaMemcpyAsync(d_plain, plain.data(), plain.size() * sizeof(PairInfo),
-                            cudaMemcpyHostToDevice, s);
+    DeviceTables t;
+    t.counters = reinterpret_cast<int32_t *>(base + kOffCounters);
+    t.status = reinterpret_cast<int32_t *>(base + kOffStatus);
+    t.classes = reinterpret_cast<ClassInfo *>(base + kOffClasses);
+    t.pairs = reinterpret_cast<PairInfo *>(base + kOffPairs);
+    t.plain = reinterpret_cast<PairInfo *>(base + kOffPlain);
+    t.scratch = reinterpret_cast<uint32_t *>(base + kOffBoundary);
+    // the status word must start at zero on every call (enqueue_plan zeroes
+    // the queue heads itself)
+    cudaError_t e = cudaMemsetAsync(base + kOffStatus, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && !hp.classes.empty())
+        e = cudaMemcpyAsync(const_cast<ClassInfo *>(t.classes), hp.classes.data(),
+                            hp.classes.size() * sizeof(ClassInfo), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !hp.pairs.empty())
+        e = cudaMemcpyAsync(const_cast<PairInfo *>(t.pairs), hp.pairs.data(),
+                            hp.pairs.size() * sizeof(PairInfo), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !hp.plain.empty())
+        e = cudaMemcpyAsync(const_cast<PairInfo *>(t.plain), hp.plain.data(),
+                            hp.plain.size() * sizeof(PairInfo), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return err(SW_ECUDA, "sw_align_batch_static: table copy: %s", cudaGetErrorString(e));
     const Outputs o{out_score, out_qend, out_rend, out_qstart, out_rstart};
-    if (!pairs.empty()) {
-        GroupParams g;
-        std::memset(&g, 0, sizeof g);
-        g.q = q_seqs;
-        g.r = r_seqs;
-        g.pairs = d_pairs;
-        g.classes = d_classes;
-        g.n_classes = (int32_t)classes.size();
-        g.counters = counters;
-        g.n_warps = n_warps;
-        g.scratch = d_bnd;
-        g.status = status;
-        g.out = o;
-        g.alphabet = A;
-        g.gap_open = gap_open;
-        g.gap_extend = gap_extend;
-        std::memcpy(g.mat, score_matrix, (size_t)A * A);
-        e = launch_group(g, kind, grid, s);
-        if (e != cudaSuccess)
-            return err(SW_ECUDA, "sw_align_batch_static: launch: %s", cudaGetErrorString(e));
-    }
-    if (!plain.empty()) {
-        PlainParams pp;
-        std::memset(&pp, 0, sizeof pp);
-        pp.q = q_seqs;
-        pp.r = r_seqs;
-        pp.pairs = d_plain;
-        pp.n_pairs = (int32_t)plain.size();
-        pp.status = status;
-        pp.out = o;
-        pp.alphabet = A;
-        pp.gap_open = gap_open;
-        pp.gap_extend = gap_extend;
-        std::memcpy(pp.mat, score_matrix, (size_t)A * A);
-        const bool wide = plain_max_n > 1024;
-        e = launch_plain(pp, wide ? kPlainWideThreads : std::max(32, (plain_max_n + 31) / 32 * 32),
-                         wide ? kPlainMaxRows : 1, s);
-        if (e != cudaSuccess)
-            return err(SW_ECUDA, "sw_align_batch_static: launch: %s", cudaGetErrorString(e));
-    }
+    e = enqueue_plan(hp, t, q_seqs, r_seqs, o, score_matrix, alphabet_size, gap_open, gap_extend,
+                     s);
+    if (e != cudaSuccess)
+        return err(SW_ECUDA, "sw_align_batch_static: launch: %s", cudaGetErrorString(e));
     return SW_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 namespace swgb {
@@ -123,6 +124,28 @@ int64_t sweep_steps(int n, int m, int G);
 // Profile element width of the group kernel.
 enum class ProfileKind : int { kInt32 = 0, kInt8 = 1 };
 
+// A batch planned on the host (host_plan.cpp): the device tables to upload
+// and the launch shapes.
+struct HostPlan {
+    ProfileKind kind = ProfileKind::kInt32;
+    std::vector<PairInfo> pairs;     // persistent kernel, schedule order
+    std::vector<ClassInfo> classes;  // its queues
+    std::vector<PairInfo> plain;     // one-block-per-pair kernel
+    int grid = 0, n_warps = 0;
+    int64_t scratch_words = 0;       // strip-boundary words the pairs need
+    int plain_threads = 32, plain_kmax = 1;
+    int64_t q_bytes = 0, r_bytes = 0;  // residues the offsets span
+};
+// Where a HostPlan's tables live on the device.
+struct DeviceTables {
+    const PairInfo *pairs = nullptr;
+    const ClassInfo *classes = nullptr;
+    const PairInfo *plain = nullptr;
+    int32_t *counters = nullptr;  // kMaxClasses words, zeroed by enqueue_plan
+    uint32_t *scratch = nullptr;  // scratch_words words
+    int32_t *status = nullptr;
+};
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_group(const GroupParams &p, ProfileKind kind, int grid, cudaStream_t s);
 int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes);
@@ -133,6 +156,18 @@ cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_
 size_t plain_smem_bytes(int threads, int alphabet);
 
 int set_error(int code, const char *msg);  // message for sw_last_error()
+
+// Checks the arguments and plans a batch (no device allocation; queries the
+// group kernel's occupancy on the current device).  Returns an sw_status;
+// on failure *msg says why.
+int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
+                   const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
+                   int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
+                   std::string *msg);
+// Enqueues the kernels of a planned batch on s (queue-head reset included).
+cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
+                         const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,
+                         int ge, cudaStream_t s);
 
 cudaError_t launch_check_residues(const uint8_t *seqs, int64_t n, int alphabet,
                                   unsigned long long *bad, cudaStream_t s);
