@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0 = auto)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per rate point")
+    ap.add_argument("--serve-rate0", type=float, default=250.0, help="first offered rate, req/s")
+    ap.add_argument("--serve-points", type=int, default=14)
+    ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -175,6 +180,120 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------- serving
+
+def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
+    """Open-loop serving: Poisson arrivals of requests of floor(log-uniform
+    [1, 4096]) pairs, half from the DNA workload and half from the protein
+    workload, offered at rates growing x1.5 per point until the server no
+    longer keeps up (served rate below 90% of offered, or p99 above 1 s).
+    Latency = completion on the GPU (server clock) - scheduled arrival, so
+    a late submitter counts against the server, as a real client would.
+    Every request's results are compared with the same pairs run as one
+    whole batch."""
+    import queue
+    import threading
+    protein = wl.gen_config(2)
+    prot_res = _batch_results(swgb, ctx, protein)
+    pools = {"dna": dna, "protein": protein}
+    pool_res = {"dna": dna_res, "protein": prot_res}
+    reqs = wl.serving_requests(args.serve_requests, 1.0, pools=pools)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    srv = swgb.sw_server_create(ctx, budget, streams=8, staging_bytes=2 << 30)
+    identical = True
+
+    def check(rq, out):
+        exp = pool_res[rq.kind][rq.first:rq.first + rq.batch.n_pairs]
+        return bool(np.array_equal(out, exp))
+
+    def submit(rq):
+        b = rq.batch
+        return swgb.sw_server_submit(srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix,
+                                     b.gap_open, b.gap_extend, timeout_ms=120000)
+
+    for rq in reqs[:16]:  # warm-up, one at a time
+        out = swgb.sw_server_wait(srv, submit(rq), rq.batch.n_pairs, timeout_ms=120000)
+        identical &= check(rq, out)
+    points = []
+    rate = args.serve_rate0
+    try:
+        for _ in range(args.serve_points):
+            n = min(len(reqs), max(200, int(rate * 20.0)))
+            todo = reqs[:n]
+            arrival = np.zeros(n, dtype=np.int64)
+            ids: queue.Queue = queue.Queue()
+            t0 = time.monotonic_ns() + 20_000_000
+
+            def submitter():
+                try:
+                    for i, rq in enumerate(todo):
+                        at = t0 + int(rq.arrival_s / rate * 1e9)
+                        arrival[i] = at
+                        delay = (at - time.monotonic_ns()) / 1e9
+                        if delay > 0:
+                            time.sleep(delay)
+                        ids.put((i, submit(rq)))
+                except Exception as e:  # surfaced by the waiter
+                    ids.put((-1, e))
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat = np.zeros(n)
+            done_last = 0
+            cells = 0
+            for _k in range(n):
+                i, rid = ids.get()
+                if i < 0:
+                    raise rid
+                rq = todo[i]
+                out, done_ns = swgb.sw_server_wait(srv, rid, rq.batch.n_pairs, timeout_ms=120000,
+                                                   return_done_ns=True)
+                identical &= check(rq, out)
+                lat[i] = (done_ns - arrival[i]) / 1e6
+                done_last = max(done_last, done_ns)
+                cells += rq.batch.cells
+            th.join()
+            span = (done_last - t0) / 1e9
+            served = n / span
+            pt = {"offered_rps": rate, "requests": n, "served_rps": served,
+                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                  "gcups": cells / span / 1e9}
+            points.append(pt)
+            if served < 0.9 * rate or pt["p99_ms"] > 1000.0:
+                break
+            rate *= 1.5
+        st = swgb.sw_server_stats(srv)
+    finally:
+        swgb.sw_server_destroy(srv)
+    kept = [p for p in points if p["served_rps"] >= 0.9 * p["offered_rps"]
+            and p["p99_ms"] <= 1000.0]
+    best = kept[-1] if kept else None
+    return {"p99_ms": best["p99_ms"] if best else None, "p50_ms": best["p50_ms"] if best else None,
+            "at_rps": best["offered_rps"] if best else None,
+            "max_sustained_rps": best["served_rps"] if best else None,
+            "peak_gcups": max(p["gcups"] for p in points) if points else None,
+            "identical_outputs": identical, "budget_gb": args.serve_budget_gb, "streams": 8,
+            "device_bytes_peak": st["device_bytes_peak"],
+            "requests": "Poisson arrivals; floor(log-uniform[1,4096]) pairs; 50% dna-100k, "
+                        "50% protein-20k pairs",
+            "points": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in p.items()}
+                       for p in points]}
+
+
+def _batch_results(swgb, ctx, batch) -> np.ndarray:
+    """(n, 5) results of a whole batch in one planned launch."""
+    import torch
+    q = torch.from_numpy(batch.q_seqs).cuda()
+    r = torch.from_numpy(batch.r_seqs).cuda()
+    out = torch.zeros((5, batch.n_pairs), dtype=torch.int32, device=q.device)
+    plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                               batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED, 0)
+    swgb.sw_plan_execute(plan, q, r, out, None)
+    torch.cuda.synchronize()
+    swgb.sw_plan_destroy(plan)
+    return out.T.contiguous().cpu().numpy()
+
+
 # ------------------------------------------------------------------- our arm
 
 def reverse_cells(res: np.ndarray) -> int:
@@ -292,6 +411,14 @@ def run_ours(args, rank, world, local):
            "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same}
 
     swgb.sw_plan_destroy(plan)
+
+    serve = None
+    if not args.no_serve and rank == 0 and world == 1:
+        if args.config == 1:
+            serve = serve_sweep(swgb, ctx, batch, res, args)
+        else:
+            dna = wl.gen_config(1)
+            serve = serve_sweep(swgb, ctx, dna, _batch_results(swgb, ctx, dna), args)
     swgb.sw_ctx_destroy(ctx)
 
     cpu = None
@@ -312,7 +439,7 @@ def run_ours(args, rank, world, local):
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "clocks": clk,
                 "gpu_launches": info["launches"] * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -252,13 +252,16 @@ int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_offsets,
  *
  * sw_server_create: a server on ctx's device with a device-memory budget of
  * budget_bytes (allocated once, at creation, as the arena that holds every
- * admitted request's sequences, tables, scratch and outputs), `streams`
- * requests at most on the GPU at a time (one stream each, 1..64), and a
- * pinned host staging pool of staging_bytes.  A worker thread admits queued
- * requests in arrival order whenever a stream slot is free and the
- * request's device bytes fit in what the arena has left, launches it on its
- * slot's stream (so requests overlap on the device) and retires it when its
- * completion event fires.
+ * launch's sequences, tables, scratch and outputs), at most `streams`
+ * launches on the GPU at a time (one stream each, 1..64), and a pinned host
+ * staging pool of staging_bytes.  A worker thread forms launches whenever a
+ * stream slot is free: the oldest queued request plus the later queued
+ * requests with the same scoring (matrix, gap costs), up to 262144 pairs and
+ * 4e9 cells per launch and what the arena has left.  Each launch is planned
+ * as one batch of the batched path; launches on different slots overlap on
+ * the device.  A request's device footprint is bounded at submission by its
+ * sequences, 40 B of pair record and 20 B of outputs per pair, and the
+ * strip-boundary scratch of its pairs at the narrowest lane-group width.
  *
  * sw_server_submit: queue a request given as HOST arrays (sequences,
  * offsets, matrix; copied into the staging pool before the call returns, so
@@ -268,9 +271,15 @@ int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_offsets,
  *
  * sw_server_wait: wait up to timeout_ms for a request, copy its results to
  * out_host (5 x n_pairs int32: scores, qend, rend, qstart, rstart) and
- * forget it.  SW_ETIMEOUT leaves it pending (wait again later).
+ * forget it.  SW_ETIMEOUT leaves it pending (wait again later).  If done_ns
+ * is not NULL it receives the CLOCK_MONOTONIC time, in nanoseconds, at
+ * which the worker saw the request's work finish on the GPU (results back
+ * in the staging pool), so that a client can measure latency from its own
+ * arrival times on the same clock.
  *
- * Results equal those of sw_plan_execute on the same batch.
+ * Results equal those of sw_plan_execute on the same batch.  The paper runs
+ * fixed batches only (Section 3); the server is this library's addition for
+ * callers whose pairs arrive over time.
  */
 typedef struct sw_server sw_server;
 int sw_server_create(sw_ctx *ctx, int64_t budget_bytes, int32_t streams, int64_t staging_bytes,
@@ -280,9 +289,14 @@ int sw_server_submit(sw_server *server, const uint8_t *q_seqs, const int64_t *q_
                      const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
                      int32_t gap_extend, int32_t timeout_ms, int64_t *request_id);
 int sw_server_poll(sw_server *server, int64_t request_id, int32_t *done);
-int sw_server_wait(sw_server *server, int64_t request_id, int32_t timeout_ms, int32_t *out_host);
+int sw_server_wait(sw_server *server, int64_t request_id, int32_t timeout_ms, int32_t *out_host,
+                   int64_t *done_ns);
 int sw_server_stats(sw_server *server, int64_t *completed, int64_t *in_flight, int64_t *queued,
                     int64_t *device_bytes_in_use, int64_t *device_bytes_peak);
+/* Launches the worker has started so far, the pairs they held and the host
+ * milliseconds spent planning them (any pointer may be NULL). */
+int sw_server_launches(sw_server *server, int64_t *launches, int64_t *pairs_launched,
+                       double *plan_ms);
 int sw_server_destroy(sw_server *server);
 
 /*

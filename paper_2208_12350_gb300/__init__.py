@@ -56,9 +56,11 @@ SIGNATURES = {
     "sw_server_submit": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32,
                           ctypes.POINTER(_I64)], ctypes.c_int),
     "sw_server_poll": ([_P, _I64, ctypes.POINTER(_I32)], ctypes.c_int),
-    "sw_server_wait": ([_P, _I64, _I32, _P], ctypes.c_int),
+    "sw_server_wait": ([_P, _I64, _I32, _P, ctypes.POINTER(_I64)], ctypes.c_int),
     "sw_server_stats": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                          ctypes.POINTER(_I64), ctypes.POINTER(_I64)], ctypes.c_int),
+    "sw_server_launches": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sw_server_destroy": ([_P], ctypes.c_int),
     "sw_microbench_int": ([_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -302,11 +304,16 @@ def sw_server_poll(server: int, request_id: int) -> bool:
     return bool(d.value)
 
 
-def sw_server_wait(server: int, request_id: int, n_pairs: int, timeout_ms: int = 60000) -> np.ndarray:
-    """(n_pairs, 5) int32 results of a request."""
+def sw_server_wait(server: int, request_id: int, n_pairs: int, timeout_ms: int = 60000,
+                   return_done_ns: bool = False):
+    """(n_pairs, 5) int32 results of a request; with return_done_ns, also the
+    CLOCK_MONOTONIC ns (time.monotonic_ns's clock) at which it finished."""
     out = np.empty((5, n_pairs), dtype=np.int32)
-    _check(load().sw_server_wait(server, request_id, timeout_ms, out.ctypes.data), "sw_server_wait")
-    return out.T.copy()
+    done = _I64()
+    _check(load().sw_server_wait(server, request_id, timeout_ms, out.ctypes.data,
+                                 ctypes.byref(done)), "sw_server_wait")
+    res = out.T.copy()
+    return (res, done.value) if return_done_ns else res
 
 
 def sw_server_stats(server: int) -> dict:
@@ -314,6 +321,14 @@ def sw_server_stats(server: int) -> dict:
     _check(load().sw_server_stats(server, *[ctypes.byref(x) for x in v]), "sw_server_stats")
     return dict(zip(["completed", "in_flight", "queued", "device_bytes_in_use",
                      "device_bytes_peak"], [x.value for x in v]))
+
+
+def sw_server_launches(server: int) -> dict:
+    """{"launches", "pairs", "plan_ms"} so far."""
+    a, b, c = _I64(), _I64(), ctypes.c_double()
+    _check(load().sw_server_launches(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "sw_server_launches")
+    return {"launches": a.value, "pairs": b.value, "plan_ms": c.value}
 
 
 def sw_server_destroy(server: int) -> None:

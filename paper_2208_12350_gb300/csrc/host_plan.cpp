@@ -22,11 +22,19 @@ static int plan_err(std::string *msg, int code, const char *fmt, long long a = 0
     return code;
 }
 
-int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
-                   const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
-                   int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
-                   std::string *msg) {
-    *out = HostPlan();
+static int smax_of(const int8_t *mat, int A, int *smin_out) {
+    int smax = -128, smin = 127;
+    for (int i = 0; i < A * A; ++i) {
+        smax = std::max(smax, (int)mat[i]);
+        smin = std::min(smin, (int)mat[i]);
+    }
+    if (smin_out) *smin_out = smin;
+    return smax;
+}
+
+int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
+                const int8_t *mat, int32_t A, int32_t go, int32_t ge, int64_t *q_bytes,
+                int64_t *r_bytes, int64_t *max_scratch_words, std::string *msg) {
     if (n_pairs < 0) return plan_err(msg, SW_EINVAL, "n_pairs < 0");
     if (n_pairs > 0 && (!q_offsets || !r_offsets))
         return plan_err(msg, SW_EINVAL, "offsets are NULL");
@@ -37,16 +45,8 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         return plan_err(msg, SW_EINVAL, "need gap_open <= gap_extend <= 0 (got %lld, %lld)", go,
                         ge);
     if (go < -SW_MAX_GAP) return plan_err(msg, SW_EINVAL, "|gap_open| above %lld", SW_MAX_GAP);
-    if (mode != SW_MODE_AUTO && mode != SW_MODE_PLAIN && mode != SW_MODE_BATCHED)
-        return plan_err(msg, SW_EINVAL, "unknown mode %lld", mode);
-    if (mode == SW_MODE_AUTO) mode = SW_MODE_BATCHED;
-
-    int smax = -128, smin = 127;
-    for (int i = 0; i < A * A; ++i) {
-        smax = std::max(smax, (int)mat[i]);
-        smin = std::min(smin, (int)mat[i]);
-    }
-    std::vector<int32_t> n(n_pairs), m(n_pairs);
+    const int smax = smax_of(mat, A, nullptr);
+    int64_t words = 0;
     for (int32_t i = 0; i < n_pairs; ++i) {
         const int64_t a = q_offsets[i + 1] - q_offsets[i];
         const int64_t b = r_offsets[i + 1] - r_offsets[i];
@@ -55,8 +55,34 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         if (a > SW_MAX_LEN || b > SW_MAX_LEN)
             return plan_err(msg, SW_ERANGE, "pair %lld has lengths (%lld, %lld) above SW_MAX_LEN", i,
                             a, b);
-        n[i] = (int32_t)a;
-        m[i] = (int32_t)b;
+        if (a > (1 << kMinLog2G) * kRows && b > 0 &&
+            group_path_eligible((int)a, (int)b, smax, go, ge))
+            words += boundary_words((int)b);
+    }
+    if (q_bytes) *q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
+    if (r_bytes) *r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
+    if (max_scratch_words) *max_scratch_words = words;
+    return SW_OK;
+}
+
+int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
+                   const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
+                   int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
+                   std::string *msg, int min_pairs_per_warp, int sample_cap) {
+    *out = HostPlan();
+    int rc = check_batch(q_offsets, r_offsets, n_pairs, mat, A, go, ge, nullptr, nullptr,
+                         nullptr, msg);
+    if (rc != SW_OK) return rc;
+    if (mode != SW_MODE_AUTO && mode != SW_MODE_PLAIN && mode != SW_MODE_BATCHED)
+        return plan_err(msg, SW_EINVAL, "unknown mode %lld", mode);
+    if (mode == SW_MODE_AUTO) mode = SW_MODE_BATCHED;
+
+    int smin = 0;
+    const int smax = smax_of(mat, A, &smin);
+    std::vector<int32_t> n(n_pairs), m(n_pairs);
+    for (int32_t i = 0; i < n_pairs; ++i) {
+        n[i] = (int32_t)(q_offsets[i + 1] - q_offsets[i]);
+        m[i] = (int32_t)(r_offsets[i + 1] - r_offsets[i]);
     }
     out->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
     out->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
@@ -67,11 +93,27 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     else
         out->kind = ProfileKind::kInt32;
 
+    // The persistent kernel takes every eligible pair, unless its shared
+    // memory for this alphabet and profile does not fit the device (int32
+    // profiles of large alphabets): then every pair takes the plain kernel.
+    bool group_fits = mode != SW_MODE_PLAIN;
+    int bps = 0;
+    if (group_fits) {
+        bool any = false;
+        for (int32_t i = 0; i < n_pairs && !any; ++i)
+            any = group_path_eligible(n[i], m[i], smax, go, ge);
+        if (any) {
+            int smem = 0;
+            bps = group_blocks_per_sm(out->kind, A, &smem);
+            if (bps < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
+            group_fits = bps > 0;
+        }
+    }
     std::vector<PlanPair> gp;  // group-path pairs, id = index into gid
     std::vector<int32_t> gid;
     int plain_max_n = 0;
     for (int32_t i = 0; i < n_pairs; ++i) {
-        if (mode == SW_MODE_PLAIN || !group_path_eligible(n[i], m[i], smax, go, ge)) {
+        if (!group_fits || !group_path_eligible(n[i], m[i], smax, go, ge)) {
             out->plain.push_back({q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0});
             plain_max_n = std::max(plain_max_n, n[i]);
         } else {
@@ -80,16 +122,13 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         }
     }
     if (!gp.empty()) {
-        int smem = 0;
-        const int bps = group_blocks_per_sm(out->kind, A, &smem);
-        if (bps <= 0)
-            return plan_err(msg, SW_ECUDA, "group kernel does not fit (%lld B shared memory)", smem);
-        const int64_t want = ((int64_t)gp.size() + kGroupWarps - 1) / kGroupWarps;
+        const int64_t per_block = (int64_t)kGroupWarps * std::max(1, min_pairs_per_warp);
+        const int64_t want = ((int64_t)gp.size() + per_block - 1) / per_block;
         out->grid = (int)std::min<int64_t>((int64_t)bps * sm_count, want);
         out->n_warps = out->grid * kGroupWarps;
     }
     const std::vector<PlannedClass> planned =
-        plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction);
+        plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction, sample_cap);
     out->pairs.reserve(gp.size());
     int warp_begin = 0;
     for (const PlannedClass &pc : planned) {

@@ -56,6 +56,9 @@
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
 // a_qend..a_0 and b_rend..b_0.  Every 2U steps the group looks for a cell of
 // score S; once found, it only finishes the columns up to that one.
+#include <algorithm>
+#include <mutex>
+
 #include "sw_internal.h"
 
 namespace swgb {
@@ -560,25 +563,46 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
            (size_t)kColdWords * 4 * kGroupWarps * 32 + kGroupWarps * per_warp;
 }
 
+// The dynamic shared-memory limit of each instantiation is raised once, to
+// what the largest alphabet needs, so that concurrent planning of batches
+// with different alphabets (from several host threads) never lowers it
+// under a launch that needs more.  Occupancy per (profile, alphabet) is
+// cached per device.
 int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes) {
     const size_t smem = group_smem_bytes(kind, alphabet);
     if (smem_bytes) *smem_bytes = (int)smem;
-    int blocks = 0;
-    cudaError_t e;
-    if (kind == ProfileKind::kInt8) {
-        e = cudaFuncSetAttribute(sw_group_kernel<kRows, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &blocks, sw_group_kernel<kRows, true>, kGroupWarps * 32, smem);
-    } else {
-        e = cudaFuncSetAttribute(sw_group_kernel<kRows, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &blocks, sw_group_kernel<kRows, false>, kGroupWarps * 32, smem);
+    if (alphabet < 1 || alphabet > kMaxAlphabet) return -1;
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static int cache[kMaxDevices][2][kMaxAlphabet + 1];
+    static bool raised[kMaxDevices][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    const int ki = kind == ProfileKind::kInt8 ? 1 : 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache[dev][ki][alphabet] > 0) return cache[dev][ki][alphabet];
+    cudaError_t e = cudaSuccess;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+        return -1;
+    if (smem > (size_t)optin) return 0;  // this alphabet's profile does not fit
+    if (!raised[dev][ki]) {
+        const int top = (int)std::min<size_t>(group_smem_bytes(kind, kMaxAlphabet), (size_t)optin);
+        e = ki ? cudaFuncSetAttribute(sw_group_kernel<kRows, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, top)
+               : cudaFuncSetAttribute(sw_group_kernel<kRows, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, top);
+        if (e != cudaSuccess) return -1;
+        raised[dev][ki] = true;
     }
+    int blocks = 0;
+    e = ki ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sw_group_kernel<kRows, true>,
+                                                           kGroupWarps * 32, smem)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sw_group_kernel<kRows, false>,
+                                                           kGroupWarps * 32, smem);
     if (e != cudaSuccess) return -1;
+    cache[dev][ki][alphabet] = blocks;
     return blocks;
 }
 

@@ -30,32 +30,42 @@ int64_t sweep_steps(int n, int m, int G) {
     return strips * cols;
 }
 
-static double est_cost(const PlanPair &p, int G) {
-    return 1.25 * (double)sweep_steps(p.n, p.m, G);
-}
-
 namespace {
+
+// est_cost[lg][i]: estimated time of pair i under lane-group width 2^lg, in
+// wavefront steps (forward sweep plus a quarter for the reverse pass).
+struct Costs {
+    std::vector<double> at[6];
+    double operator()(int lg, int32_t id) const { return at[lg][(size_t)id]; }
+};
+
+Costs compute_costs(const std::vector<PlanPair> &pairs) {
+    Costs c;
+    for (int lg = kMinLog2G; lg <= 5; ++lg) {
+        c.at[lg].resize(pairs.size());
+        for (size_t i = 0; i < pairs.size(); ++i)
+            c.at[lg][i] = 1.25 * (double)sweep_steps(pairs[i].n, pairs[i].m, 1 << lg);
+    }
+    return c;
+}
 
 struct Candidate {
     std::vector<PlannedClass> classes;
     double makespan = 0;
 };
 
-// Longest-first schedule of every class on its warps' groups; returns the
+// Longest-first schedule of every class on its warps' groups, over a sample
+// of the pairs (with the warp count scaled by the same factor); returns the
 // time the last warp finishes (in wavefront steps).
-double simulate(const std::vector<PlanPair> &pairs, const std::vector<PlannedClass> &cls,
-                int n_warps, const std::vector<int> &sample_ids) {
+double simulate(const Costs &cost, const std::vector<PlannedClass> &cls, int n_warps,
+                const std::vector<char> &sampled, double scale) {
     const int nc = (int)cls.size();
     if (nc == 0) return 0;
-    // per class: sampled costs (largest first) and a scaled warp count
-    const double scale = pairs.empty() ? 1.0 : (double)sample_ids.size() / (double)pairs.size();
     std::vector<std::vector<double>> q(nc);
-    std::vector<int> idx_of(pairs.size(), -1);
-    for (size_t k = 0; k < sample_ids.size(); ++k) idx_of[sample_ids[k]] = 1;
     for (int c = 0; c < nc; ++c) {
-        const int G = 1 << cls[c].log2g;
         for (int32_t id : cls[c].pairs)
-            if (idx_of[id] > 0) q[c].push_back(est_cost(pairs[id], G));
+            if (sampled[(size_t)id]) q[c].push_back(cost(cls[c].log2g, id));
+        std::sort(q[c].begin(), q[c].end(), std::greater<double>());
     }
     int sw = std::max(1, (int)std::lround(n_warps * scale));
     std::vector<int> start;
@@ -70,66 +80,65 @@ double simulate(const std::vector<PlanPair> &pairs, const std::vector<PlannedCla
         if (start.empty()) start.push_back(0);
     }
     sw = (int)start.size();
-    using Ev = std::tuple<double, int, int>;  // time, warp, class visit index
+    // An event is k idle groups of warp w, free from time t, on the warp's
+    // v-th class visit: one entry stands for all of a warp's groups that
+    // fall idle together, so a warp costs one entry, not one per group.
+    using Ev = std::tuple<double, int, int, int>;  // time, warp, visit, groups
     std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> ev;
     std::vector<int> pos(nc, 0), visit(sw, 0), busy(sw, 0);
     std::vector<double> wend(sw, 0.0);
     for (int w = 0; w < sw; ++w) {
-        const int P = 32 >> cls[start[w]].log2g;
-        busy[w] = P;
-        for (int g = 0; g < P; ++g) ev.emplace(0.0, w, 0);
+        busy[w] = 32 >> cls[start[w]].log2g;
+        ev.emplace(0.0, w, 0, busy[w]);
     }
     double makespan = 0;
     while (!ev.empty()) {
-        auto [t, w, v] = ev.top();
+        auto [t, w, v, k] = ev.top();
         ev.pop();
         if (v != visit[w]) continue;
         const int c = (start[w] + v) % nc;
         if (pos[c] < (int)q[c].size()) {
-            ev.emplace(t + q[c][pos[c]++], w, v);
+            ev.emplace(t + q[c][pos[c]++], w, v, 1);
+            if (k > 1) ev.emplace(t, w, v, k - 1);
             continue;
         }
         wend[w] = std::max(wend[w], t);
-        if (--busy[w] == 0) {
+        busy[w] -= k;
+        if (busy[w] == 0) {
             makespan = std::max(makespan, wend[w]);
             if (++visit[w] < nc) {
                 const int c2 = (start[w] + visit[w]) % nc;
-                const int P = 32 >> cls[c2].log2g;
-                busy[w] = P;
-                for (int g = 0; g < P; ++g) ev.emplace(wend[w], w, visit[w]);
+                busy[w] = 32 >> cls[c2].log2g;
+                ev.emplace(wend[w], w, visit[w], busy[w]);
             }
         }
     }
     return makespan;
 }
 
-std::vector<PlannedClass> build(const std::vector<PlanPair> &pairs, int n_warps, int gn,
-                                double frac) {
-    const int Gn = 1 << gn;
+// Classes of candidate (Gn = 2^gn, cap = frac x mean load per group) with
+// warp shares in proportion to class work; pairs within a class unsorted.
+std::vector<PlannedClass> build(const std::vector<PlanPair> &pairs, const Costs &cost,
+                                int n_warps, int gn, double frac) {
     double total = 0;
-    for (const auto &p : pairs) total += est_cost(p, Gn);
+    for (const auto &p : pairs) total += cost(gn, p.id);
     const double groups = (double)n_warps * (32 >> gn);
     const double cap = frac * total / std::max(1.0, groups);
     std::vector<std::vector<int32_t>> by(6);
+    std::vector<double> work(6, 0.0);
     for (const auto &p : pairs) {
         int lg = gn;
-        if (est_cost(p, Gn) > cap) {
+        if (cost(gn, p.id) > cap) {
             for (lg = gn + 1; lg < 5; ++lg)
-                if (est_cost(p, 1 << lg) <= cap) break;
+                if (cost(lg, p.id) <= cap) break;
         }
         by[lg].push_back(p.id);
+        work[lg] += cost(lg, p.id) / (32 >> lg);
     }
     std::vector<PlannedClass> cls;
     double work_total = 0;
-    std::vector<double> work(6, 0.0);
     for (int lg = 5; lg >= 0; --lg) {
         if (by[lg].empty()) continue;
-        std::sort(by[lg].begin(), by[lg].end(), [&](int32_t a, int32_t b) {
-            const double ca = est_cost(pairs[a], 1 << lg), cb = est_cost(pairs[b], 1 << lg);
-            if (ca != cb) return ca > cb;
-            return a < b;
-        });
-        for (int32_t id : by[lg]) work[lg] += est_cost(pairs[id], 1 << lg) / (32 >> lg);
         work_total += work[lg];
         cls.push_back({lg, std::move(by[lg]), 0});
     }
@@ -148,31 +157,53 @@ std::vector<PlannedClass> build(const std::vector<PlanPair> &pairs, int n_warps,
     return cls;
 }
 
+// Longest first within each class (ties by pair id), as the kernel's
+// queues hand pairs out in order.
+void sort_classes(std::vector<PlannedClass> &cls, const Costs &cost) {
+    std::vector<std::pair<double, int32_t>> key;
+    for (auto &c : cls) {
+        key.clear();
+        key.reserve(c.pairs.size());
+        for (int32_t id : c.pairs) key.emplace_back(-cost(c.log2g, id), id);
+        std::sort(key.begin(), key.end());
+        for (size_t k = 0; k < key.size(); ++k) c.pairs[k] = key[k].second;
+    }
+}
+
 }  // namespace
 
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
-                                       int narrow_log2g_hint, double cap_fraction_hint) {
+                                       int narrow_log2g_hint, double cap_fraction_hint,
+                                       int sample_cap) {
     if (pairs.empty()) return {};
     n_warps = std::max(1, n_warps);
-    if (narrow_log2g_hint >= 0)
-        return build(pairs, n_warps, std::max(narrow_log2g_hint, kMinLog2G), cap_fraction_hint);
+    const Costs cost = compute_costs(pairs);
+    if (narrow_log2g_hint >= 0) {
+        auto cls = build(pairs, cost, n_warps, std::max(narrow_log2g_hint, kMinLog2G),
+                         cap_fraction_hint);
+        sort_classes(cls, cost);
+        return cls;
+    }
     // a deterministic sample for the simulation
-    std::vector<int> sample;
-    const size_t step = std::max<size_t>(1, pairs.size() / 8192);
-    for (size_t k = 0; k < pairs.size(); k += step) sample.push_back((int)k);
+    std::vector<char> sampled(pairs.size(), 0);
+    const size_t step = std::max<size_t>(1, pairs.size() / (size_t)std::max(64, sample_cap));
+    size_t n_sampled = 0;
+    for (size_t k = 0; k < pairs.size(); k += step, ++n_sampled) sampled[k] = 1;
+    const double scale = (double)n_sampled / (double)pairs.size();
     Candidate best;
     bool have = false;
     for (int gn = kMinLog2G; gn <= 3; ++gn) {
         for (double frac : {0.25, 0.5, 1.0}) {
             Candidate c;
-            c.classes = build(pairs, n_warps, gn, frac);
-            c.makespan = simulate(pairs, c.classes, n_warps, sample);
+            c.classes = build(pairs, cost, n_warps, gn, frac);
+            c.makespan = simulate(cost, c.classes, n_warps, sampled, scale);
             if (!have || c.makespan < best.makespan) {
                 best = std::move(c);
                 have = true;
             }
         }
     }
+    sort_classes(best.classes, cost);
     return best.classes;
 }
 

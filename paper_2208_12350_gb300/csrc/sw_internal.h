@@ -118,7 +118,8 @@ struct PlannedClass {
     int warps;                   // warps that start on this class
 };
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
-                                       int narrow_log2g_hint, double cap_fraction_hint);
+                                       int narrow_log2g_hint, double cap_fraction_hint,
+                                       int sample_cap = 8192);
 int64_t sweep_steps(int n, int m, int G);
 
 // Profile element width of the group kernel.
@@ -160,10 +161,22 @@ int set_error(int code, const char *msg);  // message for sw_last_error()
 // Checks the arguments and plans a batch (no device allocation; queries the
 // group kernel's occupancy on the current device).  Returns an sw_status;
 // on failure *msg says why.
+// Argument and length checks shared by every entry point.  On success
+// fills the sequence byte counts and an upper bound on the strip-boundary
+// scratch any plan of the batch needs (every group-path pair at the
+// narrowest lane-group width).
+int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
+                const int8_t *mat, int32_t A, int32_t go, int32_t ge, int64_t *q_bytes,
+                int64_t *r_bytes, int64_t *max_scratch_words, std::string *msg);
+// min_pairs_per_warp: the grid of the persistent kernel gets at most one
+// warp per this many group-path pairs (1 = lowest latency; 32 >> kMinLog2G
+// fills every group of the narrowest width, for a GPU shared with other
+// launches).  sample_cap: pairs the planner's schedule simulation looks at
+// (fewer plan faster, more plan better).
 int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
-                   std::string *msg);
+                   std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192);
 // Enqueues the kernels of a planned batch on s (queue-head reset included).
 cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
                          const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,

@@ -185,6 +185,28 @@ def test_asymmetric_matrix_and_small_alphabet(gpu_lib, ctx):
     assert_same(got, expect, "asym")
 
 
+def test_largest_alphabet_with_wide_scores(gpu_lib, ctx):
+    """32 residue codes with scores outside the int8 profile's range: the
+    int32 profile of so large an alphabet does not fit in shared memory, so
+    every pair takes the plain kernel, still exact."""
+    rng = np.random.default_rng(37)
+    mat = rng.integers(-100, 101, size=(32, 32)).astype(np.int8)
+    np.fill_diagonal(mat, 100)
+    qs = [rng.integers(0, 32, int(rng.integers(0, 120))).astype(np.uint8) for _ in range(200)]
+    rs = [rng.integers(0, 32, int(rng.integers(0, 300))).astype(np.uint8) for _ in range(200)]
+    b = wl.make_batch("a32", qs, rs, mat, -50, -5)
+    expect = oracle.align_workload(b)
+    got, info = run_lib(gpu_lib, ctx, b)
+    assert_same(got, expect, "alphabet 32, wide scores")
+    assert info["plain_pairs"] == b.n_pairs
+    # the same alphabet with int8-range scores fits and takes the batched path
+    mat8 = np.clip(mat, -20, 20).astype(np.int8)
+    b8 = wl.make_batch("a32i8", qs, rs, mat8, -10, -2)
+    got8, info8 = run_lib(gpu_lib, ctx, b8)
+    assert_same(got8, oracle.align_workload(b8), "alphabet 32, int8 profile")
+    assert info8["group_pairs"] > 0
+
+
 def test_graph_replay_and_repeat(gpu_lib, ctx):
     import torch
     b = wl.gen_config(0, n_pairs=500)

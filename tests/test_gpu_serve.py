@@ -134,3 +134,31 @@ def test_concurrent_clients(gpu_lib, ctx):
     assert not errors, errors
     for b, o in zip(batches, results):
         assert np.array_equal(o, oracle.align_workload(b))
+
+
+def test_queued_requests_merge_into_one_launch(gpu_lib, ctx):
+    """With one stream slot busy on a large request, the requests queued
+    behind it run as merged launches: one per scoring, DNA and protein kept
+    apart, results still exact."""
+    swgb = gpu_lib
+    big = wl.gen_config(1, n_pairs=60000)
+    small = _requests(12, seed=33)
+    srv = swgb.sw_server_create(ctx, 4 << 30, streams=1, staging_bytes=1 << 28)
+    try:
+        rid_big = swgb.sw_server_submit(srv, big.q_seqs, big.q_offsets, big.r_seqs,
+                                        big.r_offsets, big.matrix, big.gap_open, big.gap_extend)
+        ids = [swgb.sw_server_submit(srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix,
+                                     b.gap_open, b.gap_extend) for b in small]
+        outs = [swgb.sw_server_wait(srv, rid, b.n_pairs) for rid, b in zip(ids, small)]
+        out_big = swgb.sw_server_wait(srv, rid_big, big.n_pairs)
+        launches = swgb.sw_server_launches(srv)["launches"]
+    finally:
+        swgb.sw_server_destroy(srv)
+    kinds = {b.name.split("-")[-1] for b in small}
+    # the large request alone, then at most a few merged launches
+    assert launches <= 1 + 2 * len(kinds), launches
+    assert launches < 1 + len(small)
+    for b, o in zip(small, outs):
+        assert np.array_equal(o, oracle.align_workload(b))
+    idx = np.arange(0, big.n_pairs, 211)
+    assert np.array_equal(out_big[idx], oracle.align_workload(big, idx=idx))

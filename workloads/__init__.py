@@ -205,6 +205,14 @@ class Batch:
         r = self.r_seqs[self.r_offsets[i]:self.r_offsets[i + 1]]
         return q, r
 
+    def slice(self, lo: int, hi: int) -> "Batch":
+        """Pairs lo..hi-1 as their own batch (contiguous, so no repacking)."""
+        qo, ro = self.q_offsets[lo:hi + 1], self.r_offsets[lo:hi + 1]
+        return Batch(f"{self.name}[{lo}:{hi}]", self.q_seqs[qo[0]:qo[-1]].copy(), qo - qo[0],
+                     self.r_seqs[ro[0]:ro[-1]].copy(), ro - ro[0], self.matrix,
+                     self.gap_open, self.gap_extend,
+                     None if self.planted is None else self.planted[lo:hi].copy())
+
     def subset(self, idx) -> "Batch":
         idx = np.asarray(idx, dtype=np.int64)
         qs = [self.pair(int(i))[0] for i in idx]
@@ -358,22 +366,42 @@ class Request:
     arrival_s: float
     kind: str
     batch: Batch
+    first: int = 0  # index of the request's first pair in its kind's pool
 
 
 def serving_requests(n_requests: int, rate_per_s: float, seed: int = BASE_SEED + 4,
-                     max_pairs: int = 4096) -> list[Request]:
-    """Poisson arrivals; sizes floor(log-uniform[1, max_pairs]); DNA/protein 50/50."""
+                     max_pairs: int = 4096, pools: dict | None = None) -> list[Request]:
+    """Serving workload: Poisson arrivals at rate_per_s, request sizes
+    floor(log-uniform[1, max_pairs]) pairs, half DNA and half protein.
+
+    A DNA request takes the next consecutive pairs of the 100k-pair DNA
+    workload, a protein request those of the 20k-pair protein workload
+    (wrapping to the start when a pool runs out).  pools may pass those two
+    batches in ({"dna": ..., "protein": ...}); otherwise the needed prefixes
+    are generated.  Arrival times scale exactly with 1 / rate_per_s, so one
+    request list serves a whole rate sweep via arrival_s * old / new rate.
+    """
     st = Stream(seed, 11)
     u = st.uniform(0, 3 * n_requests).reshape(3, n_requests)
     gaps = -np.log1p(-u[0]) / rate_per_s
     arrivals = np.cumsum(gaps) - gaps[0]
     sizes = np.clip(np.floor(np.exp(u[1] * math.log(max_pairs))), 1, max_pairs).astype(np.int64)
     kinds = np.where(u[2] < 0.5, "dna", "protein")
+    pools = dict(pools or {})
+    for kind, cfg in (("dna", 1), ("protein", 2)):
+        if kind not in pools:
+            need = int(sizes[kinds == kind].sum())
+            pools[kind] = gen_config(cfg, n_pairs=max(1, min(need, CONFIGS[cfg]["n_pairs"])))
+    cursor = {"dna": 0, "protein": 0}
     out = []
     for i in range(n_requests):
-        base = 1 if kinds[i] == "dna" else 2
-        c = CONFIGS[base]
-        b = generate(c["kind"], int(sizes[i]), c["qlen"], c["rlen"],
-                     seed * 7919 + 1000003 * (i + 1), f"req{i}-{kinds[i]}")
-        out.append(Request(i, float(arrivals[i]), str(kinds[i]), b))
+        kind = str(kinds[i])
+        pool = pools[kind]
+        k = int(min(sizes[i], pool.n_pairs))
+        if cursor[kind] + k > pool.n_pairs:
+            cursor[kind] = 0
+        b = pool.slice(cursor[kind], cursor[kind] + k)
+        b.name = f"req{i}-{kind}"
+        cursor[kind] += k
+        out.append(Request(i, float(arrivals[i]), kind, b, cursor[kind] - k))
     return out
