@@ -129,7 +129,12 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
  * residues the plan's offsets index; the five outputs are DEVICE arrays of
  * n_pairs int32, written at each pair's position in the batch.  Residue
  * codes are clamped to alphabet_size - 1 on the device (use
- * sw_check_residues to validate).  Asynchronous; the plan may be executed
+ * sw_check_residues to validate).  The batched kernel reads residues in
+ * whole 16-byte aligned chunks, so it may read up to 15 bytes before or
+ * after a sequence; both buffers must lie in memory from the CUDA
+ * allocators (whose allocations cover whole aligned 16-byte chunks), which
+ * every device pointer of a cudaMalloc'd or PyTorch tensor does.
+ * Asynchronous; the plan may be executed
  * again once this execution has been ordered before the next on the same
  * stream.  Executions of one plan on different streams must not overlap.
  */

@@ -55,9 +55,8 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
         if (a > SW_MAX_LEN || b > SW_MAX_LEN)
             return plan_err(msg, SW_ERANGE, "pair %lld has lengths (%lld, %lld) above SW_MAX_LEN", i,
                             a, b);
-        if (a > (1 << kMinLog2G) * kRows && b > 0 &&
-            group_path_eligible((int)a, (int)b, smax, go, ge))
-            words += boundary_words((int)b);
+        if (a > 0 && b > 0 && group_path_eligible((int)a, (int)b, smax, go, ge))
+            words += pair_scratch_words((int)a, (int)b, 1 << kMinLog2G, kRows);
     }
     if (q_bytes) *q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
     if (r_bytes) *r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
@@ -139,9 +138,10 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         for (int32_t k : pc.pairs) {
             const int32_t i = gid[k];
             PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
-            if (n[i] > G * kRows && m[i] > 0) {
+            const int64_t w = n[i] > 0 && m[i] > 0 ? pair_scratch_words(n[i], m[i], G, kRows) : 0;
+            if (w > 0) {
                 pi.scratch = out->scratch_words;
-                out->scratch_words += boundary_words(m[i]);
+                out->scratch_words += w;
             }
             out->pairs.push_back(pi);
         }

@@ -54,8 +54,17 @@
 // its first column (j >= -31).
 //
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
-// a_qend..a_0 and b_rend..b_0.  Every 2U steps the group looks for a cell of
-// score S; once found, it only finishes the columns up to that one.
+// a_qend..a_0 and b_rend..b_0, transposed: the reversed reference prefix
+// gives the rows (in registers, strip by strip) and the reversed query
+// prefix the columns, with the substitution matrix read transposed.  The
+// start rule wants, among the cells of score S, the largest rstart (the
+// smallest reversed reference index, here a row) and then the largest
+// qstart (the smallest column).  Strips run in row order, so the sweep ends
+// with the first strip that holds a cell of score S: its smallest such row,
+// and that row's smallest such column, which the per-row end key already
+// gives.  The rows below that strip are never computed; had the reverse
+// sweep kept the query as rows, every strip before the one holding the
+// start would have run over all rend + 1 columns.
 #include <algorithm>
 #include <mutex>
 
@@ -95,19 +104,22 @@ __device__ __forceinline__ int byte_hi(uint32_t w) {
     return (int)d;
 }
 
-// Profile of one lane: for residue c in [0, A] (A = pad) and the lane's R
-// rows, (s(q_row, c) - go) << 16, or a pad score for rows past the query.
-// Layout [c][chunk][lane]: conflict-free loads whatever residue each lane
-// asks for.
+// Profile of one lane: for column residue c in [0, A] (A = pad) and the
+// lane's R rows, (s - go) << 16 with s the substitution score of the row's
+// residue against c, or a pad score for rows past the end.  The score of
+// row residue x against column residue c is smat[x * rs + c * cs]: rs = A,
+// cs = 1 when rows are query residues (the matrix row is the query
+// residue), rs = 1, cs = A for the transposed reverse sweep.  Layout
+// [c][chunk][lane]: conflict-free loads whatever residue each lane asks for.
 template <int R, bool P8>
 __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_t *a, int dir,
                                               int row0, int nrows, const int8_t *smat, int A,
-                                              int go) {
+                                              int go, int rs, int cs) {
     int qa[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + r;
-        qa[r] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * A : -1;
+        qa[r] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * rs : -1;
     }
     for (int c = 0; c <= A; ++c) {
         if constexpr (P8) {
@@ -117,7 +129,7 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
             for (int k = 0; k < R / 4; ++k) w[k] = 0u;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int v = (qa[r] >= 0 && c < A) ? (int)smat[qa[r] + c] - go : -128;
+                const int v = (qa[r] >= 0 && c < A) ? (int)smat[qa[r] + c * cs] - go : -128;
                 w[r >> 2] |= (uint32_t)(uint8_t)(int8_t)v << (8 * (r & 3));
             }
             if constexpr (R == 8) {
@@ -136,7 +148,7 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int r = 4 * k + u;
-                    v[u] = (qa[r] >= 0 && c < A) ? ((int)smat[qa[r] + c] - go) * 65536
+                    v[u] = (qa[r] >= 0 && c < A) ? ((int)smat[qa[r] + c * cs] - go) * 65536
                                                  : kScaledPad;
                 }
                 *reinterpret_cast<int4 *>(prof + (((size_t)c * (R / 4) + k) * 32 + lane) * 16) =
@@ -311,7 +323,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         // fresh DP state, stream cursors; waits for the strip's first data.
         auto begin_strip = [&](int ps) {
             const int n = cold.n[t], m = cold.m[t];
-            build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n, smat, A, go);
+            build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n, smat, A, go,
+                                 rev ? 1 : A, rev ? A : 1);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 H[r] = 0;
@@ -454,56 +467,63 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 flush_out(min(done, (mcols + 3) & ~3));
             }
 
-            // ---- reverse sweep: stop once a cell of the forward score has appeared
-            if (rev && live && ((s & (2 * kU - 1)) == 0)) {
-                const int target = cold.target[t];
-                uint32_t lk = K[0];
-#pragma unroll
-                for (int r = 1; r < R; ++r) lk = max(lk, K[r]);
-                int found = (int)(lk >> 16) >= target ? kColBase - (int)(lk & 0xFFFFu) : 0x7fffffff;
-                for (int off = 1; off < G; off <<= 1)
-                    found = min(found, __shfl_xor_sync(gmask, found, off, G));
-                if (found != 0x7fffffff && found + 1 < stop) {
-                    stop = found + 1;
-                    lim = stop + G - 1;
-                }
-            }
-
             // ---- end of a strip / sweep
             if (live && s >= lim) {
                 if (has_out) flush_out((mcols + 3) & ~3);
                 const int ps = cold.ps[t], passes = cold.passes[t];
+                const int row0 = ps * G * R + gl * R;
                 uint32_t best_key = cold.best_key[t];
                 int best_row = cold.best_row[t];
-                if (ps < passes) {
-                    const int row0 = ps * G * R + gl * R;
+                // reverse sweep: this strip's smallest row holding a cell of the
+                // forward score, with that row's smallest such column
+                int frow = 0x7fffffff, fcol = 0;
+                if (!rev) {
+                    if (ps < passes) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (K[r] > best_key) {
-                            best_key = K[r];
-                            best_row = row0 + r;
+                        for (int r = 0; r < R; ++r)
+                            if (K[r] > best_key) {
+                                best_key = K[r];
+                                best_row = row0 + r;
+                            }
+                    }
+                    cold.best_key[t] = best_key;
+                    cold.best_row[t] = best_row;
+                } else {
+                    const int target = cold.target[t];
+#pragma unroll
+                    for (int r = R - 1; r >= 0; --r)
+                        if ((int)(K[r] >> 16) >= target) {
+                            frow = row0 + r;
+                            fcol = kColBase - (int)(K[r] & 0xFFFFu);
                         }
+                    for (int off = 1; off < G; off <<= 1) {
+                        const int orow = __shfl_xor_sync(gmask, frow, off, G);
+                        const int ocol = __shfl_xor_sync(gmask, fcol, off, G);
+                        if (orow < frow) {
+                            frow = orow;
+                            fcol = ocol;
+                        }
+                    }
                 }
-                cold.best_key[t] = best_key;
-                cold.best_row[t] = best_row;
                 // boundary words stored by lane G-1 are read by lane 0's copies
                 // of the next strip; no copy may still be in flight into a ring
                 if (has_out) __threadfence();
                 cp_async_wait<0>();
                 __syncwarp(gmask);
-                if (ps + 1 < passes) {
+                const bool rev_found = rev && frow != 0x7fffffff;
+                if (ps + 1 < passes && !rev_found) {
                     begin_strip(ps + 1);
                 } else {
-                    for (int off = 1; off < G; off <<= 1) {
-                        const uint32_t ok = __shfl_xor_sync(gmask, best_key, off, G);
-                        const int orow = __shfl_xor_sync(gmask, best_row, off, G);
-                        if (ok > best_key || (ok == best_key && orow < best_row)) {
-                            best_key = ok;
-                            best_row = orow;
-                        }
-                    }
                     bool done = true;
                     if (!rev) {
+                        for (int off = 1; off < G; off <<= 1) {
+                            const uint32_t ok = __shfl_xor_sync(gmask, best_key, off, G);
+                            const int orow = __shfl_xor_sync(gmask, best_row, off, G);
+                            if (ok > best_key || (ok == best_key && orow < best_row)) {
+                                best_key = ok;
+                                best_row = orow;
+                            }
+                        }
                         const int S = (int)(best_key >> 16);
                         const int qend = best_row;
                         const int rend = kColBase - (int)(best_key & 0xFFFFu);
@@ -514,7 +534,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             cold.target[t] = S;
                             rev = true;
                             done = false;
-                            begin_sweep(cold.a[t] + qend, bcol + rend, qend + 1, rend + 1, -1);
+                            // transposed: reversed reference prefix as rows,
+                            // reversed query prefix as columns
+                            begin_sweep(bcol + rend, cold.a[t] + qend, rend + 1, qend + 1, -1);
                         }
                     }
                     if (done) {
@@ -524,14 +546,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             int o0 = 0, o1 = -1, o2 = -1, o3 = -1, o4 = -1;
                             if (S > 0) {
                                 const int qend = cold.qend[t], rend = cold.rend[t];
-                                const int S2 = (int)(best_key >> 16);
-                                const int l = kColBase - (int)(best_key & 0xFFFFu);
-                                if (S2 != S) atomicOr(p.status, kStatusReverseMismatch);
+                                if (!rev_found) atomicOr(p.status, kStatusReverseMismatch);
                                 o0 = S;
                                 o1 = qend;
                                 o2 = rend;
-                                o3 = qend - best_row;
-                                o4 = rend - l;
+                                o3 = rev_found ? qend - fcol : -1;
+                                o4 = rev_found ? rend - frow : -1;
                             }
                             p.out.score[id] = o0;
                             p.out.qend[id] = o1;

@@ -90,16 +90,30 @@ struct PlainParams {
     int8_t mat[kMaxAlphabet * kMaxAlphabet];
 };
 
-// Strip-boundary words a pair needs when its query spans more than one row
-// strip: two buffers (previous strip's last row / this strip's last row) of
-// m rounded up to a multiple of 4 words, 16-byte aligned, plus 4 words of
-// tail so that a 16-byte chunk read past the last column stays inside.
-inline int64_t boundary_words(int m) { return 2 * (int64_t)((m + 3) & ~3) + 4; }
+// Strip-boundary words of a sweep over `cols` columns whose rows span more
+// than one strip: two buffers (previous strip's last row / this strip's
+// last row) of cols rounded up to a multiple of 4 words, 16-byte aligned,
+// plus 4 words of tail so that a 16-byte chunk read past the last column
+// stays inside.
+inline int64_t boundary_words(int cols) { return 2 * (int64_t)((cols + 3) & ~3) + 4; }
+
+// Scratch words of a batched-path pair on lane groups of G lanes.  The
+// forward sweep has the query as rows and the reference as columns; the
+// reverse sweep is transposed (reversed reference prefix as rows, reversed
+// query prefix as columns), so either may need strips; one buffer sized for
+// the longer sequence serves both, one after the other.
+inline int64_t pair_scratch_words(int n, int m, int G, int rows_per_lane) {
+    const int strip = G * rows_per_lane;
+    if (n <= strip && m <= strip) return 0;
+    return boundary_words(n > m ? n : m);
+}
 
 // Whether a pair can take the batched kernel's scaled int32 arithmetic.
+// Both sweeps index columns below kColBase (the forward one the reference,
+// the transposed reverse one the query).
 inline bool group_path_eligible(int n, int m, int smax, int gap_open, int gap_extend) {
     if (-gap_open > kMaxScaledGap || -gap_extend > kMaxScaledGap) return false;
-    if (m > kColBase) return false;
+    if (m > kColBase || n > kColBase) return false;
     const int64_t bound = (int64_t)(smax > 0 ? smax : 0) * (n < m ? n : m);
     return bound <= kMaxScaledScore;
 }
