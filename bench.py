@@ -46,10 +46,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=CONFIG)
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="only the first N pairs of the workload (0 = all); for profiler captures")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the planner's own lane-group choice instead of measuring candidates")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, ".swgb_tune_cache.json"))
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests per rate point")
     ap.add_argument("--serve-rate0", type=float, default=250.0, help="first offered rate, req/s")
     ap.add_argument("--serve-points", type=int, default=14)
@@ -73,18 +78,24 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_rate(batch, n_pairs: int, threads: int) -> dict:
+def oracle_rate(batch, n_pairs: int, threads: int, gpu_res=None) -> dict:
+    """The CPU oracle timed on the first n_pairs pairs; with gpu_res, also
+    whether the GPU's results for those pairs equal the oracle's."""
     import oracle
     oracle.build()
-    sub = batch.subset(np.arange(n_pairs))
+    sub = batch.slice(0, n_pairs)
     t0 = time.perf_counter()
-    oracle.align_workload(sub, threads=threads)
+    ref = oracle.align_workload(sub, threads=threads)
     dt = time.perf_counter() - t0
     cells = sub.cells
-    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
-            "sample": f"first {n_pairs} pairs of {batch.name} ({cells / 1e9:.3f} G forward cells), "
-                      f"{dt:.2f} s on {threads} host threads",
-            "seconds": dt}
+    out = {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+           "sample": f"first {n_pairs} pairs of {batch.name} ({cells / 1e9:.3f} G forward cells), "
+                     f"{dt:.2f} s on {threads} host threads",
+           "seconds": dt}
+    if gpu_res is not None:
+        out["gpu_identical_pairs"] = int(np.sum(np.all(ref == gpu_res[:n_pairs], axis=1)))
+        out["gpu_identical"] = bool(np.array_equal(ref, gpu_res[:n_pairs]))
+    return out
 
 
 def auto_cpu_pairs(batch, threads: int, target_s: float = 12.0) -> int:
@@ -166,7 +177,7 @@ def run_reference(args, rank):
         r = oracle_rate(batch, n, threads)
         vals.append(r["value"])
         secs += r["seconds"]
-        cells += batch.subset(np.arange(n)).cells
+        cells += batch.slice(0, n).cells
     value = cells / secs / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -178,6 +189,32 @@ def run_reference(args, rank):
             "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ ncu traffic
+
+def profiled_traffic(batch, tune) -> int | None:
+    """DRAM bytes per launch of the group kernel from the committed ncu
+    summary, if that capture was of this workload, this tuning and this
+    kernel source (else None: the counters are stale)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"sw_group_kernel_{batch.name}.md")
+    src = os.path.join(ROOT, "paper_2208_12350_gb300", "csrc", "kernel_group.cu")
+    if not os.path.exists(path) or tune is None:
+        return None
+    text = open(path).read()
+    sha = re.search(r"kernel_sha256: ([0-9a-f]{64})", text)
+    tun = re.search(r"tuning: narrow_log2g=(-?\d+) cap_fraction=([0-9.e+]+)", text)
+    byt = re.search(r"dram_bytes_per_launch: (\d+)", text)
+    if not (sha and tun and byt):
+        return None
+    if sha.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None
+    if int(tun.group(1)) != tune["narrow_log2g"] or \
+            abs(float(tun.group(2)) - tune["cap_fraction"]) > 1e-9:
+        return None
+    return int(byt.group(1))
 
 
 # ------------------------------------------------------------------- serving
@@ -330,7 +367,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     swgb.load()
-    batch = wl.gen_config(args.config)
+    batch = wl.gen_config(args.config, n_pairs=args.pairs or None)
     cells = batch.cells
     ctx = swgb.sw_ctx_create(local)
     sms = swgb.sw_ctx_sm_count(ctx)
@@ -339,6 +376,13 @@ def run_ours(args, rank, world, local):
     r = torch.from_numpy(batch.r_seqs).to(dev)
     out = torch.zeros((5, batch.n_pairs), dtype=torch.int32, device=dev)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tune = None
+    if not args.no_autotune:
+        # measured choice of the lane-group widths (cached by GPU and batch shape)
+        tune = swgb.sw_autotune(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                                batch.gap_open, batch.gap_extend, q, r, out,
+                                cache_path=args.tune_cache, stream=stream)
+        torch.cuda.synchronize()
     plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
                                batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
                                swgb.SW_PLAN_GRAPH)
@@ -371,10 +415,14 @@ def run_ours(args, rank, world, local):
     mb_rate, _ = swgb.sw_microbench_int("viaddmax_s32", local, 2048)
     peak_measured = mb_rate / 1e12
     sm_mhz = clk.get("sm_mhz")
+    traffic = profiled_traffic(batch, tune) if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] \
+        else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
-            "frac": achieved / peak_measured if peak_measured else None, "traffic": None,
+            "frac": achieved / peak_measured if peak_measured else None, "traffic": traffic,
             "peak_kind": "measured __viaddmax_s32 issue rate, whole device, this run",
-            "ops_per_cell": OPS_PER_CELL, "cells_forward": cells, "cells_reverse": rcells}
+            "ops_per_cell": OPS_PER_CELL, "cells_forward": cells, "cells_reverse": rcells,
+            "traffic_unit": "DRAM bytes per launch (ncu, committed summary)",
+            "algorithmic_bytes": int(batch.q_seqs.nbytes + batch.r_seqs.nbytes + 20 * batch.n_pairs)}
 
     # --- plain one-block-per-pair comparator
     plain = None
@@ -425,7 +473,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = cpu_cores()
         n = args.cpu_pairs or auto_cpu_pairs(batch, threads)
-        cpu = oracle_rate(batch, n, threads)
+        cpu = oracle_rate(batch, n, threads, gpu_res=res)
         cpu.pop("seconds")
 
     if rank == 0:
@@ -436,6 +484,7 @@ def run_ours(args, rank, world, local):
                 "config": {"workload": batch.name, "pairs": batch.n_pairs,
                            "forward_cells": cells, "mode": "batched persistent + CUDA graph",
                            "l2": "flushed between steps (512 MB write)", "sms": sms,
+                           "tuning": tune,
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,

@@ -230,7 +230,8 @@ int sw_check_residues(const uint8_t *seqs, int64_t n, int32_t alphabet_size,
  * HOST arrays, as for sw_plan_create.
  *
  * Limits: at most SW_STATIC_MAX_PAIRS pairs per call, and the pairs whose
- * query spans more than one row strip need 2 x (reference length) boundary
+ * query or reference spans more than one row strip (the reverse sweep takes
+ * the reference as rows) need about 2 x (longer sequence length) boundary
  * words each, at most SW_STATIC_MAX_BOUNDARY_WORDS in total; a batch beyond
  * either is rejected with SW_ERANGE before anything is enqueued (split it).
  *

@@ -85,7 +85,10 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     }
     out->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
     out->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
-    if (A <= 4)
+#ifndef SWGB_SMALL_ALPHABET_INT32
+#define SWGB_SMALL_ALPHABET_INT32 1
+#endif
+    if (A <= 4 && SWGB_SMALL_ALPHABET_INT32)
         out->kind = ProfileKind::kInt32;
     else if (smax - go <= 127 && smin - go >= -127)
         out->kind = ProfileKind::kInt8;

@@ -78,8 +78,13 @@ constexpr unsigned kFull = 0xffffffffu;
 #define SWGB_GROUP_UNROLL 4
 #endif
 constexpr int kU = SWGB_GROUP_UNROLL;  // steps per block
-static_assert(kU == 4, "the staging rings move 4 columns (16 bytes of boundary) per block");
-constexpr int kAhead = 3;              // blocks between a cp.async and the first use
+#ifndef SWGB_STEP_ORDER_FENCE
+#define SWGB_STEP_ORDER_FENCE 1
+#endif
+static_assert(kU == 4 || kU == 8, "blocks move whole 16-byte chunks of 4 boundary columns");
+// blocks between a cp.async and the first use; the copies in flight plus the
+// block being read stay within six of the eight 16-byte slots of a ring
+constexpr int kAhead = kU == 4 ? 3 : 2;
 constexpr int kMaxGroups = 32 >> kMinLog2G;
 constexpr int kRingBytes = 128;        // per group and ring
 
@@ -414,10 +419,17 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 const int byte = res_ring[((uint32_t)(uintptr_t)bcol + j * dir) & (kRingBytes - 1)];
                 cres[u] = in ? min(byte, A - 1) : A;
             }
-            uint4 bw = make_uint4(0xC0000000u, 0xC0000000u, 0xC0000000u, 0xC0000000u);
-            if (gl == 0 && has_in && s < mcols)
-                bw = *reinterpret_cast<const uint4 *>(bin_ring + ((s >> 2) & 7) * 4);
-            const uint32_t bws[kU] = {bw.x, bw.y, bw.z, bw.w};
+            uint32_t bws[kU];
+#pragma unroll
+            for (int h = 0; h < kU / 4; ++h) {
+                uint4 bw = make_uint4(0xC0000000u, 0xC0000000u, 0xC0000000u, 0xC0000000u);
+                if (gl == 0 && has_in && s + 4 * h < mcols)
+                    bw = *reinterpret_cast<const uint4 *>(bin_ring + (((s >> 2) + h) & 7) * 4);
+                bws[4 * h] = bw.x;
+                bws[4 * h + 1] = bw.y;
+                bws[4 * h + 2] = bw.z;
+                bws[4 * h + 3] = bw.w;
+            }
 
             // ---- U wavefront steps, the same instructions on every lane
 #pragma unroll
@@ -434,9 +446,11 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     inF = (int)(w & 0xFFFF0000u);
                 }
                 int c = cres[u];
+#if SWGB_STEP_ORDER_FENCE
                 // keep this step's profile loads after its shuffle, so the
                 // compiler does not hoist every unrolled step's loads
                 asm volatile("" : "+r"(c) : "r"(inH));
+#endif
                 int sc[R];
                 load_scores<R, P8>(prof, c, lane, sc);
                 const int cj = kColBase - j;
