@@ -37,21 +37,22 @@
 // column leaves H = 0 and E = go, which gives the same first real column as
 // the E = -infinity boundary.
 //
-// Recurrence (Section II-B.1, Fig. 8), per cell, six instructions, E and F
-// held minus go so that the row-to-row chain is two instructions deep:
-//   E'  = viaddmax(E', ge, H_left)               E' = max(E' + ge, H_left)
-//   T   = viaddmax(H_diag, s - go, E') + go      T  = max(H_diag + s, E)
-//   F'  = viaddmax(F'_up, ge, H_up)              F' = max(F'_up + ge, H_up)
-//   H   = viaddmax_relu(F', go, T)               H  = max(F, T, 0)
-//   K   = viaddmax(H, kColBase - j, K)           end-cell key of the row
-// The profile holds s - go.  All scores are scaled by 2^16, so
-// K = (H << 16) | (kColBase - j) orders cells by larger H, then smaller column,
-// at one instruction per cell; rows are compared in ascending order with a
-// strict "greater" so the smaller row wins ties.  The plan sends a pair
-// here only when smax * min(n, m) <= 32766, |go|, |ge| <= 16383 and
-// m <= kColBase, which keeps every scaled value and key inside int32 and the
-// column part in [0, 65535) also on the pad columns a lane computes before
-// its first column (j >= -31).
+// Recurrence (Section II-B.1, Fig. 8), per cell, with H kept as H + go
+// (call it X) so that both gap updates read it directly:
+//   E   = viaddmax(E, ge, X_left)                E = max(E + ge, H_left + go)
+//   F   = viaddmax(F_up, ge, X_up)               F = max(F_up + ge, H_up + go)
+//   X   = vimax3_relu(X_diag + s', E, F) + go    H = max(H_diag + s, E, F, 0)
+//   K   = viaddmax(X, kColBase - j - go, K)      end-cell key of the row
+// with s' = s - go from the profile.  Five maxes per cell (E, F, two for
+// the three-way max with 0, the key) run on the integer ALU pipe; the adds
+// fuse into them or issue on the FMA pipe.  All scores are scaled by 2^16,
+// so K = (H << 16) | (kColBase - j) orders cells by larger H, then smaller
+// column, at one instruction per cell; rows are compared in ascending order
+// with a strict "greater" so the smaller row wins ties.  The plan sends a
+// pair here only when smax * min(n, m) <= 32766, |go|, |ge| <= 16383 and
+// n, m <= kColBase, which keeps every scaled value and key inside int32 and
+// the column part in [0, 65535) also on the pad columns a lane computes
+// before its first column (j >= -31).
 //
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
 // a_qend..a_0 and b_rend..b_0, transposed: the reversed reference prefix
@@ -223,6 +224,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     const int A = p.alphabet;
     const int go = p.gap_open, ge = p.gap_extend;
     const int goS = go * 65536, geS = ge * 65536;
+    // boundary word of "no row above": H = 0 (stored as H + go) and F = -inf
+    // (0xC000 = -16384 in the high half, -2^30 scaled)
+    const uint32_t kNoBound = 0xC0000000u | ((uint32_t)go & 0xFFFFu);
     constexpr int NT = kGroupWarps * 32;
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         // hot state: DP registers, the strip's step counters and stream cursors
         int H[R], E[R];
         uint32_t K[R];
-        int diag0 = 0, outH = 0, outF = kScaledNegInf;
+        int diag0 = goS, outH = goS, outF = kScaledNegInf;
         int s = 0, lim = 0, stop = 0, dir = 1;
         const uint8_t *bcol = p.r;  // column 0 of the current sweep
         int roff = 0;               // bcol's offset in its 16-byte chunk (mirrored if dir < 0)
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         bool live = false, rev = false, drained = false;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            H[r] = 0;
+            H[r] = goS;
             E[r] = kScaledNegInf;
             K[r] = 0u;
         }
@@ -332,12 +336,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                                  rev ? 1 : A, rev ? A : 1);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                H[r] = 0;
+                H[r] = goS;
                 E[r] = kScaledNegInf;
                 K[r] = 0u;
             }
-            diag0 = 0;
-            outH = 0;
+            diag0 = goS;
+            outH = goS;
             outF = kScaledNegInf;
             s = 0;
             lim = stop + G - 1;
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             uint32_t bws[kU];
 #pragma unroll
             for (int h = 0; h < kU / 4; ++h) {
-                uint4 bw = make_uint4(0xC0000000u, 0xC0000000u, 0xC0000000u, 0xC0000000u);
+                uint4 bw = make_uint4(kNoBound, kNoBound, kNoBound, kNoBound);
                 if (gl == 0 && has_in && s + 4 * h < mcols)
                     bw = *reinterpret_cast<const uint4 *>(bin_ring + (((s >> 2) + h) & 7) * 4);
                 bws[4 * h] = bw.x;
@@ -439,9 +443,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 int inH = __shfl_up_sync(kFull, outH, 1, G);
                 int inF = __shfl_up_sync(kFull, outF, 1, G);
                 if (gl == 0) {
-                    // previous strip's last row, or H = 0 / F' = -inf above the
-                    // first strip and outside the columns (0xC000 = -16384 << 16)
-                    const uint32_t w = in ? bws[u] : 0xC0000000u;
+                    // previous strip's last row, or H = 0 / F = -inf above the
+                    // first strip and outside the columns
+                    const uint32_t w = in ? bws[u] : kNoBound;
                     inH = (int)(w << 16);
                     inF = (int)(w & 0xFFFF0000u);
                 }
@@ -453,7 +457,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
 #endif
                 int sc[R];
                 load_scores<R, P8>(prof, c, lane, sc);
-                const int cj = kColBase - j;
+                // key column part, less go: the key of H + go is (H << 16) + cj
+                const int cjg = kColBase - j - goS;
                 int diag = diag0;
                 int F = __viaddmax_s32(inF, geS, inH);
                 int hprev = 0;
@@ -461,12 +466,11 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 for (int r = 0; r < R; ++r) {
                     if (r > 0) F = __viaddmax_s32(F, geS, hprev);
                     E[r] = __viaddmax_s32(E[r], geS, H[r]);
-                    const int T = __viaddmax_s32(diag, sc[r], E[r]) + goS;
-                    const int h = __viaddmax_s32_relu(F, goS, T);
+                    const int h = __vimax3_s32_relu(diag + sc[r], E[r], F) + goS;
                     diag = H[r];
                     H[r] = h;
                     hprev = h;
-                    K[r] = (uint32_t)__viaddmax_s32(h, cj, (int)K[r]);
+                    K[r] = (uint32_t)__viaddmax_s32(h, cjg, (int)K[r]);
                 }
                 outH = hprev;
                 outF = F;
