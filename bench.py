@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-pairs", type=int, default=0, help="oracle sample size (0 = auto)")
+    ap.add_argument("--gaps", type=int, nargs=2, metavar=("OPEN", "EXTEND"), default=None,
+                    help="override the workload's gap costs (equal values take the linear-gap kernel)")
+    ap.add_argument("--dna-scores", type=int, nargs=2, metavar=("MATCH", "MISMATCH"),
+                    default=None, help="override a DNA workload's match/mismatch scores")
+    ap.add_argument("--ends-only", action="store_true",
+                    help="score and end cell only (no reverse pass)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's own lane-group choice instead of measuring candidates")
@@ -78,7 +84,7 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_rate(batch, n_pairs: int, threads: int, gpu_res=None) -> dict:
+def oracle_rate(batch, n_pairs: int, threads: int, gpu_res=None, cols: int = 5) -> dict:
     """The CPU oracle timed on the first n_pairs pairs; with gpu_res, also
     whether the GPU's results for those pairs equal the oracle's."""
     import oracle
@@ -93,8 +99,9 @@ def oracle_rate(batch, n_pairs: int, threads: int, gpu_res=None) -> dict:
                      f"{dt:.2f} s on {threads} host threads",
            "seconds": dt}
     if gpu_res is not None:
-        out["gpu_identical_pairs"] = int(np.sum(np.all(ref == gpu_res[:n_pairs], axis=1)))
-        out["gpu_identical"] = bool(np.array_equal(ref, gpu_res[:n_pairs]))
+        a, b = ref[:, :cols], gpu_res[:n_pairs, :cols]
+        out["gpu_identical_pairs"] = int(np.sum(np.all(a == b, axis=1)))
+        out["gpu_identical"] = bool(np.array_equal(a, b))
     return out
 
 
@@ -368,6 +375,13 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     swgb.load()
     batch = wl.gen_config(args.config, n_pairs=args.pairs or None)
+    if args.dna_scores:
+        batch.matrix = wl.dna_matrix(*args.dna_scores)
+        batch.name += f"-dna{args.dna_scores[0]:+d}{args.dna_scores[1]:+d}"
+    if args.gaps:
+        batch.gap_open, batch.gap_extend = args.gaps
+        batch.name += f"-gaps{args.gaps[0]}{args.gaps[1]}"
+    flags = swgb.SW_PLAN_ENDS_ONLY if args.ends_only else 0
     cells = batch.cells
     ctx = swgb.sw_ctx_create(local)
     sms = swgb.sw_ctx_sm_count(ctx)
@@ -385,7 +399,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
     plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
                                batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
-                               swgb.SW_PLAN_GRAPH)
+                               swgb.SW_PLAN_GRAPH | flags)
     info = swgb.sw_plan_info(plan)
 
     def barrier():
@@ -405,7 +419,7 @@ def run_ours(args, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_total = float(t.item())
     res = out.T.contiguous().cpu().numpy()
-    rcells = reverse_cells(res)
+    rcells = 0 if args.ends_only else reverse_cells(res)
     value = cells * args.steps * world / t_total / 1e9
     per_launch = t_total / args.steps
 
@@ -428,7 +442,7 @@ def run_ours(args, rank, world, local):
     plain = None
     if not args.no_plain:
         pplan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
-                                    batch.gap_open, batch.gap_extend, swgb.SW_MODE_PLAIN, 0)
+                                    batch.gap_open, batch.gap_extend, swgb.SW_MODE_PLAIN, flags)
         out2 = torch.zeros_like(out)
         pt = time_plan(swgb, torch, pplan, q, r, out2, stream, max(3, args.steps // 2), 1, flush)
         same = bool(torch.equal(out, out2))
@@ -443,7 +457,7 @@ def run_ours(args, rank, world, local):
     oh = torch.zeros((5, batch.n_pairs), dtype=torch.int32).pin_memory()
     eplan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
                                 batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
-                                swgb.SW_PLAN_GRAPH)
+                                swgb.SW_PLAN_GRAPH | flags)
     for _ in range(args.warmup):
         swgb.sw_plan_execute_host(eplan, qh, rh, oh, stream)
     barrier()
@@ -461,7 +475,8 @@ def run_ours(args, rank, world, local):
     swgb.sw_plan_destroy(plan)
 
     serve = None
-    if not args.no_serve and rank == 0 and world == 1:
+    overridden = bool(args.gaps or args.dna_scores or args.ends_only or args.pairs)
+    if not args.no_serve and rank == 0 and world == 1 and not overridden:
         if args.config == 1:
             serve = serve_sweep(swgb, ctx, batch, res, args)
         else:
@@ -473,7 +488,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = cpu_cores()
         n = args.cpu_pairs or auto_cpu_pairs(batch, threads)
-        cpu = oracle_rate(batch, n, threads, gpu_res=res)
+        cpu = oracle_rate(batch, n, threads, gpu_res=res, cols=3 if args.ends_only else 5)
         cpu.pop("seconds")
 
     if rank == 0:

@@ -77,6 +77,12 @@ typedef enum {
 /* Plan flags. */
 #define SW_PLAN_GRAPH 1u /* capture the launch sequence in a CUDA graph and */
                          /* replay it while pointers and stream repeat       */
+/* Ends only: score, qend and rend, without the reverse pass (the forward
+ * sweep alone, as ADEPT's first kernel, Section III-B).  out_qstart and
+ * out_rstart are not written and may be NULL; sw_plan_execute_host copies
+ * back only the first 3 x n_pairs values.  Score-only callers use this
+ * mode too: the end cell comes with the score at no extra cost. */
+#define SW_PLAN_ENDS_ONLY 2u
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_plan sw_plan;

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "SW_OK", -1: "SW_EINVAL", -2: "SW_ERANGE", -3: "SW_ENOMEM", -
                 -5: "SW_ETIMEOUT", -6: "SW_EBUDGET"}
 SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
 SW_PLAN_GRAPH = 1
+SW_PLAN_ENDS_ONLY = 2
 SW_MAX_LEN = 65535
 
 # Every function the library exports, with its ctypes signature.

@@ -229,6 +229,7 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     p->ge = gap_extend;
     p->mode = mode == SW_MODE_AUTO ? SW_MODE_BATCHED : mode;
     p->flags = flags;
+    p->hp.ends_only = (flags & SW_PLAN_ENDS_ONLY) != 0;
     std::memcpy(p->mat, score_matrix, (size_t)alphabet_size * alphabet_size);
     if ((rc = upload(&p->d_pairs, p->hp.pairs)) || (rc = upload(&p->d_classes, p->hp.classes)) ||
         (rc = upload(&p->d_plain, p->hp.plain))) {
@@ -264,8 +265,8 @@ int sw_plan_execute(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seqs,
                     int32_t *out_qstart, int32_t *out_rstart, void *stream) {
     if (!p) return fail(SW_EINVAL, "sw_plan_execute: plan is NULL");
     if (p->n_pairs == 0) return SW_OK;
-    if (!q_seqs || !r_seqs || !out_score || !out_qend || !out_rend || !out_qstart ||
-        !out_rstart)
+    if (!q_seqs || !r_seqs || !out_score || !out_qend || !out_rend ||
+        (!p->hp.ends_only && (!out_qstart || !out_rstart)))
         return fail(SW_EINVAL, "sw_plan_execute: NULL device pointer");
     DeviceGuard g(p->ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", p->ctx->device);
@@ -331,7 +332,9 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
     int rc = sw_plan_execute(p, p->d_q, p->d_r, p->d_out, p->d_out + n, p->d_out + 2 * n,
                              p->d_out + 3 * n, p->d_out + 4 * n, stream);
     if (rc != SW_OK) return rc;
-    SW_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out, (size_t)5 * n * sizeof(int32_t),
+    // with SW_PLAN_ENDS_ONLY the start rows are not computed and not copied
+    const int rows = p->hp.ends_only ? 3 : 5;
+    SW_CUDA_TRY(cudaMemcpyAsync(out_host, p->d_out, (size_t)rows * n * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, s));
     SW_CUDA_TRY(cudaStreamSynchronize(s));
     return SW_OK;

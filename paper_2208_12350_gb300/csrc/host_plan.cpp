@@ -83,6 +83,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         n[i] = (int32_t)(q_offsets[i + 1] - q_offsets[i]);
         m[i] = (int32_t)(r_offsets[i + 1] - r_offsets[i]);
     }
+    out->linear = go == ge;
     out->q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;
     out->r_bytes = n_pairs > 0 ? r_offsets[n_pairs] : 0;
 #ifndef SWGB_SMALL_ALPHABET_INT32
@@ -106,7 +107,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
             any = group_path_eligible(n[i], m[i], smax, go, ge);
         if (any) {
             int smem = 0;
-            bps = group_blocks_per_sm(out->kind, A, &smem);
+            bps = group_blocks_per_sm(out->kind, go == ge, A, &smem);
             if (bps < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
             group_fits = bps > 0;
         }
@@ -183,8 +184,9 @@ cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_
         gp.alphabet = A;
         gp.gap_open = go;
         gp.gap_extend = ge;
+        gp.ends_only = hp.ends_only ? 1 : 0;
         std::memcpy(gp.mat, mat, (size_t)A * A);
-        e = launch_group(gp, hp.kind, hp.grid, s);
+        e = launch_group(gp, hp.kind, hp.linear, hp.grid, s);
         if (e != cudaSuccess) return e;
     }
     if (!hp.plain.empty()) {
@@ -199,6 +201,7 @@ cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_
         pp.alphabet = A;
         pp.gap_open = go;
         pp.gap_extend = ge;
+        pp.ends_only = hp.ends_only ? 1 : 0;
         std::memcpy(pp.mat, mat, (size_t)A * A);
         e = launch_plain(pp, hp.plain_threads, hp.plain_kmax, s);
     }

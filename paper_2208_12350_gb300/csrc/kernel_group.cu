@@ -217,7 +217,7 @@ constexpr int kColdWords = 2 * 2 + 11;  // 32-bit words per lane
 
 }  // namespace
 
-template <int R, bool P8>
+template <int R, bool P8, bool LIN>
 __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     sw_group_kernel(const __grid_constant__ GroupParams p) {
     extern __shared__ __align__(16) char smem_group[];
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 const int j = s + u - gl;
                 const bool in = (unsigned)j < (unsigned)mcols;
                 int inH = __shfl_up_sync(kFull, outH, 1, G);
-                int inF = __shfl_up_sync(kFull, outF, 1, G);
+                int inF = LIN ? 0 : __shfl_up_sync(kFull, outF, 1, G);
                 if (gl == 0) {
                     // previous strip's last row, or H = 0 / F = -inf above the
                     // first strip and outside the columns
@@ -460,13 +460,19 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 // key column part, less go: the key of H + go is (H << 16) + cj
                 const int cjg = kColBase - j - goS;
                 int diag = diag0;
-                int F = __viaddmax_s32(inF, geS, inH);
-                int hprev = 0;
+                int F = LIN ? 0 : __viaddmax_s32(inF, geS, inH);
+                int hprev = inH;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (r > 0) F = __viaddmax_s32(F, geS, hprev);
-                    E[r] = __viaddmax_s32(E[r], geS, H[r]);
-                    const int h = __vimax3_s32_relu(diag + sc[r], E[r], F) + goS;
+                    int h;
+                    if constexpr (LIN) {
+                        // go == ge: E = H_left + go and F = H_up + go exactly
+                        h = __vimax3_s32_relu(diag + sc[r], H[r], hprev) + goS;
+                    } else {
+                        if (r > 0) F = __viaddmax_s32(F, geS, hprev);
+                        E[r] = __viaddmax_s32(E[r], geS, H[r]);
+                        h = __vimax3_s32_relu(diag + sc[r], E[r], F) + goS;
+                    }
                     diag = H[r];
                     H[r] = h;
                     hprev = h;
@@ -549,6 +555,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                         if (S > 0) {
                             cold.qend[t] = qend;
                             cold.rend[t] = rend;
+                        }
+                        if (S > 0 && !p.ends_only) {
                             cold.target[t] = S;
                             rev = true;
                             done = false;
@@ -564,7 +572,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             int o0 = 0, o1 = -1, o2 = -1, o3 = -1, o4 = -1;
                             if (S > 0) {
                                 const int qend = cold.qend[t], rend = cold.rend[t];
-                                if (!rev_found) atomicOr(p.status, kStatusReverseMismatch);
+                                if (!rev_found && !p.ends_only)
+                                    atomicOr(p.status, kStatusReverseMismatch);
                                 o0 = S;
                                 o1 = qend;
                                 o2 = rend;
@@ -574,8 +583,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                             p.out.score[id] = o0;
                             p.out.qend[id] = o1;
                             p.out.rend[id] = o2;
-                            p.out.qstart[id] = o3;
-                            p.out.rstart[id] = o4;
+                            if (!p.ends_only) {
+                                p.out.qstart[id] = o3;
+                                p.out.rstart[id] = o4;
+                            }
                         }
                         live = false;
                         rev = false;
@@ -606,20 +617,30 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
 // with different alphabets (from several host threads) never lowers it
 // under a launch that needs more.  Occupancy per (profile, alphabet) is
 // cached per device.
-int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes) {
+namespace {
+// the four instantiations, indexed by (int8 profile, linear gaps)
+using GroupKernel = void (*)(GroupParams);
+GroupKernel group_kernel_of(bool p8, bool lin) {
+    if (p8) return lin ? sw_group_kernel<kRows, true, true> : sw_group_kernel<kRows, true, false>;
+    return lin ? sw_group_kernel<kRows, false, true> : sw_group_kernel<kRows, false, false>;
+}
+}  // namespace
+
+int group_blocks_per_sm(ProfileKind kind, bool linear, int alphabet, int *smem_bytes) {
     const size_t smem = group_smem_bytes(kind, alphabet);
     if (smem_bytes) *smem_bytes = (int)smem;
     if (alphabet < 1 || alphabet > kMaxAlphabet) return -1;
     constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static int cache[kMaxDevices][2][kMaxAlphabet + 1];
-    static bool raised[kMaxDevices][2];
+    static int cache[kMaxDevices][4][kMaxAlphabet + 1];
+    static bool raised[kMaxDevices][4];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
-    const int ki = kind == ProfileKind::kInt8 ? 1 : 0;
+    const bool p8 = kind == ProfileKind::kInt8;
+    const int ki = (p8 ? 2 : 0) + (linear ? 1 : 0);
+    const GroupKernel fn = group_kernel_of(p8, linear);
     std::lock_guard<std::mutex> lk(mu);
     if (cache[dev][ki][alphabet] > 0) return cache[dev][ki][alphabet];
-    cudaError_t e = cudaSuccess;
     int optin = 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
         cudaSuccess)
@@ -627,30 +648,24 @@ int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes) {
     if (smem > (size_t)optin) return 0;  // this alphabet's profile does not fit
     if (!raised[dev][ki]) {
         const int top = (int)std::min<size_t>(group_smem_bytes(kind, kMaxAlphabet), (size_t)optin);
-        e = ki ? cudaFuncSetAttribute(sw_group_kernel<kRows, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, top)
-               : cudaFuncSetAttribute(sw_group_kernel<kRows, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, top);
-        if (e != cudaSuccess) return -1;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, top) !=
+            cudaSuccess)
+            return -1;
         raised[dev][ki] = true;
     }
     int blocks = 0;
-    e = ki ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sw_group_kernel<kRows, true>,
-                                                           kGroupWarps * 32, smem)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sw_group_kernel<kRows, false>,
-                                                           kGroupWarps * 32, smem);
-    if (e != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kGroupWarps * 32, smem) !=
+        cudaSuccess)
+        return -1;
     cache[dev][ki][alphabet] = blocks;
     return blocks;
 }
 
-cudaError_t launch_group(const GroupParams &p, ProfileKind kind, int grid, cudaStream_t s) {
+cudaError_t launch_group(const GroupParams &p, ProfileKind kind, bool linear, int grid,
+                         cudaStream_t s) {
     if (p.n_classes <= 0 || grid <= 0) return cudaSuccess;
     const size_t smem = group_smem_bytes(kind, p.alphabet);
-    if (kind == ProfileKind::kInt8)
-        sw_group_kernel<kRows, true><<<grid, kGroupWarps * 32, smem, s>>>(p);
-    else
-        sw_group_kernel<kRows, false><<<grid, kGroupWarps * 32, smem, s>>>(p);
+    group_kernel_of(kind == ProfileKind::kInt8, linear)<<<grid, kGroupWarps * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -149,7 +149,11 @@ __global__ void __launch_bounds__(KMAX == 1 ? 1024 : kPlainWideThreads)
                                            p.gap_extend, xH, xF, red);
     const int S = (int)(key >> 32);
     int o0 = 0, o1 = -1, o2 = -1, o3 = -1, o4 = -1;
-    if (S > 0) {  // block-uniform
+    if (S > 0 && p.ends_only) {
+        o0 = S;
+        o1 = 0xFFFF - (int)(key & 0xFFFF);
+        o2 = 0xFFFF - (int)((key >> 16) & 0xFFFF);
+    } else if (S > 0) {  // block-uniform
         const int rend = 0xFFFF - (int)((key >> 16) & 0xFFFF);
         const int qend = 0xFFFF - (int)(key & 0xFFFF);
         const uint64_t k2 = plain_sweep<KMAX>(q + qend, -1, qend + 1, r + rend, -1, rend + 1,
@@ -168,8 +172,10 @@ __global__ void __launch_bounds__(KMAX == 1 ? 1024 : kPlainWideThreads)
         p.out.score[pi.id] = o0;
         p.out.qend[pi.id] = o1;
         p.out.rend[pi.id] = o2;
-        p.out.qstart[pi.id] = o3;
-        p.out.rstart[pi.id] = o4;
+        if (!p.ends_only) {
+            p.out.qstart[pi.id] = o3;
+            p.out.rstart[pi.id] = o4;
+        }
     }
 }
 

@@ -75,6 +75,7 @@ struct GroupParams {
     Outputs out;
     int32_t alphabet;
     int32_t gap_open, gap_extend;  // unscaled, <= 0
+    int32_t ends_only;             // skip the reverse pass (qstart/rstart not written)
     int8_t mat[kMaxAlphabet * kMaxAlphabet];
 };
 
@@ -87,6 +88,7 @@ struct PlainParams {
     Outputs out;
     int32_t alphabet;
     int32_t gap_open, gap_extend;
+    int32_t ends_only;
     int8_t mat[kMaxAlphabet * kMaxAlphabet];
 };
 
@@ -150,6 +152,8 @@ struct HostPlan {
     int64_t scratch_words = 0;       // strip-boundary words the pairs need
     int plain_threads = 32, plain_kmax = 1;
     int64_t q_bytes = 0, r_bytes = 0;  // residues the offsets span
+    bool linear = false;     // gap_open == gap_extend: the kernel without E and F
+    bool ends_only = false;  // no reverse pass (set by the caller after planning)
 };
 // Where a HostPlan's tables live on the device.
 struct DeviceTables {
@@ -162,8 +166,10 @@ struct DeviceTables {
 };
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_group(const GroupParams &p, ProfileKind kind, int grid, cudaStream_t s);
-int group_blocks_per_sm(ProfileKind kind, int alphabet, int *smem_bytes);
+// linear: gap_open == gap_extend, the instantiation without E and F
+cudaError_t launch_group(const GroupParams &p, ProfileKind kind, bool linear, int grid,
+                         cudaStream_t s);
+int group_blocks_per_sm(ProfileKind kind, bool linear, int alphabet, int *smem_bytes);
 size_t group_smem_bytes(ProfileKind kind, int alphabet);
 
 cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_max,

@@ -274,3 +274,55 @@ def test_check_residues(gpu_lib):
     gpu_lib.sw_check_residues(s, s.numel(), 4, bad)
     torch.cuda.synchronize()
     assert int(bad.item()) == 3
+
+
+def _with_gaps(b, go, ge, matrix=None, name="regapped"):
+    return wl.make_batch(name, [b.pair(i)[0] for i in range(b.n_pairs)],
+                         [b.pair(i)[1] for i in range(b.n_pairs)],
+                         b.matrix if matrix is None else matrix, go, ge)
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=[f"G{1 << t[0] if t[0] >= 0 else 'auto'}-cap{t[1]:g}"
+                                                 for t in TUNINGS])
+def test_linear_gaps_take_the_linear_kernel(gpu_lib, ctx, tuning):
+    """gap_open == gap_extend runs the instantiation without E and F; it must
+    equal the Gotoh oracle (which keeps E and F) on DNA with the paper's
+    Fig. 2 scoring (+2/-2, gap -1) and on protein with BLOSUM62 and gap -4,
+    with lengths spanning several strips, under every lane-group width."""
+    dna = _with_gaps(wl.gen_config(1, n_pairs=400), -1, -1,
+                     matrix=wl.dna_matrix(2, -2), name="fig2-scoring")
+    prot = _with_gaps(wl.gen_config(2, n_pairs=300), -4, -4, name="blosum-linear")
+    for b in (dna, prot):
+        expect = oracle.align_workload(b)
+        got, info = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_BATCHED, tuning=tuning)
+        assert info["group_pairs"] == b.n_pairs
+        assert_same(got, expect, f"{b.name} tuning {tuning}")
+
+
+@pytest.mark.parametrize("k", [0, 2])
+def test_ends_only_plans(gpu_lib, ctx, k):
+    """SW_PLAN_ENDS_ONLY: score, qend, rend equal the oracle's; the start
+    outputs are left untouched (batched, plain, graph and host-buffer forms)."""
+    import torch
+    b = wl.gen_config(k, n_pairs=600)
+    expect = oracle.align_workload(b)
+    for mode in (gpu_lib.SW_MODE_BATCHED, gpu_lib.SW_MODE_PLAIN):
+        flags = gpu_lib.SW_PLAN_ENDS_ONLY | gpu_lib.SW_PLAN_GRAPH
+        al = gpu_lib.Aligner(b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix, b.gap_open,
+                             b.gap_extend, mode=mode, flags=flags, ctx=ctx)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            al.run(stream=s)
+        s.synchronize()
+        got = al.results()
+        assert_same(got[:, :3], expect[:, :3], f"ends only, mode {mode}")
+        assert np.all(got[:, 3:] == -7), "start outputs were written"
+        qh = torch.from_numpy(b.q_seqs).pin_memory()
+        rh = torch.from_numpy(b.r_seqs).pin_memory()
+        oh = torch.full((5, b.n_pairs), -9, dtype=torch.int32).pin_memory()
+        gpu_lib.sw_plan_execute_host(al.plan, qh, rh, oh, s)
+        host = oh.numpy().T
+        assert_same(host[:, :3], expect[:, :3], f"ends only, host buffers, mode {mode}")
+        assert np.all(host[:, 3:] == -9)
+        al.close()
+    assert gpu_lib.sw_ctx_status(ctx) == 0
