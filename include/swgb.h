@@ -312,6 +312,39 @@ int sw_server_launches(sw_server *server, int64_t *launches, int64_t *pairs_laun
 int sw_server_destroy(sw_server *server);
 
 /*
+ * Traceback: the alignment itself (Fig. 2(c)'s traceback from the maximal
+ * cell), as a CIGAR per pair, for a batch already aligned.
+ *
+ * results: HOST, 5 x n_pairs int32 rows (score, qend, rend, qstart,
+ * rstart), as sw_plan_execute writes them.  For each pair with score > 0
+ * the alignment is the best global alignment, under the same affine
+ * scoring, of q[qstart..qend] against r[rstart..rend] (its score is the
+ * pair's score); among co-optimal ones the walk back from the last cell
+ * takes the diagonal first, then a gap in the query (D), then a gap in the
+ * reference (I), and inside a gap steps back out where the run opened.
+ * Ops are run-length encoded as (length << 4) | code, code M = 0, I = 1
+ * (query residue only), D = 2 (reference residue only), first op first.
+ *
+ * sw_cigar_capacity: HOST helper; offsets[0..n_pairs] with room
+ * (qend - qstart + 1) + (rend - rstart + 1) ops for each aligned pair, 0
+ * for the others.
+ * sw_traceback: q_seqs, r_seqs, out_ops, out_n_ops on the DEVICE; offsets,
+ * matrix, results and cigar_offsets on the HOST.  Pair p's ops go to
+ * out_ops[cigar_offsets[p] ..], their count to out_n_ops[p] (0 when the
+ * score is 0).  The library allocates its scratch (choice bits of each
+ * span, at most about 1 GiB per launch) for the call and synchronises
+ * `stream` before returning.  Errors: SW_EINVAL (bad arguments), SW_ERANGE
+ * (coordinates outside a pair, or room below the pair's need), SW_ENOMEM,
+ * SW_ECUDA.
+ */
+int sw_cigar_capacity(const int32_t *results, int32_t n_pairs, int64_t *offsets);
+int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
+                 const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                 const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                 int32_t gap_extend, const int32_t *results, const int64_t *cigar_offsets,
+                 uint32_t *out_ops, int32_t *out_n_ops, void *stream);
+
+/*
  * Integer issue-rate microbenchmark on `device` (made current for the call;
  * synchronous).  op: 0 = 32-bit add, 1 = 32-bit max, 2 = __viaddmax_s32
  * (add then max), 3 = __vimax3_s32_relu, 4 = __viaddmax_s16x2,

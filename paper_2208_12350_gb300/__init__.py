@@ -63,6 +63,9 @@ SIGNATURES = {
     "sw_server_launches": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sw_server_destroy": ([_P], ctypes.c_int),
+    "sw_cigar_capacity": ([_P, _I32, _P], ctypes.c_int),
+    "sw_traceback": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P],
+                     ctypes.c_int),
     "sw_microbench_int": ([_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -334,6 +337,42 @@ def sw_server_launches(server: int) -> dict:
 
 def sw_server_destroy(server: int) -> None:
     _check(load().sw_server_destroy(server), "sw_server_destroy")
+
+
+# --------------------------------------------------------------- traceback
+
+CIGAR_CODES = "MID"
+
+
+def sw_cigar_capacity(results) -> np.ndarray:
+    """Host (5, n_pairs) int32 results -> int64 offsets of room per pair."""
+    res = np.ascontiguousarray(results, dtype=np.int32)
+    n = res.shape[1]
+    off = np.zeros(n + 1, dtype=np.int64)
+    _check(load().sw_cigar_capacity(res.ctypes.data, n, off.ctypes.data), "sw_cigar_capacity")
+    return off
+
+
+def sw_traceback(ctx: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, gap_open: int,
+                 gap_extend: int, results, cigar_offsets, out_ops, out_n_ops,
+                 stream=None) -> None:
+    """Sequences and outputs on the device; offsets, matrix, results (5, n)
+    and cigar_offsets on the host.  Synchronises the stream."""
+    qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
+    mat = _host_i8(score_matrix)
+    res = np.ascontiguousarray(results, dtype=np.int32)
+    co = _host_i64(cigar_offsets)
+    _check(load().sw_traceback(ctx, _addr(q_seqs), qo.ctypes.data, _addr(r_seqs), ro.ctypes.data,
+                               len(qo) - 1, mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
+                               res.ctypes.data, co.ctypes.data, _addr(out_ops), _addr(out_n_ops),
+                               _stream(stream)), "sw_traceback")
+
+
+def cigar_strings(ops, offsets, n_ops) -> list[str]:
+    """Per-pair CIGAR text ('12M1D3M') from run-length ops."""
+    ops = np.asarray(ops)
+    return ["".join(f"{int(o) >> 4}{CIGAR_CODES[int(o) & 15]}"
+                    for o in ops[offsets[p]:offsets[p] + n_ops[p]]) for p in range(len(n_ops))]
 
 
 # ----------------------------------------------------------------- helpers

@@ -83,6 +83,10 @@ struct sw_ctx {
     std::vector<std::pair<sw_plan *, cudaEvent_t>> retired;
 };
 
+namespace swgb {
+int ctx_device(const ::sw_ctx *ctx) { return ctx->device; }
+}  // namespace swgb
+
 struct sw_plan {
     sw_ctx *ctx = nullptr;
     int32_t n_pairs = 0;

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+struct sw_ctx;  // the library context (include/swgb.h)
+
 namespace swgb {
 
 // Scores on the batched path are held scaled by 2^16 so that the low half
@@ -177,6 +179,7 @@ cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_
 size_t plain_smem_bytes(int threads, int alphabet);
 
 int set_error(int code, const char *msg);  // message for sw_last_error()
+int ctx_device(const ::sw_ctx *ctx);          // the CUDA device a context works on
 
 // Checks the arguments and plans a batch (no device allocation; queries the
 // group kernel's occupancy on the current device).  Returns an sw_status;
