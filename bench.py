@@ -57,6 +57,8 @@ def parse():
                     default=None, help="override a DNA workload's match/mismatch scores")
     ap.add_argument("--ends-only", action="store_true",
                     help="score and end cell only (no reverse pass)")
+    ap.add_argument("--cigar", action="store_true",
+                    help="also time the traceback (CIGAR) of every aligned pair")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's own lane-group choice instead of measuring candidates")
@@ -474,6 +476,29 @@ def run_ours(args, rank, world, local):
 
     swgb.sw_plan_destroy(plan)
 
+    cigar = None
+    if args.cigar and not args.ends_only:
+        # traceback of every aligned pair: cells = the spans' global DP
+        res5 = np.ascontiguousarray(res.T)
+        coff = swgb.sw_cigar_capacity(res5)
+        ops = torch.zeros(max(1, int(coff[-1])), dtype=torch.int32, device=dev)
+        nops = torch.zeros(batch.n_pairs, dtype=torch.int32, device=dev)
+        ok = res[:, 0] > 0
+        span_cells = int(np.sum((res[ok, 1] - res[ok, 3] + 1).astype(np.int64) *
+                                (res[ok, 2] - res[ok, 4] + 1)))
+        swgb.sw_traceback(ctx, q, batch.q_offsets, r, batch.r_offsets, batch.matrix,
+                          batch.gap_open, batch.gap_extend, res5, coff, ops, nops, stream)
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            swgb.sw_traceback(ctx, q, batch.q_offsets, r, batch.r_offsets, batch.matrix,
+                              batch.gap_open, batch.gap_extend, res5, coff, ops, nops, stream)
+        dt = (time.perf_counter() - t0) / reps
+        cigar = {"value": span_cells / dt / 1e9, "unit": "GCUPS (span cells)", "ms": dt * 1e3,
+                 "span_cells": span_cells, "pairs": int(ok.sum()),
+                 "ops": int(nops.sum().item()),
+                 "note": "host-timed blocking call incl. scratch allocation"}
+
     serve = None
     overridden = bool(args.gaps or args.dna_scores or args.ends_only or args.pairs)
     if not args.no_serve and rank == 0 and world == 1 and not overridden:
@@ -503,7 +528,8 @@ def run_ours(args, rank, world, local):
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "clocks": clk,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "cigar": cigar,
+                "clocks": clk,
                 "gpu_launches": info["launches"] * args.steps}
         print(json.dumps(line), flush=True)
     if world > 1:
