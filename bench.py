@@ -11,8 +11,9 @@ the CPU oracle timed on this host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank runs the full workload on its own GPU
-(weak scaling, no collective on the data path); rank 0 prints the line.
+Under torchrun (N > 1) the workload grows to N times the per-GPU size and is
+split across the ranks by longest-processing-time over n*m (weak scaling,
+no collective on the data path); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -376,7 +377,20 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     swgb.load()
-    batch = wl.gen_config(args.config, n_pairs=args.pairs or None)
+    if world > 1:
+        # weak scaling: a global workload of world x the per-GPU size, split by
+        # longest-processing-time over n*m so every rank gets the same DP work
+        from paper_2208_12350_gb300 import shard
+        per = args.pairs or wl.CONFIGS[args.config]["n_pairs"]
+        full = wl.gen_config(args.config, n_pairs=per * world)
+        mine = shard.lpt_partition(shard.pair_costs(full.q_offsets, full.r_offsets), world)[rank]
+        q_, qo_, r_, ro_ = shard.shard_batch(full.q_seqs, full.q_offsets, full.r_seqs,
+                                             full.r_offsets, mine)
+        batch = wl.Batch(full.name, q_, qo_, r_, ro_, full.matrix,
+                         full.gap_open, full.gap_extend, full.planted[mine])
+        del full
+    else:
+        batch = wl.gen_config(args.config, n_pairs=args.pairs or None)
     if args.dna_scores:
         batch.matrix = wl.dna_matrix(*args.dna_scores)
         batch.name += f"-dna{args.dna_scores[0]:+d}{args.dna_scores[1]:+d}"
@@ -422,7 +436,12 @@ def run_ours(args, rank, world, local):
         t_total = float(t.item())
     res = out.T.contiguous().cpu().numpy()
     rcells = 0 if args.ends_only else reverse_cells(res)
-    value = cells * args.steps * world / t_total / 1e9
+    job_cells = cells
+    if world > 1:
+        c = torch.tensor([cells], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(c)
+        job_cells = int(c.item())
+    value = job_cells * args.steps / t_total / 1e9
     per_launch = t_total / args.steps
 
     # --- integer roofline of the batched kernel (events timed live above)
@@ -470,7 +489,7 @@ def run_ours(args, rank, world, local):
     e2e_t = time.perf_counter() - t0
     e2e_same = bool(np.array_equal(oh.numpy().T, res))
     swgb.sw_plan_destroy(eplan)
-    e2e = {"value": cells * args.steps * world / e2e_t / 1e9, "unit": "GCUPS",
+    e2e = {"value": job_cells * args.steps / e2e_t / 1e9, "unit": "GCUPS",
            "h2d_bytes_per_step": int(batch.q_seqs.nbytes + batch.r_seqs.nbytes),
            "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same}
 
@@ -524,6 +543,8 @@ def run_ours(args, rank, world, local):
                 "config": {"workload": batch.name, "pairs": batch.n_pairs,
                            "forward_cells": cells, "mode": "batched persistent + CUDA graph",
                            "l2": "flushed between steps (512 MB write)", "sms": sms,
+                           "shards": (f"{world} LPT shards of {world} x the per-GPU pairs"
+                                      if world > 1 else None),
                            "tuning": tune,
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
