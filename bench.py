@@ -215,14 +215,15 @@ def profiled_traffic(batch, tune) -> int | None:
         return None
     text = open(path).read()
     sha = re.search(r"kernel_sha256: ([0-9a-f]{64})", text)
-    tun = re.search(r"tuning: narrow_log2g=(-?\d+) cap_fraction=([0-9.e+]+)", text)
+    tun = re.search(r"tuning: narrow_log2g=(-?\d+) cap_fraction=([0-9.e+]+|any)", text)
     byt = re.search(r"dram_bytes_per_launch: (\d+)", text)
     if not (sha and tun and byt):
         return None
     if sha.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
         return None
-    if int(tun.group(1)) != tune["narrow_log2g"] or \
-            abs(float(tun.group(2)) - tune["cap_fraction"]) > 1e-9:
+    if int(tun.group(1)) != tune["narrow_log2g"]:
+        return None
+    if tun.group(2) != "any" and abs(float(tun.group(2)) - tune["cap_fraction"]) > 1e-9:
         return None
     return int(byt.group(1))
 

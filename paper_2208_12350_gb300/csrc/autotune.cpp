@@ -34,9 +34,14 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
     return h;
 }
 
+// Part of every cache key: a tuning measured on another kernel build is not
+// reused.  Changed whenever the batched kernel's code changes.
+constexpr char kKernelRevision[] = "group-kernel-r8 H+go / transposed reverse / linear instantiation";
+
 std::string batch_key(const char *gpu, int sms, const int64_t *qo, const int64_t *ro, int n_pairs,
                       const int8_t *mat, int A, int go, int ge) {
     uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, kKernelRevision, sizeof kKernelRevision - 1);
     h = fnv1a(h, gpu, std::strlen(gpu));
     h = fnv1a(h, &sms, sizeof sms);
     h = fnv1a(h, &n_pairs, sizeof n_pairs);

@@ -52,7 +52,7 @@
 // pair here only when smax * min(n, m) <= 32766, |go|, |ge| <= 16383 and
 // n, m <= kColBase, which keeps every scaled value and key inside int32 and
 // the column part in [0, 65535) also on the pad columns a lane computes
-// before its first column (j >= -31).
+// before its first column (j >= -63).
 //
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
 // a_qend..a_0 and b_rend..b_0, transposed: the reversed reference prefix
@@ -82,6 +82,15 @@ constexpr int kU = SWGB_GROUP_UNROLL;  // steps per block
 #ifndef SWGB_STEP_ORDER_FENCE
 #define SWGB_STEP_ORDER_FENCE 1
 #endif
+#ifndef SWGB_SPLIT_ROWS
+#define SWGB_SPLIT_ROWS 0
+#endif
+// A lane's R rows as two halves a column apart (2: two independent row
+// chains per step) or one block of R rows (1).  Measured on 100k and 200k
+// DNA pairs, the split form was 0.2 % and 1.1 % slower, so it is off; it
+// stays as a build option (int32 profile only).
+template <bool P8>
+__host__ __device__ constexpr int halves_of() { return (SWGB_SPLIT_ROWS && !P8) ? 2 : 1; }
 static_assert(kU == 4 || kU == 8, "blocks move whole 16-byte chunks of 4 boundary columns");
 // blocks between a cp.async and the first use; the copies in flight plus the
 // block being read stay within six of the eight 16-byte slots of a ring
@@ -203,6 +212,40 @@ __device__ __forceinline__ void load_scores(const char *prof, int c, int lane, i
     }
 }
 
+// Scores of the lane's rows with the upper half of the rows against column
+// residue c0 and the lower half against c1 (c0 == c1 for one block of rows).
+template <int R, bool P8, int HALVES>
+__device__ __forceinline__ void load_scores_halves(const char *prof, int c0, int c1, int lane,
+                                                   int (&sc)[R]) {
+    if constexpr (HALVES == 1) {
+        load_scores<R, P8>(prof, c0, lane, sc);
+    } else if constexpr (P8) {
+        static_assert(R == 16, "split int8 profile rows assume 16 rows per lane");
+        const uint2 w0 = *reinterpret_cast<const uint2 *>(prof + ((size_t)c0 * 32 + lane) * 16);
+        const uint2 w1 = *reinterpret_cast<const uint2 *>(prof + ((size_t)c1 * 32 + lane) * 16 + 8);
+        const uint32_t ws[4] = {w0.x, w0.y, w1.x, w1.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sc[4 * k + 0] = byte_hi<0>(ws[k]);
+            sc[4 * k + 1] = byte_hi<1>(ws[k]);
+            sc[4 * k + 2] = byte_hi<2>(ws[k]);
+            sc[4 * k + 3] = byte_hi<3>(ws[k]);
+        }
+    } else {
+        static_assert(R % 8 == 0, "split int32 profile rows need whole 4-row chunks per half");
+#pragma unroll
+        for (int k = 0; k < R / 4; ++k) {
+            const int c = k < R / 8 ? c0 : c1;
+            const int4 v = *reinterpret_cast<const int4 *>(
+                prof + (((size_t)c * (R / 4) + k) * 32 + lane) * 16);
+            sc[4 * k + 0] = v.x;
+            sc[4 * k + 1] = v.y;
+            sc[4 * k + 2] = v.z;
+            sc[4 * k + 3] = v.w;
+        }
+    }
+}
+
 // Per-lane bookkeeping of a group that only the strip and sweep transitions
 // read: kept in shared memory (one array per field, indexed by thread) so
 // the step loop's registers hold the DP state alone.
@@ -221,6 +264,7 @@ template <int R, bool P8, bool LIN>
 __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     sw_group_kernel(const __grid_constant__ GroupParams p) {
     extern __shared__ __align__(16) char smem_group[];
+    constexpr int kHalves = halves_of<P8>();
     const int A = p.alphabet;
     const int go = p.gap_open, ge = p.gap_extend;
     const int goS = go * 65536, geS = ge * 65536;
@@ -280,6 +324,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         int H[R], E[R];
         uint32_t K[R];
         int diag0 = goS, outH = goS, outF = kScaledNegInf;
+        // split rows: the upper half's last row (H + go and F) at the lower
+        // half's column (from the previous step) and one column earlier, and
+        // the column residue the lower half takes next
+        int midH = goS, midF = kScaledNegInf, midD = goS, ccarry = A;
         int s = 0, lim = 0, stop = 0, dir = 1;
         const uint8_t *bcol = p.r;  // column 0 of the current sweep
         int roff = 0;               // bcol's offset in its 16-byte chunk (mirrored if dir < 0)
@@ -343,8 +391,13 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             diag0 = goS;
             outH = goS;
             outF = kScaledNegInf;
+            midH = goS;
+            midF = kScaledNegInf;
+            midD = goS;
+            ccarry = A;
             s = 0;
-            lim = stop + G - 1;
+            // the lane's last row reaches the last column kHalves * G - 1 steps late
+            lim = stop + kHalves * G - 1;
             const int m4 = (m + 3) & ~3;
             uint32_t *bnd = cold.bnd[t];
             bin = bnd + ((ps + 1) & 1) * m4;
@@ -415,10 +468,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             cp_async_wait<kAhead>();
             __syncwarp();
 
+            // column residues of the upper rows (the lower half takes each one
+            // step later, so its residue is the upper half's of the step before)
             int cres[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int j = s + u - gl;
+                const int j = s + u - kHalves * gl;
                 const bool in = (unsigned)j < (unsigned)mcols;
                 const int byte = res_ring[((uint32_t)(uintptr_t)bcol + j * dir) & (kRingBytes - 1)];
                 cres[u] = in ? min(byte, A - 1) : A;
@@ -435,35 +490,43 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 bws[4 * h + 3] = bw.w;
             }
 
-            // ---- U wavefront steps, the same instructions on every lane
+            // ---- U wavefront steps, the same instructions on every lane.  With
+            // split rows, rows [0, R/2) work on column j0 = s - 2 gl and rows
+            // [R/2, R) on j0 - 1: two independent row chains per step, the
+            // lower one fed by the upper one's last row of the step before.
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const int j = s + u - gl;
-                const bool in = (unsigned)j < (unsigned)mcols;
+                constexpr int RH = R / kHalves;
+                const int j0 = s + u - kHalves * gl;  // column of the upper rows
+                const int j1 = j0 - (kHalves - 1);    // column of the lane's last row
+                const bool in0 = (unsigned)j0 < (unsigned)mcols;
+                const bool in1 = (unsigned)j1 < (unsigned)mcols;
                 int inH = __shfl_up_sync(kFull, outH, 1, G);
                 int inF = LIN ? 0 : __shfl_up_sync(kFull, outF, 1, G);
                 if (gl == 0) {
                     // previous strip's last row, or H = 0 / F = -inf above the
                     // first strip and outside the columns
-                    const uint32_t w = in ? bws[u] : kNoBound;
+                    const uint32_t w = in0 ? bws[u] : kNoBound;
                     inH = (int)(w << 16);
                     inF = (int)(w & 0xFFFF0000u);
                 }
-                int c = cres[u];
+                int c0 = cres[u];
+                int c1 = kHalves == 2 ? (u == 0 ? ccarry : cres[u - 1]) : c0;
 #if SWGB_STEP_ORDER_FENCE
                 // keep this step's profile loads after its shuffle, so the
                 // compiler does not hoist every unrolled step's loads
-                asm volatile("" : "+r"(c) : "r"(inH));
+                asm volatile("" : "+r"(c0), "+r"(c1) : "r"(inH));
 #endif
                 int sc[R];
-                load_scores<R, P8>(prof, c, lane, sc);
+                load_scores_halves<R, P8, kHalves>(prof, c0, c1, lane, sc);
                 // key column part, less go: the key of H + go is (H << 16) + cj
-                const int cjg = kColBase - j - goS;
+                const int cjg0 = kColBase - j0 - goS;
+                // upper rows, from the row above (shuffle or strip boundary)
                 int diag = diag0;
                 int F = LIN ? 0 : __viaddmax_s32(inF, geS, inH);
                 int hprev = inH;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < RH; ++r) {
                     int h;
                     if constexpr (LIN) {
                         // go == ge: E = H_left + go and F = H_up + go exactly
@@ -476,18 +539,48 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     diag = H[r];
                     H[r] = h;
                     hprev = h;
-                    K[r] = (uint32_t)__viaddmax_s32(h, cjg, (int)K[r]);
+                    K[r] = (uint32_t)__viaddmax_s32(h, cjg0, (int)K[r]);
+                }
+                if constexpr (kHalves == 2) {
+                    // lower rows, one column behind, from the upper half's last
+                    // row of the previous step
+                    const int upH = hprev, upF = F;
+                    const int cjg1 = cjg0 + 1;
+                    int diag1 = midD;
+                    int F1 = LIN ? 0 : __viaddmax_s32(midF, geS, midH);
+                    int hprev1 = midH;
+#pragma unroll
+                    for (int r = RH; r < R; ++r) {
+                        int h;
+                        if constexpr (LIN) {
+                            h = __vimax3_s32_relu(diag1 + sc[r], H[r], hprev1) + goS;
+                        } else {
+                            if (r > RH) F1 = __viaddmax_s32(F1, geS, hprev1);
+                            E[r] = __viaddmax_s32(E[r], geS, H[r]);
+                            h = __vimax3_s32_relu(diag1 + sc[r], E[r], F1) + goS;
+                        }
+                        diag1 = H[r];
+                        H[r] = h;
+                        hprev1 = h;
+                        K[r] = (uint32_t)__viaddmax_s32(h, cjg1, (int)K[r]);
+                    }
+                    midD = midH;
+                    midH = upH;
+                    midF = upF;
+                    hprev = hprev1;
+                    F = F1;
                 }
                 outH = hprev;
                 outF = F;
-                if (gl == G - 1 && has_out && in)
-                    bout_ring[j & 31] = __byte_perm((uint32_t)outH, (uint32_t)outF, 0x7632);
+                if (gl == G - 1 && has_out && in1)
+                    bout_ring[j1 & 31] = __byte_perm((uint32_t)outH, (uint32_t)outF, 0x7632);
                 diag0 = inH;
             }
+            ccarry = cres[kU - 1];
             s += kU;
             if (has_out) {
-                // words of the columns below s - G + 1 are complete
-                const int done = (s - G + 1) & ~3;
+                // words of the columns below s - kHalves * G + 1 are complete
+                const int done = (s - kHalves * G + 1) & ~3;
                 flush_out(min(done, (mcols + 3) & ~3));
             }
 

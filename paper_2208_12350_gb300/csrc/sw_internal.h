@@ -20,10 +20,11 @@ constexpr int32_t kScaledNegInf = -(1 << 30);  // E/F "-infinity", scaled domain
 constexpr int32_t kPlainNegInf = -(1 << 30);   // E/F "-infinity", plain int32
 constexpr int32_t kScaledPad = -(1 << 29);     // profile score of rows beyond n
 constexpr int kMaxScaledScore = 32766;         // (S << 16) + 65535 < 2^31
-// Column part of the end-cell key: kColBase - j.  Lanes start up to 31
-// columns early (pad columns, j >= -31), so references of the batched path
-// are limited to kColBase residues to keep the part in [0, 65535).
-constexpr int kColBase = 65503;
+// Column part of the end-cell key: kColBase - j.  A lane's last row starts
+// up to 2 x 32 - 1 = 63 columns early (pad columns, j >= -63, with split
+// rows), so sequences of the batched path are limited to kColBase residues
+// to keep the part in [0, 65535).
+constexpr int kColBase = 65535 - 64;
 constexpr int kMaxScaledGap = 16383;
 constexpr int kMaxAlphabet = 32;
 #ifndef SWGB_ROWS

@@ -142,6 +142,29 @@ def test_long_sequences_and_maximum_length(gpu_lib, ctx):
     assert_same(got, expect, "long batched")
 
 
+@pytest.mark.parametrize("lg", [1, 5])
+def test_batched_length_limit(gpu_lib, ctx, lg):
+    """Sequences up to 65,471 residues take the batched kernel (its end key
+    keeps the column in 16 bits on the pad columns a lane's last row computes
+    before its first), one more takes the plain kernel; exact either side,
+    with the start far from the end (a long reverse sweep) and with a best
+    cell near the last column."""
+    rng = np.random.default_rng(31 + lg)
+    qs, rs = [], []
+    for n, m in [(300, 65471), (300, 65472), (65471, 200), (65472, 200)]:
+        q = rng.integers(0, 4, n).astype(np.uint8)
+        r = rng.integers(0, 4, m).astype(np.uint8)
+        k = min(n, m, 150)
+        r[m - k:] = q[:k]
+        qs.append(q)
+        rs.append(r)
+    b = wl.make_batch("limit", qs, rs, wl.dna_matrix(), -6, -1)
+    expect = oracle.align_workload(b)
+    got, info = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_AUTO, tuning=(lg, 1e9))
+    assert_same(got, expect, f"length limit G{1 << lg}")
+    assert info["plain_pairs"] == 2
+
+
 def test_wide_scores_use_plain_path(gpu_lib, ctx):
     """Scores beyond the scaled int32 key range go to the general int32 kernel."""
     rng = np.random.default_rng(29)
