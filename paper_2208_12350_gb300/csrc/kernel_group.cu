@@ -17,9 +17,11 @@
 // boundary instead: H = 0 / F = -infinity above the first strip (Section
 // II-B.1's boundary row), and for later strips the last row of the previous
 // strip, which lane G-1 wrote to global scratch.  Queries longer than G*R
-// rows take several strips ("passes").
+// rows take several strips ("passes").  (A build option, SWGB_SPLIT_ROWS,
+// runs a lane's two row halves a column apart instead; measured slower.)
 //
-// Staging.  Global memory is touched in 16-byte pieces only.  Each group has
+// Staging.  Reference residues and strip-boundary words move in 16-byte
+// pieces (the profile build reads its rows' residues directly).  Each group has
 // three small rings in shared memory: reference residues (128 bytes, filled
 // by its lane 0 with cp.async a few 4-step blocks ahead; each lane then
 // reads its residue with a shared-memory load), the previous strip's

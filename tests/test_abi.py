@@ -78,3 +78,19 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(swgb, "_lib", None)
     with pytest.raises(ImportError):
         swgb.load()
+
+
+def test_cigar_capacity_is_host_only(lib):
+    """sw_cigar_capacity runs on the host: room per aligned pair, 0 otherwise."""
+    import numpy as np
+    import paper_2208_12350_gb300 as swgb
+    res = np.array([[7, 0, 12],      # scores
+                    [4, -1, 30],     # qend
+                    [3, -1, 40],     # rend
+                    [0, -1, 10],     # qstart
+                    [0, -1, 35]], dtype=np.int32)
+    off = swgb.sw_cigar_capacity(res)
+    assert off.tolist() == [0, 5 + 4, 9, 9 + 21 + 6]
+    assert lib.sw_cigar_capacity(None, 3, None) == swgb.SW_EINVAL
+    assert lib.sw_traceback(None, None, None, None, None, 0, None, 4, -6, -1, None, None, None,
+                            None, None) == swgb.SW_EINVAL
