@@ -70,6 +70,7 @@
 // start would have run over all rend + 1 columns.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "sw_internal.h"
 
@@ -121,22 +122,32 @@ __device__ __forceinline__ int byte_hi(uint32_t w) {
     return (int)d;
 }
 
+// Scaled substitution tables, filled once per block: entry x * (A + 1) + c
+// is the profile value of row residue x against column residue c, that is
+// (s - go) << 16 (int32 profile) or s - go (int8 profile), and entry
+// x * (A + 1) + A the pad value.  Two tables: the forward sweep's (rows are
+// query residues, s = mat[x][c]) and the transposed reverse sweep's
+// (rows are reference residues, s = mat[c][x]).
+template <bool P8>
+using TabT = typename std::conditional<P8, int8_t, int32_t>::type;
+
+__host__ __device__ constexpr size_t tab_bytes(bool p8, int A) {
+    const size_t need = 2 * (size_t)A * (size_t)(A + 1) * (p8 ? 1 : 4);
+    return ((need > 1024 ? need : 1024) + 15) & ~(size_t)15;
+}
+
 // Profile of one lane: for column residue c in [0, A] (A = pad) and the
-// lane's R rows, (s - go) << 16 with s the substitution score of the row's
-// residue against c, or a pad score for rows past the end.  The score of
-// row residue x against column residue c is smat[x * rs + c * cs]: rs = A,
-// cs = 1 when rows are query residues (the matrix row is the query
-// residue), rs = 1, cs = A for the transposed reverse sweep.  Layout
-// [c][chunk][lane]: conflict-free loads whatever residue each lane asks for.
+// lane's R rows, the table value of the row's residue against c, or the pad
+// value for rows past the end.  Layout [c][chunk][lane]: conflict-free loads
+// whatever residue each lane asks for.
 template <int R, bool P8>
 __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_t *a, int dir,
-                                              int row0, int nrows, const int8_t *smat, int A,
-                                              int go, int rs, int cs) {
-    int qa[R];
+                                              int row0, int nrows, const TabT<P8> *tab, int A) {
+    int base[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + r;
-        qa[r] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * rs : -1;
+        base[r] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * (A + 1) : -1;
     }
     for (int c = 0; c <= A; ++c) {
         if constexpr (P8) {
@@ -146,7 +157,7 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
             for (int k = 0; k < R / 4; ++k) w[k] = 0u;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int v = (qa[r] >= 0 && c < A) ? (int)smat[qa[r] + c * cs] - go : -128;
+                const int v = base[r] >= 0 ? (int)tab[base[r] + c] : -128;
                 w[r >> 2] |= (uint32_t)(uint8_t)(int8_t)v << (8 * (r & 3));
             }
             if constexpr (R == 8) {
@@ -165,8 +176,7 @@ __device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int r = 4 * k + u;
-                    v[u] = (qa[r] >= 0 && c < A) ? ((int)smat[qa[r] + c * cs] - go) * 65536
-                                                 : kScaledPad;
+                    v[u] = base[r] >= 0 ? tab[base[r] + c] : kScaledPad;
                 }
                 *reinterpret_cast<int4 *>(prof + (((size_t)c * (R / 4) + k) * 32 + lane) * 16) =
                     make_int4(v[0], v[1], v[2], v[3]);
@@ -277,11 +287,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * R : (size_t)(A + 1) * (R / 4) * 32 * 16;
-    // shared memory: rings (16-byte aligned) | matrix | cold state | profiles
+    // shared memory: rings (16-byte aligned) | score tables | cold state | profiles
     char *rings = smem_group + (size_t)warp * 3 * kMaxGroups * kRingBytes;
-    int8_t *smat = reinterpret_cast<int8_t *>(smem_group + (size_t)kGroupWarps * 3 * kMaxGroups *
-                                                               kRingBytes);
-    char *cold_base = reinterpret_cast<char *>(smat) + kMaxAlphabet * kMaxAlphabet;
+    TabT<P8> *tab_fwd = reinterpret_cast<TabT<P8> *>(smem_group + (size_t)kGroupWarps * 3 *
+                                                                      kMaxGroups * kRingBytes);
+    TabT<P8> *tab_rev = tab_fwd + A * (A + 1);
+    char *cold_base = reinterpret_cast<char *>(tab_fwd) + tab_bytes(P8, A);
     char *prof = cold_base + (size_t)kColdWords * 4 * NT + warp * prof_bytes;
     Cold cold;
     cold.a = reinterpret_cast<const uint8_t **>(cold_base);
@@ -298,7 +309,18 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     cold.rend = cw + 8 * NT;
     cold.best_row = cw + 9 * NT;
     cold.best_key = reinterpret_cast<uint32_t *>(cw + 10 * NT);
-    for (int i = t; i < A * A; i += blockDim.x) smat[i] = p.mat[i];
+    for (int i = t; i < A * (A + 1); i += blockDim.x) {
+        const int x = i / (A + 1), c = i - x * (A + 1);
+        if (c == A) {
+            tab_fwd[i] = (TabT<P8>)(P8 ? -128 : kScaledPad);
+            tab_rev[i] = (TabT<P8>)(P8 ? -128 : kScaledPad);
+        } else {
+            // the plan takes the int8 profile only when s - go fits in int8
+            const int vf = (int)p.mat[x * A + c] - go, vr = (int)p.mat[c * A + x] - go;
+            tab_fwd[i] = (TabT<P8>)(P8 ? vf : vf * 65536);
+            tab_rev[i] = (TabT<P8>)(P8 ? vr : vr * 65536);
+        }
+    }
     __syncthreads();
 
     // this warp starts on the class whose warp range holds it, then walks
@@ -382,8 +404,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         // fresh DP state, stream cursors; waits for the strip's first data.
         auto begin_strip = [&](int ps) {
             const int n = cold.n[t], m = cold.m[t];
-            build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n, smat, A, go,
-                                 rev ? 1 : A, rev ? A : 1);
+            build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n,
+                                 rev ? tab_rev : tab_fwd, A);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 H[r] = goS;
@@ -703,7 +725,8 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
     const size_t per_warp = kind == ProfileKind::kInt8
                                 ? (size_t)(alphabet + 1) * 32 * kRows
                                 : (size_t)(alphabet + 1) * (kRows / 4) * 32 * 16;
-    return (size_t)kGroupWarps * 3 * kMaxGroups * kRingBytes + kMaxAlphabet * kMaxAlphabet +
+    return (size_t)kGroupWarps * 3 * kMaxGroups * kRingBytes +
+           tab_bytes(kind == ProfileKind::kInt8, alphabet) +
            (size_t)kColdWords * 4 * kGroupWarps * 32 + kGroupWarps * per_warp;
 }
 
