@@ -136,49 +136,48 @@ __host__ __device__ constexpr size_t tab_bytes(bool p8, int A) {
     return ((need > 1024 ? need : 1024) + 15) & ~(size_t)15;
 }
 
-// Profile of one lane: for column residue c in [0, A] (A = pad) and the
-// lane's R rows, the table value of the row's residue against c, or the pad
-// value for rows past the end.  Layout [c][chunk][lane]: conflict-free loads
+// Profile of the G lanes gb .. gb + G - 1 of one group, filled by all 32
+// lanes of the warp together: for column residue c in [0, A] (A = pad) and
+// each lane's R rows (rows row_base + t*R .. of the sweep for lane gb + t),
+// the table value of the row's residue against c, or the pad value for rows
+// past the end.  One work unit is one lane's four rows (an int32 chunk or an
+// int8 word) for every c.  Layout [c][chunk][lane]: conflict-free loads
 // whatever residue each lane asks for.
 template <int R, bool P8>
-__device__ __forceinline__ void build_profile(char *prof, int lane, const uint8_t *a, int dir,
-                                              int row0, int nrows, const TabT<P8> *tab, int A) {
-    int base[R];
+__device__ __forceinline__ void build_profile_group(char *prof, int lane, int gb, int log2g,
+                                                    const uint8_t *a, int dir, int row_base,
+                                                    int nrows, const TabT<P8> *tab, int A) {
+    static_assert(!P8 || R == 8 || R == 16 || R == 32, "int8 profile holds 8, 16 or 32 rows");
+    const int G = 1 << log2g;
+    const int units = G * (R / 4);
+    for (int u = lane; u < units; u += 32) {
+        const int tl = u & (G - 1), k = u >> log2g;
+        const int tlane = gb + tl;
+        int base[4];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int i = row0 + r;
-        base[r] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * (A + 1) : -1;
-    }
-    for (int c = 0; c <= A; ++c) {
-        if constexpr (P8) {
-            static_assert(R == 8 || R == 16 || R == 32, "int8 profile holds 8, 16 or 32 rows");
-            uint32_t w[R / 4];
+        for (int j = 0; j < 4; ++j) {
+            const int i = row_base + tl * R + 4 * k + j;
+            base[j] = i < nrows ? min((int)a[(ptrdiff_t)i * dir], A - 1) * (A + 1) : -1;
+        }
+        for (int c = 0; c <= A; ++c) {
+            if constexpr (P8) {
+                uint32_t w = 0u;
 #pragma unroll
-            for (int k = 0; k < R / 4; ++k) w[k] = 0u;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int v = base[r] >= 0 ? (int)tab[base[r] + c] : -128;
-                w[r >> 2] |= (uint32_t)(uint8_t)(int8_t)v << (8 * (r & 3));
-            }
-            if constexpr (R == 8) {
-                *reinterpret_cast<uint2 *>(prof + ((size_t)c * 32 + lane) * 8) =
-                    make_uint2(w[0], w[1]);
+                for (int j = 0; j < 4; ++j) {
+                    const int v = base[j] >= 0 ? (int)tab[base[j] + c] : -128;
+                    w |= (uint32_t)(uint8_t)(int8_t)v << (8 * j);
+                }
+                if constexpr (R == 8)
+                    *reinterpret_cast<uint32_t *>(prof + ((size_t)c * 32 + tlane) * 8 + k * 4) = w;
+                else
+                    *reinterpret_cast<uint32_t *>(
+                        prof + (((size_t)c * (R / 16) + (k >> 2)) * 32 + tlane) * 16 + (k & 3) * 4) =
+                        w;
             } else {
-#pragma unroll
-                for (int k = 0; k < R / 16; ++k)
-                    *reinterpret_cast<uint4 *>(prof + (((size_t)c * (R / 16) + k) * 32 + lane) * 16) =
-                        make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < R / 4; ++k) {
                 int v[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int r = 4 * k + u;
-                    v[u] = base[r] >= 0 ? tab[base[r] + c] : kScaledPad;
-                }
-                *reinterpret_cast<int4 *>(prof + (((size_t)c * (R / 4) + k) * 32 + lane) * 16) =
+                for (int j = 0; j < 4; ++j) v[j] = base[j] >= 0 ? tab[base[j] + c] : kScaledPad;
+                *reinterpret_cast<int4 *>(prof + (((size_t)c * (R / 4) + k) * 32 + tlane) * 16) =
                     make_int4(v[0], v[1], v[2], v[3]);
             }
         }
@@ -362,6 +361,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         uint32_t *bout = p.scratch;
         bool has_in = false, has_out = false;
         bool live = false, rev = false, drained = false;
+        bool need_prof = false;  // this lane's group started a strip without its profile
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             H[r] = goS;
@@ -404,8 +404,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         // fresh DP state, stream cursors; waits for the strip's first data.
         auto begin_strip = [&](int ps) {
             const int n = cold.n[t], m = cold.m[t];
-            build_profile<R, P8>(prof, lane, cold.a[t], dir, ps * G * R + gl * R, n,
-                                 rev ? tab_rev : tab_fwd, A);
+            (void)n;
+            need_prof = true;  // filled by the whole warp before the next block
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 H[r] = goS;
@@ -483,6 +483,24 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 }
             }
             if (__all_sync(kFull, !live)) break;  // every group drained and idle
+
+            // ---- profiles of the groups that started a strip, built by all lanes
+            unsigned need = __ballot_sync(kFull, need_prof);
+            if (need) {
+                __syncwarp();  // the groups' sweep state in shared memory is visible
+                while (need) {
+                    const int gb = (__ffs(need) - 1) & ~(G - 1);
+                    const int tg = warp * 32 + gb;
+                    const int gdir = __shfl_sync(kFull, dir, gb);
+                    const bool grev = __shfl_sync(kFull, (int)rev, gb) != 0;
+                    build_profile_group<R, P8>(prof, lane, gb, log2g, cold.a[tg], gdir,
+                                               cold.ps[tg] * G * R, cold.n[tg],
+                                               grev ? tab_rev : tab_fwd, A);
+                    need &= G == 32 ? 0u : ~(((1u << G) - 1u) << gb);
+                }
+                __syncwarp();
+                need_prof = false;
+            }
 
             const int mcols = live ? stop : 0;
 
