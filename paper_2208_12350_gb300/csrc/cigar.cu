@@ -298,7 +298,10 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
             first = last;
         }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // whatever was enqueued must finish before its scratch is freed, also
+    // after a failed enqueue further on
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
     cudaFree(d_tb);
     cudaFree(d_row);
     cudaFree(d_pairs);
