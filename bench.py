@@ -58,6 +58,8 @@ def parse():
                     default=None, help="override a DNA workload's match/mismatch scores")
     ap.add_argument("--ends-only", action="store_true",
                     help="score and end cell only (no reverse pass)")
+    ap.add_argument("--packed", action="store_true",
+                    help="2-bit packed DNA input (expanded on the device inside each step)")
     ap.add_argument("--cigar", action="store_true",
                     help="also time the traceback (CIGAR) of every aligned pair")
     ap.add_argument("--no-serve", action="store_true")
@@ -398,20 +400,27 @@ def run_ours(args, rank, world, local):
     if args.gaps:
         batch.gap_open, batch.gap_extend = args.gaps
         batch.name += f"-gaps{args.gaps[0]}{args.gaps[1]}"
-    flags = swgb.SW_PLAN_ENDS_ONLY if args.ends_only else 0
+    flags = (swgb.SW_PLAN_ENDS_ONLY if args.ends_only else 0) | \
+        (swgb.SW_PLAN_PACKED_2BIT if args.packed else 0)
+    # the input the plans read: one byte per residue, or 2-bit packed
+    q_in = swgb.sw_pack_2bit(batch.q_seqs) if args.packed else batch.q_seqs
+    r_in = swgb.sw_pack_2bit(batch.r_seqs) if args.packed else batch.r_seqs
     cells = batch.cells
     ctx = swgb.sw_ctx_create(local)
     sms = swgb.sw_ctx_sm_count(ctx)
     stream = torch.cuda.Stream(device=dev)
-    q = torch.from_numpy(batch.q_seqs).to(dev)
-    r = torch.from_numpy(batch.r_seqs).to(dev)
+    q = torch.from_numpy(q_in).to(dev)
+    r = torch.from_numpy(r_in).to(dev)
     out = torch.zeros((5, batch.n_pairs), dtype=torch.int32, device=dev)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # unpacked copies for the calls that take one byte per residue
+    q8 = torch.from_numpy(batch.q_seqs).to(dev) if args.packed else q
+    r8 = torch.from_numpy(batch.r_seqs).to(dev) if args.packed else r
     tune = None
     if not args.no_autotune:
         # measured choice of the lane-group widths (cached by GPU and batch shape)
         tune = swgb.sw_autotune(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
-                                batch.gap_open, batch.gap_extend, q, r, out,
+                                batch.gap_open, batch.gap_extend, q8, r8, out,
                                 cache_path=args.tune_cache, stream=stream)
         torch.cuda.synchronize()
     plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
@@ -474,8 +483,8 @@ def run_ours(args, rank, world, local):
                  "steps": len(pt), "identical_outputs": same}
 
     # --- end to end through the host-buffer C-ABI call
-    qh = torch.from_numpy(batch.q_seqs).pin_memory()
-    rh = torch.from_numpy(batch.r_seqs).pin_memory()
+    qh = torch.from_numpy(q_in).pin_memory()
+    rh = torch.from_numpy(r_in).pin_memory()
     oh = torch.zeros((5, batch.n_pairs), dtype=torch.int32).pin_memory()
     eplan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
                                 batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
@@ -491,7 +500,7 @@ def run_ours(args, rank, world, local):
     e2e_same = bool(np.array_equal(oh.numpy().T, res))
     swgb.sw_plan_destroy(eplan)
     e2e = {"value": job_cells * args.steps / e2e_t / 1e9, "unit": "GCUPS",
-           "h2d_bytes_per_step": int(batch.q_seqs.nbytes + batch.r_seqs.nbytes),
+           "h2d_bytes_per_step": int(q_in.nbytes + r_in.nbytes),
            "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same}
 
     swgb.sw_plan_destroy(plan)
@@ -506,12 +515,12 @@ def run_ours(args, rank, world, local):
         ok = res[:, 0] > 0
         span_cells = int(np.sum((res[ok, 1] - res[ok, 3] + 1).astype(np.int64) *
                                 (res[ok, 2] - res[ok, 4] + 1)))
-        swgb.sw_traceback(ctx, q, batch.q_offsets, r, batch.r_offsets, batch.matrix,
+        swgb.sw_traceback(ctx, q8, batch.q_offsets, r8, batch.r_offsets, batch.matrix,
                           batch.gap_open, batch.gap_extend, res5, coff, ops, nops, stream)
         reps = 3
         t0 = time.perf_counter()
         for _ in range(reps):
-            swgb.sw_traceback(ctx, q, batch.q_offsets, r, batch.r_offsets, batch.matrix,
+            swgb.sw_traceback(ctx, q8, batch.q_offsets, r8, batch.r_offsets, batch.matrix,
                               batch.gap_open, batch.gap_extend, res5, coff, ops, nops, stream)
         dt = (time.perf_counter() - t0) / reps
         cigar = {"value": span_cells / dt / 1e9, "unit": "GCUPS (span cells)", "ms": dt * 1e3,
@@ -520,7 +529,7 @@ def run_ours(args, rank, world, local):
                  "note": "host-timed blocking call incl. scratch allocation"}
 
     serve = None
-    overridden = bool(args.gaps or args.dna_scores or args.ends_only or args.pairs)
+    overridden = bool(args.gaps or args.dna_scores or args.ends_only or args.pairs or args.packed)
     if not args.no_serve and rank == 0 and world == 1 and not overridden:
         if args.config == 1:
             serve = serve_sweep(swgb, ctx, batch, res, args)
@@ -544,6 +553,8 @@ def run_ours(args, rank, world, local):
                 "config": {"workload": batch.name, "pairs": batch.n_pairs,
                            "forward_cells": cells, "mode": "batched persistent + CUDA graph",
                            "l2": "flushed between steps (512 MB write)", "sms": sms,
+                           "input": "2-bit packed, expanded on the device" if args.packed
+                           else "one byte per residue",
                            "shards": (f"{world} LPT shards of {world} x the per-GPU pairs"
                                       if world > 1 else None),
                            "tuning": tune,

@@ -83,6 +83,13 @@ typedef enum {
  * back only the first 3 x n_pairs values.  Score-only callers use this
  * mode too: the end cell comes with the score at no extra cost. */
 #define SW_PLAN_ENDS_ONLY 2u
+/* Packed input: q_seqs and r_seqs given to sw_plan_execute /
+ * sw_plan_execute_host are 2-bit packed streams (residue k of the stream in
+ * byte k >> 2, bits 2 (k & 3) and up; offsets still count residues); needs
+ * alphabet_size <= 4.  The plan expands them on the device before the
+ * alignment kernels (two small launches inside the same graph); the
+ * host-buffer call moves a quarter of the input bytes. */
+#define SW_PLAN_PACKED_2BIT 4u
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_plan sw_plan;
@@ -310,6 +317,15 @@ int sw_server_stats(sw_server *server, int64_t *completed, int64_t *in_flight, i
 int sw_server_launches(sw_server *server, int64_t *launches, int64_t *pairs_launched,
                        double *plan_ms);
 int sw_server_destroy(sw_server *server);
+
+/*
+ * 2-bit packing of DNA codes (0..3), four per byte, first residue in the low
+ * bits.  sw_pack_2bit: HOST arrays, (n_res + 3) / 4 bytes out; SW_ERANGE on a
+ * code above 3.  sw_unpack_2bit: DEVICE arrays (codes 4-byte aligned),
+ * enqueued on `stream`.
+ */
+int sw_pack_2bit(const uint8_t *codes, int64_t n_res, uint8_t *packed);
+int sw_unpack_2bit(const uint8_t *packed, int64_t n_res, uint8_t *codes, void *stream);
 
 /*
  * Traceback: the alignment itself (Fig. 2(c)'s traceback from the maximal

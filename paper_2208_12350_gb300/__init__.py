@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "SW_OK", -1: "SW_EINVAL", -2: "SW_ERANGE", -3: "SW_ENOMEM", -
 SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
 SW_PLAN_GRAPH = 1
 SW_PLAN_ENDS_ONLY = 2
+SW_PLAN_PACKED_2BIT = 4
 SW_MAX_LEN = 65535
 
 # Every function the library exports, with its ctypes signature.
@@ -63,6 +64,8 @@ SIGNATURES = {
     "sw_server_launches": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sw_server_destroy": ([_P], ctypes.c_int),
+    "sw_pack_2bit": ([_P, _I64, _P], ctypes.c_int),
+    "sw_unpack_2bit": ([_P, _I64, _P, _P], ctypes.c_int),
     "sw_cigar_capacity": ([_P, _I32, _P], ctypes.c_int),
     "sw_traceback": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P],
                      ctypes.c_int),
@@ -337,6 +340,23 @@ def sw_server_launches(server: int) -> dict:
 
 def sw_server_destroy(server: int) -> None:
     _check(load().sw_server_destroy(server), "sw_server_destroy")
+
+
+# ------------------------------------------------------------ 2-bit input
+
+def sw_pack_2bit(codes) -> np.ndarray:
+    """Host uint8 codes (0..3) -> (n + 3) // 4 packed bytes."""
+    c = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.zeros(max(1, (len(c) + 3) // 4), dtype=np.uint8)
+    _check(load().sw_pack_2bit(c.ctypes.data if len(c) else None, len(c), out.ctypes.data),
+           "sw_pack_2bit")
+    return out[:(len(c) + 3) // 4]
+
+
+def sw_unpack_2bit(packed, n_res: int, codes, stream=None) -> None:
+    """Device packed bytes -> device codes (4-byte aligned), on the stream."""
+    _check(load().sw_unpack_2bit(_addr(packed), n_res, _addr(codes), _stream(stream)),
+           "sw_unpack_2bit")
 
 
 # --------------------------------------------------------------- traceback

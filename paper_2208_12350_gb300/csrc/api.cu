@@ -101,6 +101,8 @@ struct sw_plan {
     uint32_t *d_scratch = nullptr;
     // host-buffer execution: staging copies of the inputs and outputs
     uint8_t *d_q = nullptr, *d_r = nullptr;
+    // packed plans: the inputs expanded to one byte per residue
+    uint8_t *d_unq = nullptr, *d_unr = nullptr;
     int32_t *d_out = nullptr;
     // graph replay
     cudaGraphExec_t gexec = nullptr;
@@ -118,6 +120,8 @@ static void plan_free(sw_plan *p) {
     cudaFree(p->d_plain);
     cudaFree(p->d_q);
     cudaFree(p->d_r);
+    cudaFree(p->d_unq);
+    cudaFree(p->d_unr);
     cudaFree(p->d_out);
     delete p;
 }
@@ -234,6 +238,18 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     p->mode = mode == SW_MODE_AUTO ? SW_MODE_BATCHED : mode;
     p->flags = flags;
     p->hp.ends_only = (flags & SW_PLAN_ENDS_ONLY) != 0;
+    if (flags & SW_PLAN_PACKED_2BIT) {
+        if (alphabet_size > 4) {
+            plan_free(p);
+            return fail(SW_EINVAL, "sw_plan_create: SW_PLAN_PACKED_2BIT needs alphabet_size <= 4");
+        }
+        if (cudaMalloc(&p->d_unq, (size_t)std::max<int64_t>(p->hp.q_bytes, 4)) != cudaSuccess ||
+            cudaMalloc(&p->d_unr, (size_t)std::max<int64_t>(p->hp.r_bytes, 4)) != cudaSuccess) {
+            cudaGetLastError();
+            plan_free(p);
+            return fail(SW_ENOMEM, "sw_plan_create: allocation of the unpacked inputs failed");
+        }
+    }
     std::memcpy(p->mat, score_matrix, (size_t)alphabet_size * alphabet_size);
     if ((rc = upload(&p->d_pairs, p->hp.pairs)) || (rc = upload(&p->d_classes, p->hp.classes)) ||
         (rc = upload(&p->d_plain, p->hp.plain))) {
@@ -260,6 +276,12 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
 
 static int enqueue(sw_plan *p, const uint8_t *q, const uint8_t *r, const Outputs &o,
                    cudaStream_t s) {
+    if (p->flags & SW_PLAN_PACKED_2BIT) {
+        SW_CUDA_TRY(enqueue_unpack_2bit(q, p->hp.q_bytes, p->d_unq, p->ctx->sm_count, s));
+        SW_CUDA_TRY(enqueue_unpack_2bit(r, p->hp.r_bytes, p->d_unr, p->ctx->sm_count, s));
+        q = p->d_unq;
+        r = p->d_unr;
+    }
     SW_CUDA_TRY(enqueue_plan(p->hp, p->dev, q, r, o, p->mat, p->A, p->go, p->ge, s));
     return SW_OK;
 }
@@ -314,9 +336,13 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
         return fail(SW_EINVAL, "sw_plan_execute_host: NULL host pointer");
     DeviceGuard g(p->ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", p->ctx->device);
+    // packed plans take a quarter of the bytes (four residues per byte)
+    const bool packed = (p->flags & SW_PLAN_PACKED_2BIT) != 0;
+    const int64_t qb = packed ? (p->hp.q_bytes + 3) / 4 : p->hp.q_bytes;
+    const int64_t rb = packed ? (p->hp.r_bytes + 3) / 4 : p->hp.r_bytes;
     if (!p->d_out) {
-        if (cudaMalloc(&p->d_q, (size_t)std::max<int64_t>(p->hp.q_bytes, 1)) != cudaSuccess ||
-            cudaMalloc(&p->d_r, (size_t)std::max<int64_t>(p->hp.r_bytes, 1)) != cudaSuccess ||
+        if (cudaMalloc(&p->d_q, (size_t)std::max<int64_t>(qb, 1)) != cudaSuccess ||
+            cudaMalloc(&p->d_r, (size_t)std::max<int64_t>(rb, 1)) != cudaSuccess ||
             cudaMalloc(&p->d_out, (size_t)5 * p->n_pairs * sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(p->d_q);
@@ -328,10 +354,8 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->hp.q_bytes > 0)
-        SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, p->hp.q_bytes, cudaMemcpyHostToDevice, s));
-    if (p->hp.r_bytes > 0)
-        SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, p->hp.r_bytes, cudaMemcpyHostToDevice, s));
+    if (qb > 0) SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, qb, cudaMemcpyHostToDevice, s));
+    if (rb > 0) SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, rb, cudaMemcpyHostToDevice, s));
     const int64_t n = p->n_pairs;
     int rc = sw_plan_execute(p, p->d_q, p->d_r, p->d_out, p->d_out + n, p->d_out + 2 * n,
                              p->d_out + 3 * n, p->d_out + 4 * n, stream);
@@ -349,7 +373,9 @@ int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int
     if (!p) return fail(SW_EINVAL, "sw_plan_info: plan is NULL");
     if (n_group_pairs) *n_group_pairs = (int32_t)p->hp.pairs.size();
     if (n_plain) *n_plain = (int32_t)p->hp.plain.size();
-    if (launches) *launches = (p->hp.pairs.empty() ? 0 : 1) + (p->hp.plain.empty() ? 0 : 1);
+    if (launches)
+        *launches = (p->hp.pairs.empty() ? 0 : 1) + (p->hp.plain.empty() ? 0 : 1) +
+                    ((p->flags & SW_PLAN_PACKED_2BIT) ? 2 : 0);
     if (scratch_bytes) *scratch_bytes = p->hp.scratch_words * (int64_t)sizeof(uint32_t);
     return SW_OK;
 }

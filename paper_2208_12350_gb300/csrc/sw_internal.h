@@ -180,6 +180,9 @@ cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_
 size_t plain_smem_bytes(int threads, int alphabet);
 
 int set_error(int code, const char *msg);  // message for sw_last_error()
+// Expands n_res 2-bit packed residues into one byte each (out 4-byte aligned).
+cudaError_t enqueue_unpack_2bit(const uint8_t *packed, int64_t n_res, uint8_t *out, int sms,
+                                cudaStream_t s);
 int ctx_device(const ::sw_ctx *ctx);          // the CUDA device a context works on
 
 // Checks the arguments and plans a batch (no device allocation; queries the

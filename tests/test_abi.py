@@ -94,3 +94,19 @@ def test_cigar_capacity_is_host_only(lib):
     assert lib.sw_cigar_capacity(None, 3, None) == swgb.SW_EINVAL
     assert lib.sw_traceback(None, None, None, None, None, 0, None, 4, -6, -1, None, None, None,
                             None, None) == swgb.SW_EINVAL
+
+
+def test_pack_2bit_is_host_only(lib):
+    """sw_pack_2bit packs four codes per byte, first in the low bits."""
+    import numpy as np
+    import paper_2208_12350_gb300 as swgb
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 3, 4, 5, 1001):
+        codes = rng.integers(0, 4, n).astype(np.uint8)
+        packed = swgb.sw_pack_2bit(codes)
+        assert len(packed) == (n + 3) // 4
+        back = ((packed[:, None] >> (2 * np.arange(4))) & 3).astype(np.uint8).reshape(-1)[:n]
+        assert np.array_equal(back, codes)
+    with pytest.raises(swgb.SwError) as e:
+        swgb.sw_pack_2bit(np.array([0, 1, 4], dtype=np.uint8))
+    assert e.value.code == swgb.SW_ERANGE
