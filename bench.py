@@ -269,6 +269,7 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
     try:
         for _ in range(args.serve_points):
             n = min(len(reqs), max(200, int(rate * 20.0)))
+            lc0 = swgb.sw_server_launches(srv)
             todo = reqs[:n]
             arrival = np.zeros(n, dtype=np.int64)
             ids: queue.Queue = queue.Queue()
@@ -303,11 +304,15 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
                 done_last = max(done_last, done_ns)
                 cells += rq.batch.cells
             th.join()
+            lc1 = swgb.sw_server_launches(srv)
             span = (done_last - t0) / 1e9
             served = n / span
             pt = {"offered_rps": rate, "requests": n, "served_rps": served,
                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                  "gcups": cells / span / 1e9}
+                  "gcups": cells / span / 1e9,
+                  "launches": lc1["launches"] - lc0["launches"],
+                  "plan_ms_per_launch": (lc1["plan_ms"] - lc0["plan_ms"]) /
+                  max(1, lc1["launches"] - lc0["launches"])}
             points.append(pt)
             if served < 0.9 * rate or pt["p99_ms"] > 1000.0:
                 break

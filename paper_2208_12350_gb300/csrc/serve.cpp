@@ -15,8 +15,11 @@
 // while other launches are in flight it is planned to fill lane groups
 // instead, and under heavy load the queue grows between launches, so each
 // launch takes many requests and runs at the batched kernel's throughput.
-// When a launch's completion event fires the worker frees its arena block
-// and slot and wakes the waiters.
+// Forming a launch is the worker's; planning and enqueueing it (milliseconds
+// of host work for tens of thousands of pairs) is done by one of a few
+// planner threads, so launches are planned in parallel.  When a launch's
+// completion event fires the worker frees its arena block and slot and
+// wakes the waiters.
 //
 // Every wait is bounded: sw_server_wait and sw_server_submit take a timeout
 // and return SW_ETIMEOUT instead of blocking forever.
@@ -163,7 +166,15 @@ constexpr size_t kLaunchFixed = 8 * kAlign + kMaxClasses * (sizeof(ClassInfo) + 
 struct Launch {
     std::vector<std::shared_ptr<Request>> reqs;
     size_t dev_off = 0, dev_bytes = 0;
+    int slot = -1;
+    bool gpu_busy = false;  // other launches were on the GPU when it was formed
+    bool enqueued = false;  // its work and completion event are on the stream
 };
+
+// Planner threads: a launch's host planning takes milliseconds for tens of
+// thousands of pairs, so several launches are planned and enqueued at once
+// while the worker keeps admitting and retiring.
+constexpr int kPlanners = 4;
 
 }  // namespace
 }  // namespace swgb
@@ -186,7 +197,10 @@ struct sw_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_space;
     std::thread worker;
-    bool stop = false;
+    std::vector<std::thread> planners;
+    std::deque<Launch *> plan_queue;   // formed, waiting for a planner
+    std::condition_variable cv_plan;
+    bool stop = false, stop_planners = false;
     int64_t next_id = 1, completed = 0, launches = 0, pairs_launched = 0;
     double plan_ms = 0;  // host time spent planning launches
     std::string worker_error;
@@ -349,7 +363,7 @@ static void worker_loop(sw_server *S) {
         // ---- completions
         for (size_t k = 0; k < S->slots.size(); ++k) {
             auto &L = S->slots[k];
-            if (!L) continue;
+            if (!L || !L->enqueued) continue;
             const cudaError_t q = cudaEventQuery(S->events[k]);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) {
@@ -396,12 +410,12 @@ static void worker_loop(sw_server *S) {
             L->reqs = std::move(reqs);
             L->dev_off = off;
             L->dev_bytes = bytes;
-            Launch *Lp = L.get();
+            L->slot = slot;
+            L->gpu_busy = busy;
+            S->plan_queue.push_back(L.get());
             S->slots[slot] = std::move(L);
             ++S->launches;
-            lk.unlock();
-            start_launch(S, *Lp, slot, busy);
-            lk.lock();
+            S->cv_plan.notify_one();
             progressed = true;
         }
         if (S->stop && S->queue.empty()) {
@@ -418,6 +432,22 @@ static void worker_loop(sw_server *S) {
             else
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
         }
+    }
+}
+
+static void planner_loop(sw_server *S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        S->cv_plan.wait(lk, [&] { return S->stop_planners || !S->plan_queue.empty(); });
+        if (S->plan_queue.empty()) break;  // stopping, nothing left
+        Launch *L = S->plan_queue.front();
+        S->plan_queue.pop_front();
+        lk.unlock();
+        start_launch(S, *L, L->slot, L->gpu_busy);  // the slot's stream is this launch's alone
+        lk.lock();
+        L->enqueued = true;
+        S->cv_work.notify_one();
     }
 }
 
@@ -458,6 +488,7 @@ int sw_server_create(sw_ctx *ctx, int64_t budget_bytes, int32_t streams, int64_t
         cudaEventCreateWithFlags(&S->events[k], cudaEventDisableTiming);
     }
     S->worker = std::thread(worker_loop, S);
+    for (int k = 0; k < kPlanners; ++k) S->planners.emplace_back(planner_loop, S);
     *out = S;
     return SW_OK;
 }
@@ -591,7 +622,14 @@ int sw_server_destroy(sw_server *S) {
         S->stop = true;
         S->cv_work.notify_all();
     }
-    if (S->worker.joinable()) S->worker.join();
+    if (S->worker.joinable()) S->worker.join();  // returns once every launch retired
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop_planners = true;
+        S->cv_plan.notify_all();
+    }
+    for (auto &th : S->planners)
+        if (th.joinable()) th.join();
     cudaSetDevice(S->device);
     for (size_t k = 0; k < S->streams.size(); ++k) {
         cudaStreamSynchronize(S->streams[k]);
