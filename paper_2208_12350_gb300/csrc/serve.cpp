@@ -16,7 +16,7 @@
 // instead, and under heavy load the queue grows between launches, so each
 // launch takes many requests and runs at the batched kernel's throughput.
 // Forming a launch is the worker's; planning and enqueueing it (milliseconds
-// of host work for tens of thousands of pairs) is done by one of a few
+// of host work for tens of thousands of pairs) is done by one of eight
 // planner threads, so launches are planned in parallel.  When a launch's
 // completion event fires the worker frees its arena block and slot and
 // wakes the waiters.
@@ -174,7 +174,7 @@ struct Launch {
 // Planner threads: a launch's host planning takes milliseconds for tens of
 // thousands of pairs, so several launches are planned and enqueued at once
 // while the worker keeps admitting and retiring.
-constexpr int kPlanners = 4;
+constexpr int kPlanners = 8;
 
 }  // namespace
 }  // namespace swgb
