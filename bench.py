@@ -60,6 +60,9 @@ def parse():
                     help="score and end cell only (no reverse pass)")
     ap.add_argument("--packed", action="store_true",
                     help="2-bit packed DNA input (expanded on the device inside each step)")
+    ap.add_argument("--no-s16x2", action="store_true",
+                    help="keep the batched kernel on scaled int32 arithmetic (one cell per "
+                         "instruction) where the packed 16-bit form would apply")
     ap.add_argument("--cigar", action="store_true",
                     help="also time the traceback (CIGAR) of every aligned pair")
     ap.add_argument("--no-serve", action="store_true")
@@ -406,7 +409,8 @@ def run_ours(args, rank, world, local):
         batch.gap_open, batch.gap_extend = args.gaps
         batch.name += f"-gaps{args.gaps[0]}{args.gaps[1]}"
     flags = (swgb.SW_PLAN_ENDS_ONLY if args.ends_only else 0) | \
-        (swgb.SW_PLAN_PACKED_2BIT if args.packed else 0)
+        (swgb.SW_PLAN_PACKED_2BIT if args.packed else 0) | \
+        (swgb.SW_PLAN_NO_S16X2 if args.no_s16x2 else 0)
     # the input the plans read: one byte per residue, or 2-bit packed
     q_in = swgb.sw_pack_2bit(batch.q_seqs) if args.packed else batch.q_seqs
     r_in = swgb.sw_pack_2bit(batch.r_seqs) if args.packed else batch.r_seqs
@@ -460,17 +464,22 @@ def run_ours(args, rank, world, local):
     per_launch = t_total / args.steps
 
     # --- integer roofline of the batched kernel (events timed live above)
-    ops = OPS_PER_CELL * (cells + rcells)
+    # the packed 16-bit form does each of the 6 ops for two cells with one
+    # instruction: 3 instruction slots per cell against the packed max's rate
+    packed16 = info["arith"] == "s16x2"
+    ops_per_cell = OPS_PER_CELL // 2 if packed16 else OPS_PER_CELL
+    peak_op = "viaddmax_s16x2" if packed16 else "viaddmax_s32"
+    ops = ops_per_cell * (cells + rcells)
     achieved = ops / per_launch / 1e12
-    mb_rate, _ = swgb.sw_microbench_int("viaddmax_s32", local, 2048)
+    mb_rate, _ = swgb.sw_microbench_int(peak_op, local, 2048)
     peak_measured = mb_rate / 1e12
     sm_mhz = clk.get("sm_mhz")
     traffic = profiled_traffic(batch, tune) if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] \
         else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
             "frac": achieved / peak_measured if peak_measured else None, "traffic": traffic,
-            "peak_kind": "measured __viaddmax_s32 issue rate, whole device, this run",
-            "ops_per_cell": OPS_PER_CELL, "cells_forward": cells, "cells_reverse": rcells,
+            "peak_kind": f"measured __{peak_op} issue rate, whole device, this run",
+            "ops_per_cell": ops_per_cell, "cells_forward": cells, "cells_reverse": rcells,
             "traffic_unit": "DRAM bytes per launch (ncu, committed summary)",
             "algorithmic_bytes": int(batch.q_seqs.nbytes + batch.r_seqs.nbytes + 20 * batch.n_pairs)}
 
@@ -554,7 +563,7 @@ def run_ours(args, rank, world, local):
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_launch * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int32", "data": "synthetic",
+                "dtype": "int16x2" if packed16 else "int32", "data": "synthetic",
                 "config": {"workload": batch.name, "pairs": batch.n_pairs,
                            "forward_cells": cells, "mode": "batched persistent + CUDA graph",
                            "l2": "flushed between steps (512 MB write)", "sms": sms,
@@ -562,7 +571,7 @@ def run_ours(args, rank, world, local):
                            else "one byte per residue",
                            "shards": (f"{world} LPT shards of {world} x the per-GPU pairs"
                                       if world > 1 else None),
-                           "tuning": tune,
+                           "tuning": tune, "arith": info["arith"],
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,

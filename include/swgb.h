@@ -90,6 +90,13 @@ typedef enum {
  * alignment kernels (two small launches inside the same graph); the
  * host-buffer call moves a quarter of the input bytes. */
 #define SW_PLAN_PACKED_2BIT 4u
+/* Keep the batched kernel on scaled int32 arithmetic.  Without this flag
+ * the plan runs the batched kernel in packed 16-bit form (two DP cells per
+ * 32-bit word, every value scaled by 8) when every pair of the batched path
+ * satisfies 8 x (smax x min(n, m) + smax - gap_open) <= 32767, the smallest
+ * matrix entry is >= gap_open and 8 x |gap_extend| <= 16384; the results
+ * are the same either way (sw_plan_arith says which form a plan took). */
+#define SW_PLAN_NO_S16X2 8u
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_plan sw_plan;
@@ -172,6 +179,14 @@ int sw_plan_execute_host(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_
  * for strip boundaries. */
 int sw_plan_info(const sw_plan *plan, int32_t *n_group_pairs, int32_t *n_plain,
                  int32_t *launches, int64_t *scratch_bytes);
+
+/* Arithmetic of a plan's batched kernel: *arith = SW_ARITH_S32 (scaled
+ * int32, one cell per instruction) or SW_ARITH_S16X2 (packed 16-bit, two
+ * cells per instruction).  Plans without batched-path pairs report
+ * SW_ARITH_S32. */
+#define SW_ARITH_S32 0
+#define SW_ARITH_S16X2 1
+int sw_plan_arith(const sw_plan *plan, int32_t *arith);
 
 int sw_plan_destroy(sw_plan *plan);
 

@@ -25,6 +25,8 @@ SW_MODE_AUTO, SW_MODE_PLAIN, SW_MODE_BATCHED = 0, 1, 2
 SW_PLAN_GRAPH = 1
 SW_PLAN_ENDS_ONLY = 2
 SW_PLAN_PACKED_2BIT = 4
+SW_PLAN_NO_S16X2 = 8
+SW_ARITH_S32, SW_ARITH_S16X2 = 0, 1
 SW_MAX_LEN = 65535
 
 # Every function the library exports, with its ctypes signature.
@@ -43,6 +45,7 @@ SIGNATURES = {
     "sw_plan_execute_host": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "sw_plan_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                       ctypes.POINTER(_I64)], ctypes.c_int),
+    "sw_plan_arith": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_plan_destroy": ([_P], ctypes.c_int),
     "sw_align_batch": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
                        ctypes.c_int),
@@ -198,8 +201,10 @@ def sw_plan_info(plan: int) -> dict:
     sb = _I64()
     _check(load().sw_plan_info(plan, ctypes.byref(t), ctypes.byref(p), ctypes.byref(l),
                                ctypes.byref(sb)), "sw_plan_info")
+    ar = _I32()
+    _check(load().sw_plan_arith(plan, ctypes.byref(ar)), "sw_plan_arith")
     return {"group_pairs": t.value, "plain_pairs": p.value, "launches": l.value,
-            "scratch_bytes": sb.value}
+            "scratch_bytes": sb.value, "arith": "s16x2" if ar.value == SW_ARITH_S16X2 else "s32"}
 
 
 def sw_plan_destroy(plan: int) -> None:

@@ -225,7 +225,7 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     std::string msg;
     int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
                             gap_extend, mode, ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
-                            &p->hp, &msg);
+                            &p->hp, &msg, 1, 8192, (flags & SW_PLAN_NO_S16X2) == 0);
     if (rc != SW_OK) {
         delete p;
         return fail(rc, "sw_plan_create: %s", msg.c_str());
@@ -377,6 +377,13 @@ int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int
         *launches = (p->hp.pairs.empty() ? 0 : 1) + (p->hp.plain.empty() ? 0 : 1) +
                     ((p->flags & SW_PLAN_PACKED_2BIT) ? 2 : 0);
     if (scratch_bytes) *scratch_bytes = p->hp.scratch_words * (int64_t)sizeof(uint32_t);
+    return SW_OK;
+}
+
+int sw_plan_arith(const sw_plan *p, int32_t *arith) {
+    if (!p || !arith) return fail(SW_EINVAL, "sw_plan_arith: NULL argument");
+    *arith = (!p->hp.pairs.empty() && p->hp.kind == ProfileKind::kPacked16) ? SW_ARITH_S16X2
+                                                                           : SW_ARITH_S32;
     return SW_OK;
 }
 

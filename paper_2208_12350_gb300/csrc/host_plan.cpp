@@ -67,7 +67,8 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
 int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
-                   std::string *msg, int min_pairs_per_warp, int sample_cap) {
+                   std::string *msg, int min_pairs_per_warp, int sample_cap,
+                   bool allow_packed) {
     *out = HostPlan();
     int rc = check_batch(q_offsets, r_offsets, n_pairs, mat, A, go, ge, nullptr, nullptr,
                          nullptr, msg);
@@ -89,7 +90,18 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
 #ifndef SWGB_SMALL_ALPHABET_INT32
 #define SWGB_SMALL_ALPHABET_INT32 1
 #endif
-    if (A <= 4 && SWGB_SMALL_ALPHABET_INT32)
+#ifndef SWGB_PACKED16
+#define SWGB_PACKED16 1
+#endif
+    // The packed 16-bit form takes the batch when every pair of the batched
+    // path fits its bound (one kernel per batch).
+    bool packed = allow_packed && SWGB_PACKED16 && mode != SW_MODE_PLAIN && n_pairs > 0;
+    for (int32_t i = 0; i < n_pairs && packed; ++i)
+        if (group_path_eligible(n[i], m[i], smax, go, ge))
+            packed = packed_eligible(n[i], m[i], smax, smin, go, ge);
+    if (packed)
+        out->kind = ProfileKind::kPacked16;
+    else if (A <= 4 && SWGB_SMALL_ALPHABET_INT32)
         out->kind = ProfileKind::kInt32;
     else if (smax - go <= 127 && smin - go >= -127)
         out->kind = ProfileKind::kInt8;

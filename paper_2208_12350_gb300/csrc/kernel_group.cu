@@ -56,6 +56,35 @@
 // the column part in [0, 65535) also on the pad columns a lane computes
 // before its first column (j >= -63).
 //
+// Packed 16-bit form (PK).  Two cells per instruction: word k of a lane
+// holds row k in its low half (at column j) and row R/2 + k in its high half
+// (one column behind, j - 1), the split-row schedule with both halves in one
+// register, so every packed max serves two independent row chains.  Scores
+// are scaled by 8 and held as non-negative 16-bit values:
+//   Hs = 8 H,   Es = 8 (E - go),   Fs = 8 (F - go),   s' = 8 (s - go) >= 0
+//   Es  = viaddmax2(Es, 8 ge, Hs_left)              E - go = max(E - go + ge, H_left)
+//   Fs  = viaddmax2(Fs_up, 8 ge, Hs_up)             F - go = max(F_up - go + ge, H_up)
+//   Hs  = viaddmax2_relu(vimax3_2(Hs_diag + s', Es, Fs), 8 go, 0)
+//                                                   H = max(H_diag + s, E, F, 0)
+// Hs_diag + s' is a plain 32-bit add: both halves are non-negative and their
+// sums stay below 2^15, so no carry crosses from the low half to the high
+// one; s' comes from two profile words (low-half rows against column j's
+// residue, high-half rows against column j - 1's) whose other halves are 0.
+// The end cell: the low 3 bits of every Hs are 0, so a chain
+// acc = viaddmax2(Hs_k, 7 - k, acc) over a lane's 8 words gives, per half,
+// the column's largest score with the smallest row holding it (row code
+// 7 - k).  The chain starts from a threshold T = (8 best + 7): acc differs
+// from T in a half exactly when that half's best score grew at this column,
+// and the (column, acc) pair of that step is recorded, so each half ends
+// with its largest score, the first column reaching it and the smallest row
+// there.  The transposed reverse sweep starts T at 8 S - 1 and keeps it at
+// acc: a half records the smallest row holding S and that row's first
+// column.  Rows past n and columns outside [0, m) take s' = 0 (s = go): such
+// a cell's value is reached through non-positive steps from a real cell
+// with a smaller (column, row) pair, so its record never wins.  The plan
+// takes this form only when 8 (smax min(n, m) + smax - go) <= 32767,
+// smin >= go and 8 |ge| <= 16384, which keeps every value in 16 bits.
+//
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
 // a_qend..a_0 and b_rend..b_0, transposed: the reversed reference prefix
 // gives the rows (in registers, strip by strip) and the reversed query
@@ -92,8 +121,10 @@ constexpr int kU = SWGB_GROUP_UNROLL;  // steps per block
 // chains per step) or one block of R rows (1).  Measured on 100k and 200k
 // DNA pairs, the split form was 0.2 % and 1.1 % slower, so it is off; it
 // stays as a build option (int32 profile only).
-template <bool P8>
-__host__ __device__ constexpr int halves_of() { return (SWGB_SPLIT_ROWS && !P8) ? 2 : 1; }
+template <bool P8, bool PK>
+__host__ __device__ constexpr int halves_of() {
+    return PK ? 2 : ((SWGB_SPLIT_ROWS && !P8) ? 2 : 1);
+}
 static_assert(kU == 4 || kU == 8, "blocks move whole 16-byte chunks of 4 boundary columns");
 // blocks between a cp.async and the first use; the copies in flight plus the
 // block being read stay within six of the eight 16-byte slots of a ring
@@ -143,7 +174,7 @@ __host__ __device__ constexpr size_t tab_bytes(bool p8, int A) {
 // past the end.  One work unit is one lane's four rows (an int32 chunk or an
 // int8 word) for every c.  Layout [c][chunk][lane]: conflict-free loads
 // whatever residue each lane asks for.
-template <int R, bool P8>
+template <int R, bool P8, bool PK>
 __device__ __forceinline__ void build_profile_group(char *prof, int lane, int gb, int log2g,
                                                     const uint8_t *a, int dir, int row_base,
                                                     int nrows, const TabT<P8> *tab, int A) {
@@ -173,6 +204,15 @@ __device__ __forceinline__ void build_profile_group(char *prof, int lane, int gb
                     *reinterpret_cast<uint32_t *>(
                         prof + (((size_t)c * (R / 16) + (k >> 2)) * 32 + tlane) * 16 + (k & 3) * 4) =
                         w;
+            } else if constexpr (PK) {
+                // packed form: s' = 8 (s - go) >= 0, 0 past the end; the
+                // lower R/2 rows go to the high halves
+                const int sh = 4 * k >= R / 2 ? 16 : 0;
+                int v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = (base[j] >= 0 ? tab[base[j] + c] : 0) << sh;
+                *reinterpret_cast<int4 *>(prof + (((size_t)c * (R / 4) + k) * 32 + tlane) * 16) =
+                    make_int4(v[0], v[1], v[2], v[3]);
             } else {
                 int v[4];
 #pragma unroll
@@ -271,17 +311,23 @@ constexpr int kColdWords = 2 * 2 + 11;  // 32-bit words per lane
 
 }  // namespace
 
-template <int R, bool P8, bool LIN>
+template <int R, bool P8, bool LIN, bool PK>
 __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     sw_group_kernel(const __grid_constant__ GroupParams p) {
+    static_assert(!PK || (!P8 && R == 16), "the packed form holds 16 rows in 8 words");
     extern __shared__ __align__(16) char smem_group[];
-    constexpr int kHalves = halves_of<P8>();
+    constexpr int kHalves = halves_of<P8, PK>();
+    constexpr int W = R / 2;  // packed words per lane
     const int A = p.alphabet;
     const int go = p.gap_open, ge = p.gap_extend;
     const int goS = go * 65536, geS = ge * 65536;
+    // packed form: 8 ge and 8 go in both halves
+    const uint32_t geP = ((uint32_t)(8 * ge) & 0xFFFFu) * 0x10001u;
+    const uint32_t goP = ((uint32_t)(8 * go) & 0xFFFFu) * 0x10001u;
     // boundary word of "no row above": H = 0 (stored as H + go) and F = -inf
-    // (0xC000 = -16384 in the high half, -2^30 scaled)
-    const uint32_t kNoBound = 0xC0000000u | ((uint32_t)go & 0xFFFFu);
+    // (0xC000 = -16384 in the high half, -2^30 scaled); packed form: H = 0 and
+    // F = go (F - go = 0), which gives the row below the same values
+    const uint32_t kNoBound = PK ? 0u : (0xC0000000u | ((uint32_t)go & 0xFFFFu));
     constexpr int NT = kGroupWarps * 32;
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
@@ -311,13 +357,13 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     for (int i = t; i < A * (A + 1); i += blockDim.x) {
         const int x = i / (A + 1), c = i - x * (A + 1);
         if (c == A) {
-            tab_fwd[i] = (TabT<P8>)(P8 ? -128 : kScaledPad);
-            tab_rev[i] = (TabT<P8>)(P8 ? -128 : kScaledPad);
+            tab_fwd[i] = (TabT<P8>)(PK ? 0 : P8 ? -128 : kScaledPad);
+            tab_rev[i] = (TabT<P8>)(PK ? 0 : P8 ? -128 : kScaledPad);
         } else {
             // the plan takes the int8 profile only when s - go fits in int8
             const int vf = (int)p.mat[x * A + c] - go, vr = (int)p.mat[c * A + x] - go;
-            tab_fwd[i] = (TabT<P8>)(P8 ? vf : vf * 65536);
-            tab_rev[i] = (TabT<P8>)(P8 ? vr : vr * 65536);
+            tab_fwd[i] = (TabT<P8>)(PK ? 8 * vf : P8 ? vf : vf * 65536);
+            tab_rev[i] = (TabT<P8>)(PK ? 8 * vr : P8 ? vr : vr * 65536);
         }
     }
     __syncthreads();
@@ -351,6 +397,13 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         // half's column (from the previous step) and one column earlier, and
         // the column residue the lower half takes next
         int midH = goS, midF = kScaledNegInf, midD = goS, ccarry = A;
+        // packed form: the lane's words, its last word and that word's F of
+        // the step before, word 0's row above of the step before, and the
+        // end tracking (threshold, its "keep the score" mask, one record per
+        // half: column << 16 | 8 score + row code)
+        uint32_t Hw[W], Ew[W];
+        uint32_t outHw = 0u, outFw = 0u, diag0w = 0u;
+        uint32_t Tw = 0x00070007u, tmask = 0x00070007u, rec_lo = 0u, rec_hi = 0u;
         int s = 0, lim = 0, stop = 0, dir = 1;
         const uint8_t *bcol = p.r;  // column 0 of the current sweep
         int roff = 0;               // bcol's offset in its 16-byte chunk (mirrored if dir < 0)
@@ -368,6 +421,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             E[r] = kScaledNegInf;
             K[r] = 0u;
         }
+#pragma unroll
+        for (int k = 0; k < W; ++k) Hw[k] = Ew[k] = 0u;
         cold.id[t] = -1;
 
         // Issues the cp.async copies that are due: residue chunks up to the
@@ -419,6 +474,17 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             midF = kScaledNegInf;
             midD = goS;
             ccarry = A;
+            if constexpr (PK) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) Hw[k] = Ew[k] = 0u;
+                outHw = outFw = diag0w = 0u;
+                // forward: best score 0 with the largest row code; reverse:
+                // just below the score S with any row code
+                const uint32_t t0 = rev ? (uint32_t)(8 * cold.target[t] - 1) : 7u;
+                Tw = (t0 & 0xFFFFu) * 0x10001u;
+                tmask = rev ? 0u : 0x00070007u;
+                rec_lo = rec_hi = 0u;
+            }
             s = 0;
             // the lane's last row reaches the last column kHalves * G - 1 steps late
             lim = stop + kHalves * G - 1;
@@ -493,7 +559,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     const int tg = warp * 32 + gb;
                     const int gdir = __shfl_sync(kFull, dir, gb);
                     const bool grev = __shfl_sync(kFull, (int)rev, gb) != 0;
-                    build_profile_group<R, P8>(prof, lane, gb, log2g, cold.a[tg], gdir,
+                    build_profile_group<R, P8, PK>(prof, lane, gb, log2g, cold.a[tg], gdir,
                                                cold.ps[tg] * G * R, cold.n[tg],
                                                grev ? tab_rev : tab_fwd, A);
                     need &= G == 32 ? 0u : ~(((1u << G) - 1u) << gb);
@@ -538,85 +604,147 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             // lower one fed by the upper one's last row of the step before.
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                constexpr int RH = R / kHalves;
-                const int j0 = s + u - kHalves * gl;  // column of the upper rows
-                const int j1 = j0 - (kHalves - 1);    // column of the lane's last row
-                const bool in0 = (unsigned)j0 < (unsigned)mcols;
-                const bool in1 = (unsigned)j1 < (unsigned)mcols;
-                int inH = __shfl_up_sync(kFull, outH, 1, G);
-                int inF = LIN ? 0 : __shfl_up_sync(kFull, outF, 1, G);
-                if (gl == 0) {
-                    // previous strip's last row, or H = 0 / F = -inf above the
-                    // first strip and outside the columns
-                    const uint32_t w = in0 ? bws[u] : kNoBound;
-                    inH = (int)(w << 16);
-                    inF = (int)(w & 0xFFFF0000u);
-                }
-                int c0 = cres[u];
-                int c1 = kHalves == 2 ? (u == 0 ? ccarry : cres[u - 1]) : c0;
-#if SWGB_STEP_ORDER_FENCE
-                // keep this step's profile loads after its shuffle, so the
-                // compiler does not hoist every unrolled step's loads
-                asm volatile("" : "+r"(c0), "+r"(c1) : "r"(inH));
-#endif
-                int sc[R];
-                load_scores_halves<R, P8, kHalves>(prof, c0, c1, lane, sc);
-                // key column part, less go: the key of H + go is (H << 16) + cj
-                const int cjg0 = kColBase - j0 - goS;
-                // upper rows, from the row above (shuffle or strip boundary)
-                int diag = diag0;
-                int F = LIN ? 0 : __viaddmax_s32(inF, geS, inH);
-                int hprev = inH;
-#pragma unroll
-                for (int r = 0; r < RH; ++r) {
-                    int h;
-                    if constexpr (LIN) {
-                        // go == ge: E = H_left + go and F = H_up + go exactly
-                        h = __vimax3_s32_relu(diag + sc[r], H[r], hprev) + goS;
-                    } else {
-                        if (r > 0) F = __viaddmax_s32(F, geS, hprev);
-                        E[r] = __viaddmax_s32(E[r], geS, H[r]);
-                        h = __vimax3_s32_relu(diag + sc[r], E[r], F) + goS;
+                if constexpr (PK) {
+                    // packed: low halves rows [0, R/2) at column j0 = s - 2 gl,
+                    // high halves rows [R/2, R) at j0 - 1
+                    const int j0 = s + u - 2 * gl;
+                    const int j1 = j0 - 1;
+                    const bool in0 = (unsigned)j0 < (unsigned)mcols;
+                    const bool in1 = (unsigned)j1 < (unsigned)mcols;
+                    uint32_t inH = __shfl_up_sync(kFull, outHw, 1, G);
+                    uint32_t inF = LIN ? 0u : __shfl_up_sync(kFull, outFw, 1, G);
+                    if (gl == 0) {
+                        // previous strip's last row (H, F - go), or (0, 0)
+                        const uint32_t w = in0 ? bws[u] : kNoBound;
+                        inH = w << 16;
+                        inF = w & 0xFFFF0000u;
                     }
-                    diag = H[r];
-                    H[r] = h;
-                    hprev = h;
-                    K[r] = (uint32_t)__viaddmax_s32(h, cjg0, (int)K[r]);
-                }
-                if constexpr (kHalves == 2) {
-                    // lower rows, one column behind, from the upper half's last
-                    // row of the previous step
-                    const int upH = hprev, upF = F;
-                    const int cjg1 = cjg0 + 1;
-                    int diag1 = midD;
-                    int F1 = LIN ? 0 : __viaddmax_s32(midF, geS, midH);
-                    int hprev1 = midH;
+                    // word 0's row above: the lane above's last row (high half of
+                    // its last word) and this lane's row R/2 - 1 of the step before
+                    const uint32_t upH = __byte_perm(inH, outHw, 0x5432);
+                    const uint32_t upF = LIN ? 0u : __byte_perm(inF, outFw, 0x5432);
+                    int c0 = cres[u];
+                    int c1 = u == 0 ? ccarry : cres[u - 1];
+#if SWGB_STEP_ORDER_FENCE
+                    asm volatile("" : "+r"(c0), "+r"(c1) : "r"(inH));
+#endif
+                    int sc[R];
+                    load_scores_halves<R, false, 2>(prof, c0, c1, lane, sc);
+                    uint32_t diag = diag0w;
+                    uint32_t F = LIN ? 0u : __viaddmax_s16x2(upF, geP, upH);
+                    uint32_t hprev = upH;
+                    uint32_t acc = Tw;
 #pragma unroll
-                    for (int r = RH; r < R; ++r) {
+                    for (int k = 0; k < W; ++k) {
+                        // carry-free: both halves of every term are non-negative
+                        const uint32_t D = diag + (uint32_t)sc[k] + (uint32_t)sc[W + k];
+                        uint32_t V;
+                        if constexpr (LIN) {
+                            // go == ge: E - go = H_left and F - go = H_up exactly
+                            V = __vimax3_s16x2(D, Hw[k], hprev);
+                        } else {
+                            if (k > 0) F = __viaddmax_s16x2(F, geP, hprev);
+                            Ew[k] = __viaddmax_s16x2(Ew[k], geP, Hw[k]);
+                            V = __vimax3_s16x2(D, Ew[k], F);
+                        }
+                        const uint32_t h = __viaddmax_s16x2_relu(V, goP, 0u);
+                        diag = Hw[k];
+                        Hw[k] = h;
+                        hprev = h;
+                        acc = __viaddmax_s16x2(h, (uint32_t)(W - 1 - k) * 0x10001u, acc);
+                    }
+                    outHw = hprev;
+                    outFw = F;
+                    if (gl == G - 1 && has_out && in1)
+                        bout_ring[j1 & 31] = __byte_perm(outHw, outFw, 0x7632);
+                    diag0w = upH;
+                    // a half whose best score grew records (column, acc half)
+                    const uint32_t x = acc ^ Tw;
+                    const uint32_t jw = ((uint32_t)j0 & 0xFFFFu) | ((uint32_t)j1 << 16);
+                    if (x & 0xFFFFu) rec_lo = __byte_perm(acc, jw, 0x5410);
+                    if (x >> 16) rec_hi = __byte_perm(acc, jw, 0x7632);
+                    Tw = acc | tmask;
+                } else {
+                    constexpr int RH = R / kHalves;
+                    const int j0 = s + u - kHalves * gl;  // column of the upper rows
+                    const int j1 = j0 - (kHalves - 1);    // column of the lane's last row
+                    const bool in0 = (unsigned)j0 < (unsigned)mcols;
+                    const bool in1 = (unsigned)j1 < (unsigned)mcols;
+                    int inH = __shfl_up_sync(kFull, outH, 1, G);
+                    int inF = LIN ? 0 : __shfl_up_sync(kFull, outF, 1, G);
+                    if (gl == 0) {
+                        // previous strip's last row, or H = 0 / F = -inf above the
+                        // first strip and outside the columns
+                        const uint32_t w = in0 ? bws[u] : kNoBound;
+                        inH = (int)(w << 16);
+                        inF = (int)(w & 0xFFFF0000u);
+                    }
+                    int c0 = cres[u];
+                    int c1 = kHalves == 2 ? (u == 0 ? ccarry : cres[u - 1]) : c0;
+    #if SWGB_STEP_ORDER_FENCE
+                    // keep this step's profile loads after its shuffle, so the
+                    // compiler does not hoist every unrolled step's loads
+                    asm volatile("" : "+r"(c0), "+r"(c1) : "r"(inH));
+    #endif
+                    int sc[R];
+                    load_scores_halves<R, P8, kHalves>(prof, c0, c1, lane, sc);
+                    // key column part, less go: the key of H + go is (H << 16) + cj
+                    const int cjg0 = kColBase - j0 - goS;
+                    // upper rows, from the row above (shuffle or strip boundary)
+                    int diag = diag0;
+                    int F = LIN ? 0 : __viaddmax_s32(inF, geS, inH);
+                    int hprev = inH;
+    #pragma unroll
+                    for (int r = 0; r < RH; ++r) {
                         int h;
                         if constexpr (LIN) {
-                            h = __vimax3_s32_relu(diag1 + sc[r], H[r], hprev1) + goS;
+                            // go == ge: E = H_left + go and F = H_up + go exactly
+                            h = __vimax3_s32_relu(diag + sc[r], H[r], hprev) + goS;
                         } else {
-                            if (r > RH) F1 = __viaddmax_s32(F1, geS, hprev1);
+                            if (r > 0) F = __viaddmax_s32(F, geS, hprev);
                             E[r] = __viaddmax_s32(E[r], geS, H[r]);
-                            h = __vimax3_s32_relu(diag1 + sc[r], E[r], F1) + goS;
+                            h = __vimax3_s32_relu(diag + sc[r], E[r], F) + goS;
                         }
-                        diag1 = H[r];
+                        diag = H[r];
                         H[r] = h;
-                        hprev1 = h;
-                        K[r] = (uint32_t)__viaddmax_s32(h, cjg1, (int)K[r]);
+                        hprev = h;
+                        K[r] = (uint32_t)__viaddmax_s32(h, cjg0, (int)K[r]);
                     }
-                    midD = midH;
-                    midH = upH;
-                    midF = upF;
-                    hprev = hprev1;
-                    F = F1;
+                    if constexpr (kHalves == 2) {
+                        // lower rows, one column behind, from the upper half's last
+                        // row of the previous step
+                        const int upH = hprev, upF = F;
+                        const int cjg1 = cjg0 + 1;
+                        int diag1 = midD;
+                        int F1 = LIN ? 0 : __viaddmax_s32(midF, geS, midH);
+                        int hprev1 = midH;
+    #pragma unroll
+                        for (int r = RH; r < R; ++r) {
+                            int h;
+                            if constexpr (LIN) {
+                                h = __vimax3_s32_relu(diag1 + sc[r], H[r], hprev1) + goS;
+                            } else {
+                                if (r > RH) F1 = __viaddmax_s32(F1, geS, hprev1);
+                                E[r] = __viaddmax_s32(E[r], geS, H[r]);
+                                h = __vimax3_s32_relu(diag1 + sc[r], E[r], F1) + goS;
+                            }
+                            diag1 = H[r];
+                            H[r] = h;
+                            hprev1 = h;
+                            K[r] = (uint32_t)__viaddmax_s32(h, cjg1, (int)K[r]);
+                        }
+                        midD = midH;
+                        midH = upH;
+                        midF = upF;
+                        hprev = hprev1;
+                        F = F1;
+                    }
+                    outH = hprev;
+                    outF = F;
+                    if (gl == G - 1 && has_out && in1)
+                        bout_ring[j1 & 31] = __byte_perm((uint32_t)outH, (uint32_t)outF, 0x7632);
+                    diag0 = inH;
                 }
-                outH = hprev;
-                outF = F;
-                if (gl == G - 1 && has_out && in1)
-                    bout_ring[j1 & 31] = __byte_perm((uint32_t)outH, (uint32_t)outF, 0x7632);
-                diag0 = inH;
             }
             ccarry = cres[kU - 1];
             s += kU;
@@ -638,23 +766,53 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 int frow = 0x7fffffff, fcol = 0;
                 if (!rev) {
                     if (ps < passes) {
+                        if constexpr (PK) {
+                            // the two halves' records, upper rows first
 #pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            if (K[r] > best_key) {
-                                best_key = K[r];
-                                best_row = row0 + r;
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const uint32_t rec = hh ? rec_hi : rec_lo;
+                                const int val = (int)(rec & 0xFFFFu);
+                                const int col = min((int)(rec >> 16), kColBase);
+                                const uint32_t key =
+                                    ((uint32_t)(val >> 3) << 16) | (uint32_t)(kColBase - col);
+                                const int row = row0 + hh * W + (W - 1) - (val & 7);
+                                if ((val >> 3) > 0 && key > best_key) {
+                                    best_key = key;
+                                    best_row = row;
+                                }
                             }
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                if (K[r] > best_key) {
+                                    best_key = K[r];
+                                    best_row = row0 + r;
+                                }
+                        }
                     }
                     cold.best_key[t] = best_key;
                     cold.best_row[t] = best_row;
                 } else {
                     const int target = cold.target[t];
+                    if constexpr (PK) {
+                        // lower rows first, so that the upper half's record wins
 #pragma unroll
-                    for (int r = R - 1; r >= 0; --r)
-                        if ((int)(K[r] >> 16) >= target) {
-                            frow = row0 + r;
-                            fcol = kColBase - (int)(K[r] & 0xFFFFu);
+                        for (int hh = 1; hh >= 0; --hh) {
+                            const uint32_t rec = hh ? rec_hi : rec_lo;
+                            const int val = (int)(rec & 0xFFFFu);
+                            if ((val >> 3) >= target) {
+                                frow = row0 + hh * W + (W - 1) - (val & 7);
+                                fcol = (int)(rec >> 16);
+                            }
                         }
+                    } else {
+#pragma unroll
+                        for (int r = R - 1; r >= 0; --r)
+                            if ((int)(K[r] >> 16) >= target) {
+                                frow = row0 + r;
+                                fcol = kColBase - (int)(K[r] & 0xFFFFu);
+                            }
+                    }
                     for (int off = 1; off < G; off <<= 1) {
                         const int orow = __shfl_xor_sync(gmask, frow, off, G);
                         const int ocol = __shfl_xor_sync(gmask, fcol, off, G);
@@ -754,11 +912,20 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
 // under a launch that needs more.  Occupancy per (profile, alphabet) is
 // cached per device.
 namespace {
-// the four instantiations, indexed by (int8 profile, linear gaps)
+// the six instantiations, indexed by (profile kind, linear gaps)
 using GroupKernel = void (*)(GroupParams);
-GroupKernel group_kernel_of(bool p8, bool lin) {
-    if (p8) return lin ? sw_group_kernel<kRows, true, true> : sw_group_kernel<kRows, true, false>;
-    return lin ? sw_group_kernel<kRows, false, true> : sw_group_kernel<kRows, false, false>;
+GroupKernel group_kernel_of(ProfileKind kind, bool lin) {
+    switch (kind) {
+        case ProfileKind::kInt8:
+            return lin ? sw_group_kernel<kRows, true, true, false>
+                       : sw_group_kernel<kRows, true, false, false>;
+        case ProfileKind::kPacked16:
+            return lin ? sw_group_kernel<kRows, false, true, true>
+                       : sw_group_kernel<kRows, false, false, true>;
+        default:
+            return lin ? sw_group_kernel<kRows, false, true, false>
+                       : sw_group_kernel<kRows, false, false, false>;
+    }
 }
 }  // namespace
 
@@ -768,13 +935,12 @@ int group_blocks_per_sm(ProfileKind kind, bool linear, int alphabet, int *smem_b
     if (alphabet < 1 || alphabet > kMaxAlphabet) return -1;
     constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static int cache[kMaxDevices][4][kMaxAlphabet + 1];
-    static bool raised[kMaxDevices][4];
+    static int cache[kMaxDevices][6][kMaxAlphabet + 1];
+    static bool raised[kMaxDevices][6];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
-    const bool p8 = kind == ProfileKind::kInt8;
-    const int ki = (p8 ? 2 : 0) + (linear ? 1 : 0);
-    const GroupKernel fn = group_kernel_of(p8, linear);
+    const int ki = 2 * (int)kind + (linear ? 1 : 0);
+    const GroupKernel fn = group_kernel_of(kind, linear);
     std::lock_guard<std::mutex> lk(mu);
     if (cache[dev][ki][alphabet] > 0) return cache[dev][ki][alphabet];
     int optin = 0;
@@ -801,7 +967,7 @@ cudaError_t launch_group(const GroupParams &p, ProfileKind kind, bool linear, in
                          cudaStream_t s) {
     if (p.n_classes <= 0 || grid <= 0) return cudaSuccess;
     const size_t smem = group_smem_bytes(kind, p.alphabet);
-    group_kernel_of(kind == ProfileKind::kInt8, linear)<<<grid, kGroupWarps * 32, smem, s>>>(p);
+    group_kernel_of(kind, linear)<<<grid, kGroupWarps * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -141,8 +141,18 @@ std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n
                                        int sample_cap = 8192);
 int64_t sweep_steps(int n, int m, int G);
 
-// Profile element width of the group kernel.
-enum class ProfileKind : int { kInt32 = 0, kInt8 = 1 };
+// Arithmetic and profile element width of the group kernel: scaled int32
+// with an int32 or int8 profile, or two 16-bit cells per 32-bit word.
+enum class ProfileKind : int { kInt32 = 0, kInt8 = 1, kPacked16 = 2 };
+
+// Whether a pair fits the packed 16-bit form: every value 8 x (score terms)
+// stays in a signed 16-bit half, profile scores s - go are non-negative.
+inline bool packed_eligible(int n, int m, int smax, int smin, int gap_open, int gap_extend) {
+    if (smin < gap_open || 8 * (int64_t)(-gap_extend) > 16384) return false;
+    const int64_t bound = (int64_t)(smax > 0 ? smax : 0) * (n < m ? n : m) +
+                          (smax > 0 ? smax : 0) - gap_open;
+    return 8 * bound <= 32767;
+}
 
 // A batch planned on the host (host_plan.cpp): the device tables to upload
 // and the launch shapes.
@@ -199,11 +209,13 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
 // warp per this many group-path pairs (1 = lowest latency; 32 >> kMinLog2G
 // fills every group of the narrowest width, for a GPU shared with other
 // launches).  sample_cap: pairs the planner's schedule simulation looks at
-// (fewer plan faster, more plan better).
+// (fewer plan faster, more plan better).  allow_packed = false keeps the
+// scaled int32 arithmetic even where the packed 16-bit form's bound holds.
 int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
-                   std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192);
+                   std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192,
+                   bool allow_packed = true);
 // Enqueues the kernels of a planned batch on s (queue-head reset included).
 cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
                          const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,

@@ -1,0 +1,159 @@
+"""GPU parity of the packed 16-bit form of the batched kernel.
+
+The packed form holds two DP cells per 32-bit word (scores scaled by 8, the
+end cell tracked per column with a 3-bit row code).  It must give the same
+five outputs as the scaled int32 form and the oracle, bit for bit, wherever
+the plan takes it; these tests run both forms on the same batches (the int32
+one with SW_PLAN_NO_S16X2) and check which form each plan took.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+from test_gpu_parity import EDGE, TUNINGS, assert_same, edge_batch, run_lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(gpu_lib):
+    c = gpu_lib.sw_ctx_create(0)
+    yield c
+    gpu_lib.sw_ctx_destroy(c)
+
+
+def both_forms(gpu_lib, ctx, b, expect, name, tuning=None, want_packed=True):
+    got, info = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_BATCHED, tuning=tuning)
+    assert info["arith"] == ("s16x2" if want_packed else "s32"), (name, info)
+    assert_same(got, expect, f"{name} ({info['arith']})")
+    got32, info32 = run_lib(gpu_lib, ctx, b, mode=gpu_lib.SW_MODE_BATCHED,
+                            flags=gpu_lib.SW_PLAN_NO_S16X2, tuning=tuning)
+    assert info32["arith"] == "s32"
+    assert_same(got32, expect, f"{name} (s32)")
+
+
+def test_form_selection(gpu_lib, ctx):
+    """DNA workloads fit the packed bound; full-length protein pairs
+    (11 x 400 + 22 > 4095) and scoring with a mismatch below gap_open do not."""
+    b0 = wl.gen_config(0, n_pairs=50)
+    _, info = run_lib(gpu_lib, ctx, b0)
+    assert info["arith"] == "s16x2"
+    _, info = run_lib(gpu_lib, ctx, b0, flags=gpu_lib.SW_PLAN_NO_S16X2)
+    assert info["arith"] == "s32"
+    b2 = wl.gen_config(2)
+    _, info = run_lib(gpu_lib, ctx, b2.slice(0, 2000))
+    assert info["arith"] == "s32"
+    fig2 = wl.make_batch("fig2", [b0.pair(i)[0] for i in range(b0.n_pairs)],
+                         [b0.pair(i)[1] for i in range(b0.n_pairs)], wl.dna_matrix(2, -2), -1, -1)
+    _, info = run_lib(gpu_lib, ctx, fig2)
+    assert info["arith"] == "s32"  # s - go = -1 < 0
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=[f"G{1 << t[0] if t[0] >= 0 else 'auto'}-cap{t[1]:g}"
+                                                 for t in TUNINGS])
+def test_edge_lengths_both_forms(gpu_lib, ctx, tuning):
+    """Lengths around every tile edge under every lane-group width, both forms."""
+    b = edge_batch("dna", 70 + max(tuning[0], 0), EDGE, EDGE[1::3])
+    both_forms(gpu_lib, ctx, b, oracle.align_workload(b), f"edge tuning={tuning}", tuning)
+
+
+def _periodic(unit, n):
+    return np.resize(np.array(unit, np.uint8), n)
+
+
+def test_tie_heavy_inputs(gpu_lib, ctx):
+    """Periodic and constant sequences: many cells share the best score, so
+    the end rule (smallest rend, then qend) and the start rule (largest
+    rstart, then qstart) decide among many candidates in both sweeps."""
+    rng = np.random.default_rng(101)
+    qs, rs = [], []
+    units = [[0], [0, 1], [0, 1, 2], [0, 0, 1], [2, 3, 2, 3, 1]]
+    for n in (1, 7, 8, 9, 16, 17, 40, 64, 65, 130, 300):
+        for m in (1, 8, 15, 33, 64, 200, 513):
+            uq = units[int(rng.integers(len(units)))]
+            ur = units[int(rng.integers(len(units)))]
+            qs.append(_periodic(uq, n))
+            rs.append(_periodic(ur, m))
+    b = wl.make_batch("ties", qs, rs, wl.dna_matrix(), -6, -1)
+    expect = oracle.align_workload(b)
+    for tuning in ((1, 1e9), (2, 1e9), (4, 1e9), (5, 1e9), (-1, 0.5)):
+        both_forms(gpu_lib, ctx, b, expect, f"ties {tuning}", tuning)
+    # zero gap penalties: trailing gaps are free, so gap cells tie with their
+    # neighbours (needs mismatch >= gap_open = 0 for the packed form)
+    b0 = wl.make_batch("ties-free-gaps", qs, rs, wl.dna_matrix(2, 0), 0, 0)
+    both_forms(gpu_lib, ctx, b0, oracle.align_workload(b0), "ties, gaps 0/0", (2, 1e9))
+
+
+def test_hand_worked_examples(gpu_lib, ctx):
+    """The small cases whose outputs were worked out by hand (end ties on
+    rend and on qend, a start tie, no alignment, a gap in the best path)."""
+    enc = {"A": 0, "C": 1, "G": 2, "T": 3}
+    pairs = [("ACGTACGT", "ACGTTACGT"), ("AC", "ACAC"), ("ACAC", "AC"), ("ACGGGG", "AAGGGG"),
+             ("AAAA", "CCCC"), ("ATGCT", "AGCT")]
+    qs = [np.array([enc[c] for c in q], np.uint8) for q, _ in pairs]
+    rs = [np.array([enc[c] for c in r], np.uint8) for _, r in pairs]
+    b = wl.make_batch("hand", qs, rs, wl.dna_matrix(), -6, -1)
+    expect = oracle.align_workload(b)
+    assert expect[:5].tolist() == [[18, 7, 8, 0, 0], [6, 1, 1, 0, 0], [6, 1, 1, 0, 0],
+                                   [12, 5, 5, 2, 2], [0, -1, -1, -1, -1]]
+    both_forms(gpu_lib, ctx, b, expect, "hand-worked", (1, 1e9))
+
+
+@pytest.mark.parametrize("lg", [1, 3])
+def test_packed_bound_edges(gpu_lib, ctx, lg):
+    """8 (3 min(n, m) + 3 + 6) <= 32767 holds up to min(n, m) = 1362: a
+    self-alignment there scores 4086 (scaled 32688) in the packed form; one
+    residue more and the plan keeps int32.  Both exact."""
+    rng = np.random.default_rng(53 + lg)
+    for L, packed in ((1362, True), (1363, False)):
+        qs, rs = [], []
+        for extra in (0, 5, 700):
+            q = rng.integers(0, 4, L).astype(np.uint8)
+            r = np.concatenate([rng.integers(0, 4, extra).astype(np.uint8), q])
+            qs.append(q)
+            rs.append(r)
+            qs.append(q.copy())
+            rs.append(q.copy())
+        b = wl.make_batch(f"bound-{L}", qs, rs, wl.dna_matrix(), -6, -1)
+        expect = oracle.align_workload(b)
+        assert expect[:, 0].max() == 3 * L
+        both_forms(gpu_lib, ctx, b, expect, f"bound L={L}", (lg, 1e9), want_packed=packed)
+
+
+def test_linear_gaps_packed(gpu_lib, ctx):
+    """go == ge with s - go >= 0 takes the packed form without E and F."""
+    for mat, g in ((wl.dna_matrix(), -3), (wl.dna_matrix(2, -2), -2)):
+        src = wl.gen_config(1, n_pairs=300)
+        b = wl.make_batch("lin-packed", [src.pair(i)[0] for i in range(src.n_pairs)],
+                          [src.pair(i)[1] for i in range(src.n_pairs)], mat, g, g)
+        expect = oracle.align_workload(b)
+        for tuning in ((1, 1e9), (3, 1e9), (-1, 0.5)):
+            both_forms(gpu_lib, ctx, b, expect, f"linear {g}", tuning)
+
+
+def test_protein_short_pairs_packed(gpu_lib, ctx):
+    """BLOSUM62 (-11/-1) pairs with min(n, m) <= 300 fit the packed bound."""
+    src = wl.gen_config(2, n_pairs=400)
+    qs = [src.pair(i)[0][:300] for i in range(src.n_pairs)]
+    rs = [src.pair(i)[1] for i in range(src.n_pairs)]
+    b = wl.make_batch("protein-short", qs, rs, src.matrix, src.gap_open, src.gap_extend)
+    expect = oracle.align_workload(b)
+    for tuning in ((2, 1e9), (5, 1e9), (-1, 0.5)):
+        both_forms(gpu_lib, ctx, b, expect, f"protein short {tuning}", tuning)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_full_workloads_packed_vs_int32(gpu_lib, ctx, k):
+    """The 100k- and 200k-pair DNA workloads in the benchmark's launch form:
+    the packed form equals the int32 form on every pair and the oracle on a
+    sample."""
+    b = wl.gen_config(k)
+    got, info = run_lib(gpu_lib, ctx, b, flags=gpu_lib.SW_PLAN_GRAPH)
+    assert info["arith"] == "s16x2"
+    got32, info32 = run_lib(gpu_lib, ctx, b, flags=gpu_lib.SW_PLAN_GRAPH | gpu_lib.SW_PLAN_NO_S16X2)
+    assert info32["arith"] == "s32"
+    assert_same(got, got32, f"config{k} packed vs int32")
+    idx = np.random.default_rng(k).choice(b.n_pairs, 2000, replace=False)
+    assert_same(got[idx], oracle.align_workload(b, idx=idx), f"config{k} sample")
