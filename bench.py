@@ -208,13 +208,14 @@ def run_reference(args, rank):
 
 # ------------------------------------------------------------ ncu traffic
 
-def profiled_traffic(batch, tune) -> int | None:
+def profiled_traffic(batch, tune, arith="s16x2") -> int | None:
     """DRAM bytes per launch of the group kernel from the committed ncu
-    summary, if that capture was of this workload, this tuning and this
-    kernel source (else None: the counters are stale)."""
+    summary, if that capture was of this workload, this arithmetic, this
+    tuning and this kernel source (else None: the counters are stale)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", f"sw_group_kernel_{batch.name}.md")
+    form = "" if arith == "s16x2" else "s32_"
+    path = os.path.join(ROOT, "profiles", f"sw_group_kernel_{form}{batch.name}.md")
     src = os.path.join(ROOT, "paper_2208_12350_gb300", "csrc", "kernel_group.cu")
     if not os.path.exists(path) or tune is None:
         return None
@@ -474,8 +475,8 @@ def run_ours(args, rank, world, local):
     mb_rate, _ = swgb.sw_microbench_int(peak_op, local, 2048)
     peak_measured = mb_rate / 1e12
     sm_mhz = clk.get("sm_mhz")
-    traffic = profiled_traffic(batch, tune) if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] \
-        else None
+    traffic = profiled_traffic(batch, tune, info["arith"]) \
+        if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
             "frac": achieved / peak_measured if peak_measured else None, "traffic": traffic,
             "peak_kind": f"measured __{peak_op} issue rate, whole device, this run",

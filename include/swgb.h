@@ -379,7 +379,7 @@ int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
  * Integer issue-rate microbenchmark on `device` (made current for the call;
  * synchronous).  op: 0 = 32-bit add, 1 = 32-bit max, 2 = __viaddmax_s32
  * (add then max), 3 = __vimax3_s32_relu, 4 = __viaddmax_s16x2,
- * 5 = __vimax_s32_relu.  Runs 64 warps per SM, each thread 8 independent
+ * 5 = __vimax_s32_relu, 6 = __vimax3_s16x2, 7 = __viaddmax_s16x2_relu.  Runs 64 warps per SM, each thread 8 independent
  * chains of `iters` x 16 instructions, and returns whole-device
  * instructions per second (per 32-bit lane) in *ops_per_s and the timed
  * duration in *seconds (may be NULL).  This measures the denominator of the

@@ -274,7 +274,8 @@ def sw_check_residues(seqs, n: int, alphabet_size: int, bad_count, stream=None) 
 
 
 MICROBENCH_OPS = {"iadd": 0, "imax": 1, "viaddmax_s32": 2, "vimax3_s32_relu": 3,
-                  "viaddmax_s16x2": 4, "vimax_s32_relu": 5}
+                  "viaddmax_s16x2": 4, "vimax_s32_relu": 5, "vimax3_s16x2": 6,
+                  "viaddmax_s16x2_relu": 7}
 
 
 def sw_microbench_int(op: str, device: int = 0, iters: int = 4096) -> tuple[float, float]:

@@ -17,6 +17,8 @@ __device__ __forceinline__ int step(int a, int b, int c) {
     if constexpr (OP == 3) return __vimax3_s32_relu(a, b, c);     // 3-way max with 0
     if constexpr (OP == 4) return (int)__viaddmax_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
     if constexpr (OP == 5) return __vimax_s32_relu(a, b);         // 2-way max with 0
+    if constexpr (OP == 6) return (int)__vimax3_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
+    if constexpr (OP == 7) return (int)__viaddmax_s16x2_relu((unsigned)a, (unsigned)b, (unsigned)c);
     return a;
 }
 
@@ -55,7 +57,7 @@ cudaError_t run(int blocks, int threads, int64_t iters, int *sink, cudaStream_t 
 extern "C" int sw_microbench_int(int32_t op, int32_t device, int64_t iters, double *ops_per_s,
                                  double *seconds) {
     using namespace swgb;
-    if (!ops_per_s || op < 0 || op > 5 || iters < 1) return SW_EINVAL;
+    if (!ops_per_s || op < 0 || op > 7 || iters < 1) return SW_EINVAL;
     int prev = 0;
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) return SW_ECUDA;
@@ -79,7 +81,9 @@ extern "C" int sw_microbench_int(int32_t op, int32_t device, int64_t iters, doub
             case 2: return run<2>(blocks, threads, it, sink, 0);
             case 3: return run<3>(blocks, threads, it, sink, 0);
             case 4: return run<4>(blocks, threads, it, sink, 0);
-            default: return run<5>(blocks, threads, it, sink, 0);
+            case 5: return run<5>(blocks, threads, it, sink, 0);
+            case 6: return run<6>(blocks, threads, it, sink, 0);
+            default: return run<7>(blocks, threads, it, sink, 0);
         }
     };
     float ms = 0.f;
