@@ -227,6 +227,9 @@ def profiled_traffic(batch, tune, arith="s16x2") -> int | None:
         return None
     if sha.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
         return None
+    ar = re.search(r"arith: (\w+)", text)
+    if (ar.group(1) if ar else "s32") != arith:
+        return None
     if int(tun.group(1)) != tune["narrow_log2g"]:
         return None
     if tun.group(2) != "any" and abs(float(tun.group(2)) - tune["cap_fraction"]) > 1e-9:
