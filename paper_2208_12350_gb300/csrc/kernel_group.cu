@@ -107,18 +107,19 @@ namespace swgb {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// Steps per block (one staging round, one strip-end check): 4 for the int32
-// form (at 8 it spills), 8 for the packed form (12 % faster than 4 on 100k
-// and 200k DNA pairs, fewer per-block instructions per cell).
+// Steps per block (one staging round, one strip-end check): 8 for the
+// packed form (12 % faster than 4 on 100k and 200k DNA pairs: fewer
+// per-block instructions per cell) and the int8-profile int32 form (+2 % on
+// 20k protein pairs), 4 for the int32-profile int32 form (at 8 it spills).
 #ifndef SWGB_GROUP_UNROLL
 #define SWGB_GROUP_UNROLL 4
 #endif
 #ifndef SWGB_PACKED_UNROLL
 #define SWGB_PACKED_UNROLL 8
 #endif
-template <bool PK>
+template <bool P8, bool PK>
 __host__ __device__ constexpr int unroll_of() {
-    return PK ? SWGB_PACKED_UNROLL : SWGB_GROUP_UNROLL;
+    return (PK || P8) ? SWGB_PACKED_UNROLL : SWGB_GROUP_UNROLL;
 }
 #ifndef SWGB_STEP_ORDER_FENCE
 #define SWGB_STEP_ORDER_FENCE 1
@@ -136,9 +137,9 @@ __host__ __device__ constexpr int halves_of() {
 }
 // blocks between a cp.async and the first use; the copies in flight plus the
 // block being read stay within six of the eight 16-byte slots of a ring
-template <bool PK>
+template <bool P8, bool PK>
 __host__ __device__ constexpr int ahead_of() {
-    return unroll_of<PK>() == 4 ? 3 : 2;
+    return unroll_of<P8, PK>() == 4 ? 3 : 2;
 }
 constexpr int kMaxGroups = 32 >> kMinLog2G;
 constexpr int kRingBytes = 128;        // per group and ring
@@ -329,8 +330,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
     extern __shared__ __align__(16) char smem_group[];
     constexpr int kHalves = halves_of<P8, PK>();
     constexpr int W = R / 2;  // packed words per lane
-    constexpr int kU = unroll_of<PK>();
-    constexpr int kAhead = ahead_of<PK>();
+    constexpr int kU = unroll_of<P8, PK>();
+    constexpr int kAhead = ahead_of<P8, PK>();
     static_assert(kU == 4 || kU == 8, "blocks move whole 16-byte chunks of 4 boundary columns");
     const int A = p.alphabet;
     const int go = p.gap_open, ge = p.gap_extend;
