@@ -193,6 +193,17 @@ __device__ __forceinline__ void build_profile_group(char *prof, int lane, int gb
     static_assert(!P8 || R == 8 || R == 16 || R == 32, "int8 profile holds 8, 16 or 32 rows");
     const int G = 1 << log2g;
     const int units = G * (R / 4);
+    if (row_base == 0 && dir > 0) {
+        // first strip of a forward sweep: the later strips' query rows are
+        // read by their profile builds only, one strip at a time; bring the
+        // rest of the query (up to 4 KB) into L2 now, so those builds do not
+        // wait on DRAM
+        const int line = lane * 128 + G * R;
+        if (line < nrows && lane * 128 < 4096) {
+            const uint8_t *ptr = a + line;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+        }
+    }
     for (int u = lane; u < units; u += 32) {
         const int tl = u & (G - 1), k = u >> log2g;
         const int tlane = gb + tl;
@@ -629,15 +640,13 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     // high halves rows [R/2, R) at j0 - 1
                     const int j0 = s + u - 2 * gl;
                     const int j1 = j0 - 1;
-                    const bool in0 = (unsigned)j0 < (unsigned)mcols;
                     const bool in1 = (unsigned)j1 < (unsigned)mcols;
                     uint32_t inH = __shfl_up_sync(kFull, outHw, 1, G);
                     uint32_t inF = LIN ? 0u : __shfl_up_sync(kFull, outFw, 1, G);
                     if (gl == 0) {
                         // previous strip's last row (H low, F - go high), or (0, 0)
-                        const uint32_t w = in0 ? bws[u] : kNoBound;
-                        inH = w;
-                        inF = w;
+                        inH = bws[u];
+                        inF = bws[u];
                     }
                     // word 0's row above: the lane above's last row (high half of
                     // its last word; lane 0: the boundary word's halves) and this
@@ -681,23 +690,24 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     diag0w = upH;
                     // a half whose best score grew records (step, acc half); the
                     // step gives the column: j0 = step - 2 gl, j1 = j0 - 1
-                    const uint32_t x = acc ^ Tw;
+                    // (acc >= Tw in both halves; "Tw >= acc" means unchanged)
+                    bool keep_hi, keep_lo;
+                    (void)__vibmax_s16x2(Tw, acc, &keep_hi, &keep_lo);
                     const uint32_t stw = stw0 + (uint32_t)u * 0x10001u;
-                    if (x & 0xFFFFu) rec_lo = __byte_perm(acc, stw, 0x5410);
-                    if (x >> 16) rec_hi = __byte_perm(acc, stw, 0x7632);
+                    if (!keep_lo) rec_lo = __byte_perm(acc, stw, 0x5410);
+                    if (!keep_hi) rec_hi = __byte_perm(acc, stw, 0x7632);
                     Tw = acc | tmask;
                 } else {
                     constexpr int RH = R / kHalves;
                     const int j0 = s + u - kHalves * gl;  // column of the upper rows
                     const int j1 = j0 - (kHalves - 1);    // column of the lane's last row
-                    const bool in0 = (unsigned)j0 < (unsigned)mcols;
                     const bool in1 = (unsigned)j1 < (unsigned)mcols;
                     int inH = __shfl_up_sync(kFull, outH, 1, G);
                     int inF = LIN ? 0 : __shfl_up_sync(kFull, outF, 1, G);
                     if (gl == 0) {
                         // previous strip's last row, or H = 0 / F = -inf above the
                         // first strip and outside the columns
-                        const uint32_t w = in0 ? bws[u] : kNoBound;
+                        const uint32_t w = bws[u];
                         inH = (int)(w << 16);
                         inF = (int)(w & 0xFFFF0000u);
                     }
@@ -771,14 +781,21 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
             ccarry = cres[kU - 1];
             s += kU;
             if (has_out) {
-                // words of the columns below s - kHalves * G + 1 are complete
+                // words of the columns below s - kHalves * G + 1 are complete;
+                // the 4-word group holding the last column waits for the strip end
                 const int done = (s - kHalves * G + 1) & ~3;
-                flush_out(min(done, (mcols + 3) & ~3));
+                flush_out(min(done, mcols & ~3));
             }
 
             // ---- end of a strip / sweep
             if (live && s >= lim) {
-                if (has_out) flush_out((mcols + 3) & ~3);
+                if (has_out) {
+                    // the next strip reads whole 4-word groups without a column
+                    // check: the columns past the last one say "no row above"
+                    if (gl == G - 1)
+                        for (int c = mcols; c < ((mcols + 3) & ~3); ++c) bout_ring[c & 31] = kNoBound;
+                    flush_out((mcols + 3) & ~3);
+                }
                 const int ps = cold.ps[t], passes = cold.passes[t];
                 const int row0 = ps * G * R + gl * R;
                 uint32_t best_key = cold.best_key[t];
