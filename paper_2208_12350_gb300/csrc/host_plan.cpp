@@ -143,7 +143,8 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         out->n_warps = out->grid * kGroupWarps;
     }
     const std::vector<PlannedClass> planned =
-        plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction, sample_cap);
+        plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction, sample_cap,
+                     out->kind == ProfileKind::kPacked16);
     out->pairs.reserve(gp.size());
     int warp_begin = 0;
     for (const PlannedClass &pc : planned) {

@@ -138,7 +138,7 @@ struct PlannedClass {
 };
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
                                        int narrow_log2g_hint, double cap_fraction_hint,
-                                       int sample_cap = 8192);
+                                       int sample_cap = 8192, bool half_tails = false);
 int64_t sweep_steps(int n, int m, int G);
 
 // Arithmetic and profile element width of the group kernel: scaled int32
