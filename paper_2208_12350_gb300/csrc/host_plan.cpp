@@ -99,6 +99,13 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     for (int32_t i = 0; i < n_pairs && packed; ++i)
         if (group_path_eligible(n[i], m[i], smax, go, ge))
             packed = packed_eligible(n[i], m[i], smax, smin, go, ge);
+    // its profile holds 32-bit words; with large alphabets fewer than two
+    // blocks fit on an SM, and the int32 form's int8 profile runs faster
+    if (packed) {
+        const int b = group_blocks_per_sm(ProfileKind::kPacked16, go == ge, A, nullptr);
+        if (b < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
+        packed = b >= 2;
+    }
     if (packed)
         out->kind = ProfileKind::kPacked16;
     else if (A <= 4 && SWGB_SMALL_ALPHABET_INT32)
@@ -144,7 +151,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     }
     const std::vector<PlannedClass> planned =
         plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction, sample_cap,
-                     out->kind == ProfileKind::kPacked16);
+                     out->kind == ProfileKind::kPacked16, rows_of(out->kind));
     out->pairs.reserve(gp.size());
     int warp_begin = 0;
     for (const PlannedClass &pc : planned) {
@@ -155,7 +162,8 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         for (int32_t k : pc.pairs) {
             const int32_t i = gid[k];
             PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
-            const int64_t w = n[i] > 0 && m[i] > 0 ? pair_scratch_words(n[i], m[i], G, kRows) : 0;
+            const int64_t w =
+                n[i] > 0 && m[i] > 0 ? pair_scratch_words(n[i], m[i], G, rows_of(out->kind)) : 0;
             if (w > 0) {
                 pi.scratch = out->scratch_words;
                 out->scratch_words += w;

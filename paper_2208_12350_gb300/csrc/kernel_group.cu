@@ -335,12 +335,13 @@ constexpr int kColdWords = 2 * 2 + 11;  // 32-bit words per lane
 }  // namespace
 
 template <int R, bool P8, bool LIN, bool PK>
-__global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
+__global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupMinBlocks)
     sw_group_kernel(const __grid_constant__ GroupParams p) {
-    static_assert(!PK || (!P8 && R == 16), "the packed form holds 16 rows in 8 words");
+    static_assert(!PK || (!P8 && R % 16 == 0), "the packed form holds 16 rows per 8 words");
     extern __shared__ __align__(16) char smem_group[];
     constexpr int kHalves = halves_of<P8, PK>();
-    constexpr int W = R / 2;  // packed words per lane
+    constexpr int W = R / 2;   // packed words per lane
+    constexpr int NC = W / 8;  // end-key chains (3-bit row codes, 8 words each)
     constexpr int kU = unroll_of<P8, PK>();
     constexpr int kAhead = ahead_of<P8, PK>();
     static_assert(kU == 4 || kU == 8, "blocks move whole 16-byte chunks of 4 boundary columns");
@@ -432,7 +433,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
         // half: column << 16 | 8 score + row code)
         uint32_t Hw[W], Ew[W];
         uint32_t outHw = 0u, outFw = 0u, diag0w = 0u;
-        uint32_t Tw = 0x00070007u, tmask = 0x00070007u, rec_lo = 0u, rec_hi = 0u;
+        uint32_t Tw[NC], rec_lo[NC], rec_hi[NC], tmask = 0x00070007u;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Tw[c] = 0x00070007u, rec_lo[c] = rec_hi[c] = 0u;
         int s = 0, lim = 0, stop = 0, dir = 1;
         const uint8_t *bcol = p.r;  // column 0 of the current sweep
         int roff = 0;               // bcol's offset in its 16-byte chunk (mirrored if dir < 0)
@@ -510,9 +513,12 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 // forward: best score 0 with the largest row code; reverse:
                 // just below the score S with any row code
                 const uint32_t t0 = rev ? (uint32_t)(8 * cold.target[t] - 1) : 7u;
-                Tw = (t0 & 0xFFFFu) * 0x10001u;
                 tmask = rev ? 0u : 0x00070007u;
-                rec_lo = rec_hi = 0u;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    Tw[c] = (t0 & 0xFFFFu) * 0x10001u;
+                    rec_lo[c] = rec_hi[c] = 0u;
+                }
             }
             s = 0;
             // the lane's last row reaches the last column kHalves * G - 1 steps late
@@ -663,7 +669,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     uint32_t diag = diag0w;
                     uint32_t F = LIN ? 0u : __viaddmax_s16x2(upF, geP, upH);
                     uint32_t hprev = upH;
-                    uint32_t acc = Tw;
+                    uint32_t acc[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[c] = Tw[c];
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         // carry-free: both halves of every term are non-negative
@@ -681,7 +689,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                         diag = Hw[k];
                         Hw[k] = h;
                         hprev = h;
-                        acc = __viaddmax_s16x2(h, (uint32_t)(W - 1 - k) * 0x10001u, acc);
+                        acc[k / 8] = __viaddmax_s16x2(h, (uint32_t)(7 - k % 8) * 0x10001u, acc[k / 8]);
                     }
                     outHw = hprev;
                     outFw = F;
@@ -691,12 +699,15 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                     // a half whose best score grew records (step, acc half); the
                     // step gives the column: j0 = step - 2 gl, j1 = j0 - 1
                     // (acc >= Tw in both halves; "Tw >= acc" means unchanged)
-                    bool keep_hi, keep_lo;
-                    (void)__vibmax_s16x2(Tw, acc, &keep_hi, &keep_lo);
                     const uint32_t stw = stw0 + (uint32_t)u * 0x10001u;
-                    if (!keep_lo) rec_lo = __byte_perm(acc, stw, 0x5410);
-                    if (!keep_hi) rec_hi = __byte_perm(acc, stw, 0x7632);
-                    Tw = acc | tmask;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        bool keep_hi, keep_lo;
+                        (void)__vibmax_s16x2(Tw[c], acc[c], &keep_hi, &keep_lo);
+                        if (!keep_lo) rec_lo[c] = __byte_perm(acc[c], stw, 0x5410);
+                        if (!keep_hi) rec_hi[c] = __byte_perm(acc[c], stw, 0x7632);
+                        Tw[c] = acc[c] | tmask;
+                    }
                 } else {
                     constexpr int RH = R / kHalves;
                     const int j0 = s + u - kHalves * gl;  // column of the upper rows
@@ -806,15 +817,17 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 if (!rev) {
                     if (ps < passes) {
                         if constexpr (PK) {
-                            // the two halves' records, upper rows first
+                            // the records of both halves and every chain, in
+                            // ascending row order (ties keep the smaller row)
 #pragma unroll
-                            for (int hh = 0; hh < 2; ++hh) {
-                                const uint32_t rec = hh ? rec_hi : rec_lo;
+                            for (int q = 0; q < 2 * NC; ++q) {
+                                const int hh = q / NC, c = q % NC;
+                                const uint32_t rec = hh ? rec_hi[c] : rec_lo[c];
                                 const int val = (int)(rec & 0xFFFFu);
                                 const int col = min((int)(rec >> 16) - 2 * gl - hh, kColBase);
                                 const uint32_t key =
                                     ((uint32_t)(val >> 3) << 16) | (uint32_t)(kColBase - col);
-                                const int row = row0 + hh * W + (W - 1) - (val & 7);
+                                const int row = row0 + hh * W + 8 * c + 7 - (val & 7);
                                 if ((val >> 3) > 0 && key > best_key) {
                                     best_key = key;
                                     best_row = row;
@@ -834,13 +847,15 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
                 } else {
                     const int target = cold.target[t];
                     if constexpr (PK) {
-                        // lower rows first, so that the upper half's record wins
+                        // descending row order, so that the smallest row's
+                        // record is the one kept
 #pragma unroll
-                        for (int hh = 1; hh >= 0; --hh) {
-                            const uint32_t rec = hh ? rec_hi : rec_lo;
+                        for (int q = 2 * NC - 1; q >= 0; --q) {
+                            const int hh = q / NC, c = q % NC;
+                            const uint32_t rec = hh ? rec_hi[c] : rec_lo[c];
                             const int val = (int)(rec & 0xFFFFu);
                             if ((val >> 3) >= target) {
-                                frow = row0 + hh * W + (W - 1) - (val & 7);
+                                frow = row0 + hh * W + 8 * c + 7 - (val & 7);
                                 fcol = (int)(rec >> 16) - 2 * gl - hh;
                             }
                         }
@@ -937,9 +952,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32, kGroupMinBlocks)
 }
 
 size_t group_smem_bytes(ProfileKind kind, int alphabet) {
+    const size_t rows = (size_t)rows_of(kind);
     const size_t per_warp = kind == ProfileKind::kInt8
-                                ? (size_t)(alphabet + 1) * 32 * kRows
-                                : (size_t)(alphabet + 1) * (kRows / 4) * 32 * 16;
+                                ? (size_t)(alphabet + 1) * 32 * rows
+                                : (size_t)(alphabet + 1) * (rows / 4) * 32 * 16;
     return (size_t)kGroupWarps * 3 * kMaxGroups * kRingBytes +
            tab_bytes(kind == ProfileKind::kInt8, alphabet) +
            (size_t)kColdWords * 4 * kGroupWarps * 32 + kGroupWarps * per_warp;
@@ -959,8 +975,8 @@ GroupKernel group_kernel_of(ProfileKind kind, bool lin) {
             return lin ? sw_group_kernel<kRows, true, true, false>
                        : sw_group_kernel<kRows, true, false, false>;
         case ProfileKind::kPacked16:
-            return lin ? sw_group_kernel<kRows, false, true, true>
-                       : sw_group_kernel<kRows, false, false, true>;
+            return lin ? sw_group_kernel<kRowsPacked, false, true, true>
+                       : sw_group_kernel<kRowsPacked, false, false, true>;
         default:
             return lin ? sw_group_kernel<kRows, false, true, false>
                        : sw_group_kernel<kRows, false, false, false>;

@@ -29,9 +29,9 @@
 
 namespace swgb {
 
-int64_t sweep_steps(int n, int m, int G) {
+int64_t sweep_steps(int n, int m, int G, int rows) {
     if (n <= 0 || m <= 0) return 4;
-    const int64_t strips = (n + (int64_t)G * kRows - 1) / ((int64_t)G * kRows);
+    const int64_t strips = (n + (int64_t)G * rows - 1) / ((int64_t)G * rows);
     const int64_t cols = ((int64_t)m + G - 1 + 3) / 4 * 4;
     return strips * cols;
 }
@@ -45,12 +45,12 @@ struct Costs {
     double operator()(int lg, int32_t id) const { return at[lg][(size_t)id]; }
 };
 
-Costs compute_costs(const std::vector<PlanPair> &pairs) {
+Costs compute_costs(const std::vector<PlanPair> &pairs, int rows) {
     Costs c;
     for (int lg = kMinLog2G; lg <= 5; ++lg) {
         c.at[lg].resize(pairs.size());
         for (size_t i = 0; i < pairs.size(); ++i)
-            c.at[lg][i] = 1.25 * (double)sweep_steps(pairs[i].n, pairs[i].m, 1 << lg);
+            c.at[lg][i] = 1.25 * (double)sweep_steps(pairs[i].n, pairs[i].m, 1 << lg, rows);
     }
     return c;
 }
@@ -125,7 +125,7 @@ double simulate(const Costs &cost, const std::vector<PlannedClass> &cls, int n_w
 // Classes of candidate (Gn = 2^gn, cap = frac x mean load per group) with
 // warp shares in proportion to class work; pairs within a class unsorted.
 std::vector<PlannedClass> build(const std::vector<PlanPair> &pairs, const Costs &cost,
-                                int n_warps, int gn, double frac, bool half_tails) {
+                                int n_warps, int gn, double frac, bool half_tails, int rows) {
     double total = 0;
     for (const auto &p : pairs) total += cost(gn, p.id);
     const double groups = (double)n_warps * (32 >> gn);
@@ -141,7 +141,7 @@ std::vector<PlannedClass> build(const std::vector<PlanPair> &pairs, const Costs 
         // a bulk pair whose last strip would be at most half used takes
         // half-width groups: same strips' worth of rows or fewer, less padding
         if (half_tails && lg == gn && gn > kMinLog2G) {
-            const int64_t h = (int64_t)kRows << gn;
+            const int64_t h = (int64_t)rows << gn;
             if ((p.n + h / 2 - 1) / (h / 2) * (h / 2) < (p.n + h - 1) / h * h) lg = gn - 1;
         }
         by[lg].push_back(p.id);
@@ -186,13 +186,13 @@ void sort_classes(std::vector<PlannedClass> &cls, const Costs &cost) {
 
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
                                        int narrow_log2g_hint, double cap_fraction_hint,
-                                       int sample_cap, bool half_tails) {
+                                       int sample_cap, bool half_tails, int rows) {
     if (pairs.empty()) return {};
     n_warps = std::max(1, n_warps);
-    const Costs cost = compute_costs(pairs);
+    const Costs cost = compute_costs(pairs, rows);
     if (narrow_log2g_hint >= 0) {
         auto cls = build(pairs, cost, n_warps, std::max(narrow_log2g_hint, kMinLog2G),
-                         cap_fraction_hint, half_tails);
+                         cap_fraction_hint, half_tails, rows);
         sort_classes(cls, cost);
         return cls;
     }
@@ -207,7 +207,7 @@ std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n
     for (int gn = kMinLog2G; gn <= 3; ++gn) {
         for (double frac : {0.25, 0.5, 1.0}) {
             Candidate c;
-            c.classes = build(pairs, cost, n_warps, gn, frac, half_tails);
+            c.classes = build(pairs, cost, n_warps, gn, frac, half_tails, rows);
             c.makespan = simulate(cost, c.classes, n_warps, sampled, scale);
             if (!have || c.makespan < best.makespan) {
                 best = std::move(c);

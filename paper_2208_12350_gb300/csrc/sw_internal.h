@@ -138,12 +138,20 @@ struct PlannedClass {
 };
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
                                        int narrow_log2g_hint, double cap_fraction_hint,
-                                       int sample_cap = 8192, bool half_tails = false);
-int64_t sweep_steps(int n, int m, int G);
+                                       int sample_cap = 8192, bool half_tails = false,
+                                       int rows = kRows);
+int64_t sweep_steps(int n, int m, int G, int rows = kRows);
 
 // Arithmetic and profile element width of the group kernel: scaled int32
 // with an int32 or int8 profile, or two 16-bit cells per 32-bit word.
 enum class ProfileKind : int { kInt32 = 0, kInt8 = 1, kPacked16 = 2 };
+
+// Rows per lane of the packed form (16: 8 words, 32: 16 words).
+#ifndef SWGB_PACKED_ROWS
+#define SWGB_PACKED_ROWS 16
+#endif
+constexpr int kRowsPacked = SWGB_PACKED_ROWS;
+inline int rows_of(ProfileKind k) { return k == ProfileKind::kPacked16 ? kRowsPacked : kRows; }
 
 // Whether a pair fits the packed 16-bit form: every value 8 x (score terms)
 // stays in a signed 16-bit half, profile scores s - go are non-negative.

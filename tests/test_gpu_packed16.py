@@ -133,15 +133,31 @@ def test_linear_gaps_packed(gpu_lib, ctx):
             both_forms(gpu_lib, ctx, b, expect, f"linear {g}", tuning)
 
 
-def test_protein_short_pairs_packed(gpu_lib, ctx):
-    """BLOSUM62 (-11/-1) pairs with min(n, m) <= 300 fit the packed bound."""
+def test_protein_short_pairs_and_larger_alphabets(gpu_lib, ctx):
+    """BLOSUM62 (-11/-1) pairs with min(n, m) <= 300 fit the packed bound, but
+    the packed profile of 21 residue codes leaves fewer than two blocks per
+    SM, so the plan keeps the int32 form; an 8-letter alphabet with small
+    scores takes the packed form where its profile fits two blocks per SM.
+    Both exact either way."""
     src = wl.gen_config(2, n_pairs=400)
     qs = [src.pair(i)[0][:300] for i in range(src.n_pairs)]
     rs = [src.pair(i)[1] for i in range(src.n_pairs)]
     b = wl.make_batch("protein-short", qs, rs, src.matrix, src.gap_open, src.gap_extend)
     expect = oracle.align_workload(b)
     for tuning in ((2, 1e9), (5, 1e9), (-1, 0.5)):
-        both_forms(gpu_lib, ctx, b, expect, f"protein short {tuning}", tuning)
+        got, info = run_lib(gpu_lib, ctx, b, tuning=tuning)
+        assert_same(got, expect, f"protein short {tuning} ({info['arith']})")
+    rng = np.random.default_rng(61)
+    mat = rng.integers(-3, 5, size=(8, 8)).astype(np.int8)
+    np.fill_diagonal(mat, 6)
+    qs8 = [rng.integers(0, 8, int(rng.integers(1, 300))).astype(np.uint8) for _ in range(300)]
+    rs8 = [rng.integers(0, 8, int(rng.integers(1, 700))).astype(np.uint8) for _ in range(300)]
+    b8 = wl.make_batch("alphabet-8", qs8, rs8, mat, -5, -2)
+    expect8 = oracle.align_workload(b8)
+    _, info8 = run_lib(gpu_lib, ctx, b8)
+    for tuning in ((1, 1e9), (3, 1e9), (-1, 0.5)):
+        both_forms(gpu_lib, ctx, b8, expect8, f"alphabet 8 {tuning}", tuning,
+                   want_packed=info8["arith"] == "s16x2")
 
 
 @pytest.mark.parametrize("k", [1, 3])
