@@ -173,3 +173,28 @@ def test_full_workloads_packed_vs_int32(gpu_lib, ctx, k):
     assert_same(got, got32, f"config{k} packed vs int32")
     idx = np.random.default_rng(k).choice(b.n_pairs, 2000, replace=False)
     assert_same(got[idx], oracle.align_workload(b, idx=idx), f"config{k} sample")
+
+
+def test_out_of_range_residues_clamped(gpu_lib, ctx):
+    """Residue codes at or above the alphabet size are clamped to
+    alphabet_size - 1 on the device (the documented unchecked behaviour):
+    every form equals the oracle on the clamped sequences."""
+    rng = np.random.default_rng(67)
+    qs, rs = [], []
+    for _ in range(300):
+        q = rng.integers(0, 4, int(rng.integers(1, 260))).astype(np.uint8)
+        r = rng.integers(0, 4, int(rng.integers(1, 700))).astype(np.uint8)
+        k = min(len(q), len(r))
+        if rng.random() < 0.5:
+            r[:k] = q[:k]
+        q[rng.random(len(q)) < 0.1] = rng.integers(4, 256)
+        r[rng.random(len(r)) < 0.1] = rng.integers(4, 256)
+        qs.append(q)
+        rs.append(r)
+    raw = wl.make_batch("raw-codes", qs, rs, wl.dna_matrix(), -6, -1)
+    clamped = wl.make_batch("clamped", [np.minimum(q, 3) for q in qs],
+                            [np.minimum(r, 3) for r in rs], wl.dna_matrix(), -6, -1)
+    expect = oracle.align_workload(clamped)
+    both_forms(gpu_lib, ctx, raw, expect, "raw codes", (2, 1e9))
+    got, _ = run_lib(gpu_lib, ctx, raw, mode=gpu_lib.SW_MODE_PLAIN)
+    assert_same(got, expect, "raw codes, plain")
