@@ -382,8 +382,7 @@ int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int
 
 int sw_plan_arith(const sw_plan *p, int32_t *arith) {
     if (!p || !arith) return fail(SW_EINVAL, "sw_plan_arith: NULL argument");
-    *arith = (!p->hp.pairs.empty() && p->hp.kind == ProfileKind::kPacked16) ? SW_ARITH_S16X2
-                                                                           : SW_ARITH_S32;
+    *arith = (!p->hp.pairs.empty() && is_packed(p->hp.kind)) ? SW_ARITH_S16X2 : SW_ARITH_S32;
     return SW_OK;
 }
 

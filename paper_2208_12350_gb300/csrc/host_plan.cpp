@@ -95,19 +95,27 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
 #endif
     // The packed 16-bit form takes the batch when every pair of the batched
     // path fits its bound (one kernel per batch).
-    bool packed = allow_packed && SWGB_PACKED16 && mode != SW_MODE_PLAIN && n_pairs > 0;
-    for (int32_t i = 0; i < n_pairs && packed; ++i)
-        if (group_path_eligible(n[i], m[i], smax, go, ge))
-            packed = packed_eligible(n[i], m[i], smax, smin, go, ge);
-    // its profile holds 32-bit words; with large alphabets fewer than two
-    // blocks fit on an SM, and the int32 form's int8 profile runs faster
-    if (packed) {
-        const int b = group_blocks_per_sm(ProfileKind::kPacked16, go == ge, A, nullptr);
+    // Its profile of 32-bit words needs 4 bytes per row and residue code:
+    // with large alphabets fewer than two blocks fit on an SM, and the byte
+    // profile (scores scaled by 4) takes over where its bound holds.
+    const bool try_packed = allow_packed && SWGB_PACKED16 && mode != SW_MODE_PLAIN && n_pairs > 0;
+    bool packed8 = try_packed, packed4 = try_packed;
+    for (int32_t i = 0; i < n_pairs && (packed8 || packed4); ++i)
+        if (group_path_eligible(n[i], m[i], smax, go, ge)) {
+            packed8 = packed8 && packed_eligible(n[i], m[i], smax, smin, go, ge, 8);
+            packed4 = packed4 && packed_eligible(n[i], m[i], smax, smin, go, ge, 4);
+        }
+    for (ProfileKind k : {ProfileKind::kPacked16, ProfileKind::kPacked16Bytes}) {
+        bool &ok = k == ProfileKind::kPacked16 ? packed8 : packed4;
+        if (!ok) continue;
+        const int b = group_blocks_per_sm(k, go == ge, A, nullptr);
         if (b < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
-        packed = b >= 2;
+        ok = b >= 2;
     }
-    if (packed)
+    if (packed8)
         out->kind = ProfileKind::kPacked16;
+    else if (packed4)
+        out->kind = ProfileKind::kPacked16Bytes;
     else if (A <= 4 && SWGB_SMALL_ALPHABET_INT32)
         out->kind = ProfileKind::kInt32;
     else if (smax - go <= 127 && smin - go >= -127)

@@ -165,6 +165,14 @@ __device__ __forceinline__ int byte_hi(uint32_t w) {
     return (int)d;
 }
 
+// prmt.b32 with its sign-replicating selectors (bit 3 of a nibble copies the
+// top bit of the selected byte into every bit of the result byte).
+__device__ __forceinline__ uint32_t prmt_sx(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
 // Scaled substitution tables, filled once per block: entry x * (A + 1) + c
 // is the profile value of row residue x against column residue c, that is
 // (s - go) << 16 (int32 profile) or s - go (int8 profile), and entry
@@ -215,10 +223,12 @@ __device__ __forceinline__ void build_profile_group(char *prof, int lane, int gb
         }
         for (int c = 0; c <= A; ++c) {
             if constexpr (P8) {
+                // (packed form with a byte profile: 4 (s - go) in [0, 127], 0
+                // past the end)
                 uint32_t w = 0u;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int v = base[j] >= 0 ? (int)tab[base[j] + c] : -128;
+                    const int v = base[j] >= 0 ? (int)tab[base[j] + c] : (PK ? 0 : -128);
                     w |= (uint32_t)(uint8_t)(int8_t)v << (8 * j);
                 }
                 if constexpr (R == 8)
@@ -337,20 +347,27 @@ constexpr int kColdWords = 2 * 2 + 11;  // 32-bit words per lane
 template <int R, bool P8, bool LIN, bool PK>
 __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupMinBlocks)
     sw_group_kernel(const __grid_constant__ GroupParams p) {
-    static_assert(!PK || (!P8 && R % 16 == 0), "the packed form holds 16 rows per 8 words");
+    static_assert(!PK || R % 16 == 0, "the packed form holds 16 rows per 8 words");
+    static_assert(!(PK && P8) || R == 16, "the packed byte profile holds 16 rows per lane");
     extern __shared__ __align__(16) char smem_group[];
     constexpr int kHalves = halves_of<P8, PK>();
-    constexpr int W = R / 2;   // packed words per lane
-    constexpr int NC = W / 8;  // end-key chains (3-bit row codes, 8 words each)
+    constexpr int W = R / 2;  // packed words per lane
+    // packed form: scores scaled by SC, leaving CB low bits for the row code
+    // of an end-key chain of CL words (32-bit profile words: 8 / 3 / 8; byte
+    // profile: 4 / 2 / 4, so that 4 (s - go) fits a byte)
+    constexpr int SC = P8 ? 4 : 8;
+    constexpr int CB = P8 ? 2 : 3;
+    constexpr int CL = 1 << CB;
+    constexpr int NC = W / CL;  // end-key chains
     constexpr int kU = unroll_of<P8, PK>();
     constexpr int kAhead = ahead_of<P8, PK>();
     static_assert(kU == 4 || kU == 8, "blocks move whole 16-byte chunks of 4 boundary columns");
     const int A = p.alphabet;
     const int go = p.gap_open, ge = p.gap_extend;
     const int goS = go * 65536, geS = ge * 65536;
-    // packed form: 8 ge and 8 go in both halves
-    const uint32_t geP = ((uint32_t)(8 * ge) & 0xFFFFu) * 0x10001u;
-    const uint32_t goP = ((uint32_t)(8 * go) & 0xFFFFu) * 0x10001u;
+    // packed form: SC ge and SC go in both halves
+    const uint32_t geP = ((uint32_t)(SC * ge) & 0xFFFFu) * 0x10001u;
+    const uint32_t goP = ((uint32_t)(SC * go) & 0xFFFFu) * 0x10001u;
     // boundary word of "no row above": H = 0 (stored as H + go) and F = -inf
     // (0xC000 = -16384 in the high half, -2^30 scaled); packed form: H = 0 and
     // F = go (F - go = 0), which gives the row below the same values
@@ -389,8 +406,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
         } else {
             // the plan takes the int8 profile only when s - go fits in int8
             const int vf = (int)p.mat[x * A + c] - go, vr = (int)p.mat[c * A + x] - go;
-            tab_fwd[i] = (TabT<P8>)(PK ? 8 * vf : P8 ? vf : vf * 65536);
-            tab_rev[i] = (TabT<P8>)(PK ? 8 * vr : P8 ? vr : vr * 65536);
+            tab_fwd[i] = (TabT<P8>)(PK ? SC * vf : P8 ? vf : vf * 65536);
+            tab_rev[i] = (TabT<P8>)(PK ? SC * vr : P8 ? vr : vr * 65536);
         }
     }
     __syncthreads();
@@ -433,9 +450,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
         // half: column << 16 | 8 score + row code)
         uint32_t Hw[W], Ew[W];
         uint32_t outHw = 0u, outFw = 0u, diag0w = 0u;
-        uint32_t Tw[NC], rec_lo[NC], rec_hi[NC], tmask = 0x00070007u;
+        uint32_t Tw[NC], rec_lo[NC], rec_hi[NC], tmask = (CL - 1) * 0x10001u;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) Tw[c] = 0x00070007u, rec_lo[c] = rec_hi[c] = 0u;
+        for (int c = 0; c < NC; ++c) Tw[c] = (CL - 1) * 0x10001u, rec_lo[c] = rec_hi[c] = 0u;
         int s = 0, lim = 0, stop = 0, dir = 1;
         const uint8_t *bcol = p.r;  // column 0 of the current sweep
         int roff = 0;               // bcol's offset in its 16-byte chunk (mirrored if dir < 0)
@@ -512,8 +529,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                 outHw = outFw = diag0w = 0u;
                 // forward: best score 0 with the largest row code; reverse:
                 // just below the score S with any row code
-                const uint32_t t0 = rev ? (uint32_t)(8 * cold.target[t] - 1) : 7u;
-                tmask = rev ? 0u : 0x00070007u;
+                const uint32_t t0 = rev ? (uint32_t)(SC * cold.target[t] - 1) : (uint32_t)(CL - 1);
+                tmask = rev ? 0u : (CL - 1) * 0x10001u;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     Tw[c] = (t0 & 0xFFFFu) * 0x10001u;
@@ -664,8 +681,27 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
 #if SWGB_STEP_ORDER_FENCE
                     asm volatile("" : "+r"(c0), "+r"(c1) : "r"(inH));
 #endif
-                    int sc[R];
-                    load_scores_halves<R, false, 2>(prof, c0, c1, lane, sc);
+                    // s' of word k: 32-bit profile, the sum of a low-half word
+                    // (row k, column j0) and a high-half word (row R/2 + k,
+                    // column j1); byte profile, the two rows' bytes moved to
+                    // the halves (zero-extended: every byte is below 128)
+                    uint32_t scw[W];
+                    if constexpr (P8) {
+                        const uint2 b0 = *reinterpret_cast<const uint2 *>(
+                            prof + ((size_t)c0 * 32 + lane) * 16);
+                        const uint2 b1 = *reinterpret_cast<const uint2 *>(
+                            prof + ((size_t)c1 * 32 + lane) * 16 + 8);
+#pragma unroll
+                        for (int k = 0; k < W; ++k) {
+                            constexpr unsigned kSel[4] = {0xC480u, 0xD591u, 0xE6A2u, 0xF7B3u};
+                            scw[k] = prmt_sx(k < 4 ? b0.x : b0.y, k < 4 ? b1.x : b1.y, kSel[k & 3]);
+                        }
+                    } else {
+                        int sc[R];
+                        load_scores_halves<R, false, 2>(prof, c0, c1, lane, sc);
+#pragma unroll
+                        for (int k = 0; k < W; ++k) scw[k] = (uint32_t)sc[k] + (uint32_t)sc[W + k];
+                    }
                     uint32_t diag = diag0w;
                     uint32_t F = LIN ? 0u : __viaddmax_s16x2(upF, geP, upH);
                     uint32_t hprev = upH;
@@ -675,7 +711,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         // carry-free: both halves of every term are non-negative
-                        const uint32_t D = diag + (uint32_t)sc[k] + (uint32_t)sc[W + k];
+                        const uint32_t D = diag + scw[k];
                         uint32_t V;
                         if constexpr (LIN) {
                             // go == ge: E - go = H_left and F - go = H_up exactly
@@ -689,7 +725,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                         diag = Hw[k];
                         Hw[k] = h;
                         hprev = h;
-                        acc[k / 8] = __viaddmax_s16x2(h, (uint32_t)(7 - k % 8) * 0x10001u, acc[k / 8]);
+                        acc[k / CL] = __viaddmax_s16x2(h, (uint32_t)(CL - 1 - k % CL) * 0x10001u,
+                                                       acc[k / CL]);
                     }
                     outHw = hprev;
                     outFw = F;
@@ -826,9 +863,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                                 const int val = (int)(rec & 0xFFFFu);
                                 const int col = min((int)(rec >> 16) - 2 * gl - hh, kColBase);
                                 const uint32_t key =
-                                    ((uint32_t)(val >> 3) << 16) | (uint32_t)(kColBase - col);
-                                const int row = row0 + hh * W + 8 * c + 7 - (val & 7);
-                                if ((val >> 3) > 0 && key > best_key) {
+                                    ((uint32_t)(val >> CB) << 16) | (uint32_t)(kColBase - col);
+                                const int row = row0 + hh * W + CL * c + (CL - 1) - (val & (CL - 1));
+                                if ((val >> CB) > 0 && key > best_key) {
                                     best_key = key;
                                     best_row = row;
                                 }
@@ -854,8 +891,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                             const int hh = q / NC, c = q % NC;
                             const uint32_t rec = hh ? rec_hi[c] : rec_lo[c];
                             const int val = (int)(rec & 0xFFFFu);
-                            if ((val >> 3) >= target) {
-                                frow = row0 + hh * W + 8 * c + 7 - (val & 7);
+                            if ((val >> CB) >= target) {
+                                frow = row0 + hh * W + CL * c + (CL - 1) - (val & (CL - 1));
                                 fcol = (int)(rec >> 16) - 2 * gl - hh;
                             }
                         }
@@ -953,11 +990,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
 
 size_t group_smem_bytes(ProfileKind kind, int alphabet) {
     const size_t rows = (size_t)rows_of(kind);
-    const size_t per_warp = kind == ProfileKind::kInt8
-                                ? (size_t)(alphabet + 1) * 32 * rows
-                                : (size_t)(alphabet + 1) * (rows / 4) * 32 * 16;
-    return (size_t)kGroupWarps * 3 * kMaxGroups * kRingBytes +
-           tab_bytes(kind == ProfileKind::kInt8, alphabet) +
+    const bool bytes = kind == ProfileKind::kInt8 || kind == ProfileKind::kPacked16Bytes;
+    const size_t per_warp = bytes ? (size_t)(alphabet + 1) * 32 * rows
+                                  : (size_t)(alphabet + 1) * (rows / 4) * 32 * 16;
+    return (size_t)kGroupWarps * 3 * kMaxGroups * kRingBytes + tab_bytes(bytes, alphabet) +
            (size_t)kColdWords * 4 * kGroupWarps * 32 + kGroupWarps * per_warp;
 }
 
@@ -967,7 +1003,7 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
 // under a launch that needs more.  Occupancy per (profile, alphabet) is
 // cached per device.
 namespace {
-// the six instantiations, indexed by (profile kind, linear gaps)
+// the eight instantiations, indexed by (profile kind, linear gaps)
 using GroupKernel = void (*)(GroupParams);
 GroupKernel group_kernel_of(ProfileKind kind, bool lin) {
     switch (kind) {
@@ -977,6 +1013,9 @@ GroupKernel group_kernel_of(ProfileKind kind, bool lin) {
         case ProfileKind::kPacked16:
             return lin ? sw_group_kernel<kRowsPacked, false, true, true>
                        : sw_group_kernel<kRowsPacked, false, false, true>;
+        case ProfileKind::kPacked16Bytes:
+            return lin ? sw_group_kernel<kRows, true, true, true>
+                       : sw_group_kernel<kRows, true, false, true>;
         default:
             return lin ? sw_group_kernel<kRows, false, true, false>
                        : sw_group_kernel<kRows, false, false, false>;
@@ -990,8 +1029,8 @@ int group_blocks_per_sm(ProfileKind kind, bool linear, int alphabet, int *smem_b
     if (alphabet < 1 || alphabet > kMaxAlphabet) return -1;
     constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static int cache[kMaxDevices][6][kMaxAlphabet + 1];
-    static bool raised[kMaxDevices][6];
+    static int cache[kMaxDevices][8][kMaxAlphabet + 1];
+    static bool raised[kMaxDevices][8];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
     const int ki = 2 * (int)kind + (linear ? 1 : 0);

@@ -144,7 +144,12 @@ int64_t sweep_steps(int n, int m, int G, int rows = kRows);
 
 // Arithmetic and profile element width of the group kernel: scaled int32
 // with an int32 or int8 profile, or two 16-bit cells per 32-bit word.
-enum class ProfileKind : int { kInt32 = 0, kInt8 = 1, kPacked16 = 2 };
+// The packed form comes with a profile of 32-bit words (scores scaled by 8)
+// or, for larger alphabets, of bytes (scaled by 4).
+enum class ProfileKind : int { kInt32 = 0, kInt8 = 1, kPacked16 = 2, kPacked16Bytes = 3 };
+inline bool is_packed(ProfileKind k) {
+    return k == ProfileKind::kPacked16 || k == ProfileKind::kPacked16Bytes;
+}
 
 // Rows per lane of the packed form (16: 8 words, 32: 16 words).
 #ifndef SWGB_PACKED_ROWS
@@ -153,13 +158,17 @@ enum class ProfileKind : int { kInt32 = 0, kInt8 = 1, kPacked16 = 2 };
 constexpr int kRowsPacked = SWGB_PACKED_ROWS;
 inline int rows_of(ProfileKind k) { return k == ProfileKind::kPacked16 ? kRowsPacked : kRows; }
 
-// Whether a pair fits the packed 16-bit form: every value 8 x (score terms)
-// stays in a signed 16-bit half, profile scores s - go are non-negative.
-inline bool packed_eligible(int n, int m, int smax, int smin, int gap_open, int gap_extend) {
-    if (smin < gap_open || 8 * (int64_t)(-gap_extend) > 16384) return false;
+// Whether a pair fits the packed 16-bit form with scores scaled by `scale`
+// (8 or 4): every value scale x (score terms) stays in a signed 16-bit
+// half and profile scores s - go are non-negative (with a byte profile,
+// scale 4, also at most 31, so that 4 (s - go) fits a byte below 128).
+inline bool packed_eligible(int n, int m, int smax, int smin, int gap_open, int gap_extend,
+                            int scale = 8) {
+    if (smin < gap_open || scale * (int64_t)(-gap_extend) > 16384) return false;
+    if (scale == 4 && (int64_t)smax - gap_open > 31) return false;
     const int64_t bound = (int64_t)(smax > 0 ? smax : 0) * (n < m ? n : m) +
                           (smax > 0 ? smax : 0) - gap_open;
-    return 8 * bound <= 32767;
+    return scale * bound <= 32767;
 }
 
 // A batch planned on the host (host_plan.cpp): the device tables to upload

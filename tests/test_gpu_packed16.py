@@ -35,16 +35,23 @@ def both_forms(gpu_lib, ctx, b, expect, name, tuning=None, want_packed=True):
 
 
 def test_form_selection(gpu_lib, ctx):
-    """DNA workloads fit the packed bound; full-length protein pairs
-    (11 x 400 + 22 > 4095) and scoring with a mismatch below gap_open do not."""
+    """DNA workloads fit the packed bound (32-bit profile words, scale 8);
+    protein pairs take the byte profile (scale 4: 4 (11 x 400 + 22) <= 32767,
+    s - go <= 22 < 32); a gap_open of -40 (s - go up to 51) or a mismatch
+    below gap_open keeps the int32 form."""
     b0 = wl.gen_config(0, n_pairs=50)
     _, info = run_lib(gpu_lib, ctx, b0)
     assert info["arith"] == "s16x2"
     _, info = run_lib(gpu_lib, ctx, b0, flags=gpu_lib.SW_PLAN_NO_S16X2)
     assert info["arith"] == "s32"
-    b2 = wl.gen_config(2)
-    _, info = run_lib(gpu_lib, ctx, b2.slice(0, 2000))
+    b2 = wl.gen_config(2).slice(0, 2000)
+    _, info = run_lib(gpu_lib, ctx, b2)
+    assert info["arith"] == "s16x2"
+    b2w = wl.make_batch("protein-go40", [b2.pair(i)[0] for i in range(200)],
+                        [b2.pair(i)[1] for i in range(200)], b2.matrix, -40, -1)
+    got, info = run_lib(gpu_lib, ctx, b2w)
     assert info["arith"] == "s32"
+    assert_same(got, oracle.align_workload(b2w), "protein go -40")
     fig2 = wl.make_batch("fig2", [b0.pair(i)[0] for i in range(b0.n_pairs)],
                          [b0.pair(i)[1] for i in range(b0.n_pairs)], wl.dna_matrix(2, -2), -1, -1)
     _, info = run_lib(gpu_lib, ctx, fig2)
@@ -103,11 +110,12 @@ def test_hand_worked_examples(gpu_lib, ctx):
 
 @pytest.mark.parametrize("lg", [1, 3])
 def test_packed_bound_edges(gpu_lib, ctx, lg):
-    """8 (3 min(n, m) + 3 + 6) <= 32767 holds up to min(n, m) = 1362: a
-    self-alignment there scores 4086 (scaled 32688) in the packed form; one
-    residue more and the plan keeps int32.  Both exact."""
+    """With 32-bit profile words (scale 8) the bound 8 (3 min(n, m) + 3 + 6)
+    <= 32767 holds up to min(n, m) = 1362; from 1363 the byte profile (scale
+    4) takes over, up to 2727 (a self-alignment there scores 8181, scaled
+    32724); at 2728 the plan keeps int32.  Exact on every side."""
     rng = np.random.default_rng(53 + lg)
-    for L, packed in ((1362, True), (1363, False)):
+    for L, packed in ((1362, True), (1363, True), (2727, True), (2728, False)):
         qs, rs = [], []
         for extra in (0, 5, 700):
             q = rng.integers(0, 4, L).astype(np.uint8)
@@ -134,19 +142,19 @@ def test_linear_gaps_packed(gpu_lib, ctx):
 
 
 def test_protein_short_pairs_and_larger_alphabets(gpu_lib, ctx):
-    """BLOSUM62 (-11/-1) pairs with min(n, m) <= 300 fit the packed bound, but
-    the packed profile of 21 residue codes leaves fewer than two blocks per
-    SM, so the plan keeps the int32 form; an 8-letter alphabet with small
-    scores takes the packed form where its profile fits two blocks per SM.
-    Both exact either way."""
+    """BLOSUM62 (-11/-1) pairs take the packed form with the byte profile (a
+    profile of 32-bit words for 21 residue codes leaves fewer than two blocks
+    per SM); an 8-letter alphabet with small scores takes the 32-bit words.
+    Both forms exact on both."""
     src = wl.gen_config(2, n_pairs=400)
     qs = [src.pair(i)[0][:300] for i in range(src.n_pairs)]
     rs = [src.pair(i)[1] for i in range(src.n_pairs)]
     b = wl.make_batch("protein-short", qs, rs, src.matrix, src.gap_open, src.gap_extend)
     expect = oracle.align_workload(b)
-    for tuning in ((2, 1e9), (5, 1e9), (-1, 0.5)):
-        got, info = run_lib(gpu_lib, ctx, b, tuning=tuning)
-        assert_same(got, expect, f"protein short {tuning} ({info['arith']})")
+    for tuning in ((1, 1e9), (2, 1e9), (5, 1e9), (-1, 0.5)):
+        both_forms(gpu_lib, ctx, b, expect, f"protein short {tuning}", tuning)
+    lin = wl.make_batch("protein-linear", qs, rs, src.matrix, -6, -6)
+    both_forms(gpu_lib, ctx, lin, oracle.align_workload(lin), "protein linear -6", (3, 1e9))
     rng = np.random.default_rng(61)
     mat = rng.integers(-3, 5, size=(8, 8)).astype(np.int8)
     np.fill_diagonal(mat, 6)
@@ -160,18 +168,18 @@ def test_protein_short_pairs_and_larger_alphabets(gpu_lib, ctx):
                    want_packed=info8["arith"] == "s16x2")
 
 
-@pytest.mark.parametrize("k", [1, 3])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_full_workloads_packed_vs_int32(gpu_lib, ctx, k):
-    """The 100k- and 200k-pair DNA workloads in the benchmark's launch form:
-    the packed form equals the int32 form on every pair and the oracle on a
-    sample."""
+    """The 100k- and 200k-pair DNA and the 20k-pair protein workloads in the
+    benchmark's launch form: the packed form equals the int32 form on every
+    pair and the oracle on a sample."""
     b = wl.gen_config(k)
     got, info = run_lib(gpu_lib, ctx, b, flags=gpu_lib.SW_PLAN_GRAPH)
     assert info["arith"] == "s16x2"
     got32, info32 = run_lib(gpu_lib, ctx, b, flags=gpu_lib.SW_PLAN_GRAPH | gpu_lib.SW_PLAN_NO_S16X2)
     assert info32["arith"] == "s32"
     assert_same(got, got32, f"config{k} packed vs int32")
-    idx = np.random.default_rng(k).choice(b.n_pairs, 2000, replace=False)
+    idx = np.random.default_rng(k).choice(b.n_pairs, min(2000, b.n_pairs), replace=False)
     assert_same(got[idx], oracle.align_workload(b, idx=idx), f"config{k} sample")
 
 
