@@ -10,12 +10,13 @@
 // The planner therefore keeps a narrow width Gn for the bulk and sends each
 // pair whose sweep under Gn exceeds a cap (a fraction of the mean load per
 // group) to the narrowest wider class that fits.  With half_tails (the
-// packed form) each bulk pair whose last strip under Gn would be at most
+// packed form with 32-bit profile words) each bulk pair whose last strip under Gn would be at most
 // half used (n mod Gn R in (0, Gn R / 2]) goes to Gn / 2, which computes
 // fewer padded rows for more strips: measured +1.5 % and +2.3 % on 100k and
 // 200k DNA pairs (the autotuner then preferring Gn = 8 over 4), but -23 % on
-// 20k protein pairs in the int32 form, whose strips cost more (a profile of
-// 21 residue codes per strip).  Warps start on classes in
+// 20k protein pairs in the int32 form and -28 % in the packed form with the
+// byte profile, so the plan asks for it with 32-bit profile words only.
+// Warps start on classes in
 // proportion to class work and then walk the classes cyclically.  Among a
 // few (Gn, cap) candidates the planner keeps the one whose simulated
 // longest-first schedule (each group taking the next pair when free)
