@@ -92,10 +92,12 @@ typedef enum {
 #define SW_PLAN_PACKED_2BIT 4u
 /* Keep the batched kernel on scaled int32 arithmetic.  Without this flag
  * the plan runs the batched kernel in packed 16-bit form (two DP cells per
- * 32-bit word, every value scaled by 8) when every pair of the batched path
- * satisfies 8 x (smax x min(n, m) + smax - gap_open) <= 32767, the smallest
- * matrix entry is >= gap_open and 8 x |gap_extend| <= 16384; the results
- * are the same either way (sw_plan_arith says which form a plan took). */
+ * 32-bit word, every value scaled by k) when every pair of the batched path
+ * satisfies k x (smax x min(n, m) + smax - gap_open) <= 32767, the smallest
+ * matrix entry is >= gap_open and k x |gap_extend| <= 16384, with k = 8
+ * (small alphabets, whose profile of 32-bit words leaves two blocks per SM)
+ * or k = 4 (a byte profile; also smax - gap_open <= 31); the results are
+ * the same either way (sw_plan_arith says which form a plan took). */
 #define SW_PLAN_NO_S16X2 8u
 
 typedef struct sw_ctx sw_ctx;

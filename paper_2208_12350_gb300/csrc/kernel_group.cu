@@ -84,6 +84,11 @@
 // with a smaller (column, row) pair, so its record never wins.  The plan
 // takes this form only when 8 (smax min(n, m) + smax - go) <= 32767,
 // smin >= go and 8 |ge| <= 16384, which keeps every value in 16 bits.
+// Large alphabets (protein) use a byte profile instead (P8 with PK): s' =
+// 4 (s - go) < 128 per byte, scores scaled by 4, 2-bit row codes in chains
+// of 4 words, and one sign-replicating byte permute per word that moves the
+// two rows' bytes into the halves (bound 4 (smax min(n, m) + smax - go) <=
+// 32767, smax - go <= 31).
 //
 // Reverse pass (Fig. 2(c)): the same sweep over the reversed prefixes
 // a_qend..a_0 and b_rend..b_0, transposed: the reversed reference prefix
