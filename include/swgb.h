@@ -193,6 +193,27 @@ int sw_plan_arith(const sw_plan *plan, int32_t *arith);
 int sw_plan_destroy(sw_plan *plan);
 
 /*
+ * Host-only preview of how sw_plan_create would plan a batch (no CUDA call,
+ * no allocation; for inspection and tests on machines without a GPU).
+ * Arguments as sw_plan_create (offsets and matrix on the HOST), plus the SM
+ * count of the device to plan for and the tuning (as sw_ctx_set_tuning);
+ * the group kernel's occupancy is estimated from its shared memory (228 KB
+ * per SM, 1 KB reserved per block) and its register bound (3 blocks).
+ * Outputs: *out_kind = the batched kernel's form: 0 = int32 with an int32
+ * profile, 1 = int32 with an int8 profile, 2 = packed 16-bit with a profile
+ * of 32-bit words, 3 = packed 16-bit with a byte profile; pair_log2g[i] =
+ * log2 of the lane-group width pair i is aligned with, or -1 for the
+ * one-block-per-pair kernel; pair_rank[i] = its position in that kernel's
+ * queue (group pairs: in its width class, longest first).
+ * Errors: as sw_plan_create; SW_EINVAL for bad tuning or NULL outputs.
+ */
+int sw_plan_preview(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
+                    const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                    int32_t gap_extend, int32_t mode, uint32_t flags, int32_t sm_count,
+                    int32_t narrow_log2g, double cap_fraction, int32_t *out_kind,
+                    int32_t *pair_log2g, int32_t *pair_rank);
+
+/*
  * Measured tuning of the batched path for a batch (blocking).  Runs the
  * batch - offsets and score_matrix on the HOST as for sw_plan_create,
  * q_seqs/r_seqs on the DEVICE, `out` a DEVICE scratch array of 5 x n_pairs

@@ -46,6 +46,8 @@ SIGNATURES = {
     "sw_plan_info": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                       ctypes.POINTER(_I64)], ctypes.c_int),
     "sw_plan_arith": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_plan_preview": ([_P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _I32, _I32,
+                         ctypes.c_double, ctypes.POINTER(_I32), _P, _P], ctypes.c_int),
     "sw_plan_destroy": ([_P], ctypes.c_int),
     "sw_align_batch": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
                        ctypes.c_int),
@@ -205,6 +207,28 @@ def sw_plan_info(plan: int) -> dict:
     _check(load().sw_plan_arith(plan, ctypes.byref(ar)), "sw_plan_arith")
     return {"group_pairs": t.value, "plain_pairs": p.value, "launches": l.value,
             "scratch_bytes": sb.value, "arith": "s16x2" if ar.value == SW_ARITH_S16X2 else "s32"}
+
+
+PLAN_KINDS = {0: "int32", 1: "int32-int8-profile", 2: "s16x2", 3: "s16x2-byte-profile"}
+
+
+def sw_plan_preview(q_offsets, r_offsets, score_matrix, gap_open: int, gap_extend: int,
+                    mode: int = SW_MODE_AUTO, flags: int = 0, sm_count: int = 152,
+                    narrow_log2g: int = -1, cap_fraction: float = 0.5):
+    """Host-only preview of a plan: (kind name, per-pair lane-group log2 width
+    (-1 = plain kernel), per-pair queue position).  No GPU needed."""
+    q_offsets = _host_i64(q_offsets)
+    r_offsets = _host_i64(r_offsets)
+    n = len(q_offsets) - 1
+    mat = np.ascontiguousarray(score_matrix, dtype=np.int8)
+    kind = _I32()
+    lg = np.empty(max(n, 1), np.int32)
+    rank = np.empty(max(n, 1), np.int32)
+    _check(load().sw_plan_preview(_addr(q_offsets), _addr(r_offsets), n, _addr(mat), mat.shape[0],
+                                  gap_open, gap_extend, mode, flags, sm_count, narrow_log2g,
+                                  cap_fraction, ctypes.byref(kind), _addr(lg), _addr(rank)),
+           "sw_plan_preview")
+    return PLAN_KINDS[kind.value], lg[:n], rank[:n]
 
 
 def sw_plan_destroy(plan: int) -> None:

@@ -68,7 +68,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp, int sample_cap,
-                   bool allow_packed) {
+                   bool allow_packed, BlocksPerSmFn blocks_per_sm) {
     *out = HostPlan();
     int rc = check_batch(q_offsets, r_offsets, n_pairs, mat, A, go, ge, nullptr, nullptr,
                          nullptr, msg);
@@ -108,7 +108,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     for (ProfileKind k : {ProfileKind::kPacked16, ProfileKind::kPacked16Bytes}) {
         bool &ok = k == ProfileKind::kPacked16 ? packed8 : packed4;
         if (!ok) continue;
-        const int b = group_blocks_per_sm(k, go == ge, A, nullptr);
+        const int b = blocks_per_sm(k, go == ge, A, nullptr);
         if (b < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
         ok = b >= 2;
     }
@@ -134,7 +134,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
             any = group_path_eligible(n[i], m[i], smax, go, ge);
         if (any) {
             int smem = 0;
-            bps = group_blocks_per_sm(out->kind, go == ge, A, &smem);
+            bps = blocks_per_sm(out->kind, go == ge, A, &smem);
             if (bps < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
             group_fits = bps > 0;
         }
@@ -237,4 +237,47 @@ cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_
     return e;
 }
 
+// Occupancy of the group kernel estimated from its shared memory alone (the
+// host-only preview has no device to ask): 228 KB per SM with 1 KB reserved
+// per block, 227 KB at most per block, and the blocks the registers allow
+// (the launch bounds' minimum).
+static int estimate_blocks_per_sm(ProfileKind kind, bool, int alphabet, int *smem_bytes) {
+    const size_t bytes = group_smem_bytes(kind, alphabet);
+    if (smem_bytes) *smem_bytes = (int)bytes;
+    constexpr size_t kSmemPerSm = 233472, kReservedPerBlock = 1024, kMaxPerBlock = 232448;
+    if (bytes > kMaxPerBlock) return 0;
+    const int by_smem = (int)(kSmemPerSm / (bytes + kReservedPerBlock));
+    const int by_regs = (kind == ProfileKind::kPacked16 && kRowsPacked > 16) ? 2 : kGroupMinBlocks;
+    return std::min(by_smem, by_regs);
+}
+
 }  // namespace swgb
+
+extern "C" int sw_plan_preview(const int64_t *q_offsets, const int64_t *r_offsets,
+                               int32_t n_pairs, const int8_t *score_matrix,
+                               int32_t alphabet_size, int32_t gap_open, int32_t gap_extend,
+                               int32_t mode, uint32_t flags, int32_t sm_count,
+                               int32_t narrow_log2g, double cap_fraction, int32_t *out_kind,
+                               int32_t *pair_log2g, int32_t *pair_rank) {
+    using namespace swgb;
+    if (!out_kind || (n_pairs > 0 && (!pair_log2g || !pair_rank)) || sm_count < 1 ||
+        narrow_log2g < -1 || narrow_log2g > 5 || !(cap_fraction > 0))
+        return set_error(SW_EINVAL, "sw_plan_preview: bad argument");
+    HostPlan hp;
+    std::string msg;
+    const int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size,
+                                  gap_open, gap_extend, mode, sm_count, narrow_log2g,
+                                  cap_fraction, &hp, &msg, 1, 8192,
+                                  (flags & SW_PLAN_NO_S16X2) == 0, estimate_blocks_per_sm);
+    if (rc != SW_OK) return set_error(rc, ("sw_plan_preview: " + msg).c_str());
+    *out_kind = (int32_t)hp.kind;
+    for (int32_t i = 0; i < n_pairs; ++i) pair_log2g[i] = pair_rank[i] = -1;
+    for (const ClassInfo &c : hp.classes)
+        for (int32_t k = 0; k < c.count; ++k) {
+            const int32_t id = hp.pairs[(size_t)(c.first + k)].id;
+            pair_log2g[id] = c.log2g;
+            pair_rank[id] = k;
+        }
+    for (size_t k = 0; k < hp.plain.size(); ++k) pair_rank[hp.plain[k].id] = (int32_t)k;
+    return SW_OK;
+}

@@ -228,11 +228,15 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
 // launches).  sample_cap: pairs the planner's schedule simulation looks at
 // (fewer plan faster, more plan better).  allow_packed = false keeps the
 // scaled int32 arithmetic even where the packed 16-bit form's bound holds.
+// blocks_per_sm: occupancy of the group kernel per (profile kind, linear
+// gaps, alphabet) (default: the CUDA occupancy query on the current device;
+// the host-only plan preview passes an estimate from shared memory).
+using BlocksPerSmFn = int (*)(ProfileKind, bool, int, int *);
 int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192,
-                   bool allow_packed = true);
+                   bool allow_packed = true, BlocksPerSmFn blocks_per_sm = group_blocks_per_sm);
 // Enqueues the kernels of a planned batch on s (queue-head reset included).
 cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
                          const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,
