@@ -434,7 +434,7 @@ def run_ours(args, rank, world, local):
         # measured choice of the lane-group widths (cached by GPU and batch shape)
         tune = swgb.sw_autotune(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
                                 batch.gap_open, batch.gap_extend, q8, r8, out,
-                                cache_path=args.tune_cache, stream=stream)
+                                cache_path=args.tune_cache, stream=stream, flags=flags)
         torch.cuda.synchronize()
     plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
                                batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,

@@ -232,6 +232,16 @@ int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
                 const uint8_t *r_seqs, int32_t *out, const char *cache_path, void *stream,
                 int32_t *chosen_log2g, double *chosen_frac, double *chosen_ms);
 
+/* sw_autotune for plans that will be made with plan `flags`: the candidates
+ * are planned with its SW_PLAN_ENDS_ONLY and SW_PLAN_NO_S16X2 bits (the
+ * other bits are ignored; q_seqs/r_seqs are one byte per residue), and the
+ * cache key includes those bits.  sw_autotune = flags 0. */
+int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                   int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                   int32_t gap_open, int32_t gap_extend, const uint8_t *q_seqs,
+                   const uint8_t *r_seqs, int32_t *out, uint32_t flags, const char *cache_path,
+                   void *stream, int32_t *chosen_log2g, double *chosen_frac, double *chosen_ms);
+
 /*
  * One-shot alignment of a batch whose sequences AND offsets are on the
  * DEVICE (score_matrix on the HOST).  Reads the offsets back to plan the

@@ -59,6 +59,9 @@ SIGNATURES = {
     "sw_autotune": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, ctypes.c_char_p, _P,
                      ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
                      ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "sw_autotune_ex": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _U32, ctypes.c_char_p,
+                        _P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "sw_server_create": ([_P, _I64, _I32, _I64, _PP], ctypes.c_int),
     "sw_server_submit": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32,
                           ctypes.POINTER(_I64)], ctypes.c_int),
@@ -236,16 +239,19 @@ def sw_plan_destroy(plan: int) -> None:
 
 
 def sw_autotune(ctx: int, q_offsets, r_offsets, score_matrix, gap_open: int, gap_extend: int,
-                q_seqs, r_seqs, out, cache_path: str | None = None, stream=None) -> dict:
-    """Measure the candidate tunings on a resident batch; sets the best on ctx."""
+                q_seqs, r_seqs, out, cache_path: str | None = None, stream=None,
+                flags: int = 0) -> dict:
+    """Measure the candidate tunings on a resident batch (planned with the
+    ENDS_ONLY / NO_S16X2 bits of `flags`); sets the best on ctx."""
     qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
     mat = _host_i8(score_matrix)
     lg, frac, ms = _I32(), ctypes.c_double(), ctypes.c_double()
-    _check(load().sw_autotune(ctx, qo.ctypes.data, ro.ctypes.data, len(qo) - 1, mat.ctypes.data,
-                              mat.shape[0], gap_open, gap_extend, _addr(q_seqs), _addr(r_seqs),
-                              _addr(out), cache_path.encode() if cache_path else None,
-                              _stream(stream), ctypes.byref(lg), ctypes.byref(frac),
-                              ctypes.byref(ms)), "sw_autotune")
+    _check(load().sw_autotune_ex(ctx, qo.ctypes.data, ro.ctypes.data, len(qo) - 1,
+                                 mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
+                                 _addr(q_seqs), _addr(r_seqs), _addr(out), flags,
+                                 cache_path.encode() if cache_path else None, _stream(stream),
+                                 ctypes.byref(lg), ctypes.byref(frac), ctypes.byref(ms)),
+           "sw_autotune_ex")
     return {"narrow_log2g": lg.value, "cap_fraction": frac.value, "ms": ms.value}
 
 

@@ -130,15 +130,18 @@ bool write_cache(const char *path, const std::vector<Entry> &entries, const char
 
 using namespace swgb;
 
-extern "C" int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
-                           int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
-                           int32_t gap_open, int32_t gap_extend, const uint8_t *q_seqs,
-                           const uint8_t *r_seqs, int32_t *out, const char *cache_path,
-                           void *stream, int32_t *chosen_log2g, double *chosen_frac,
-                           double *chosen_ms) {
+extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                              int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                              int32_t gap_open, int32_t gap_extend, const uint8_t *q_seqs,
+                              const uint8_t *r_seqs, int32_t *out, uint32_t flags,
+                              const char *cache_path, void *stream, int32_t *chosen_log2g,
+                              double *chosen_frac, double *chosen_ms) {
     if (!ctx || n_pairs <= 0 || !q_offsets || !r_offsets || !score_matrix || !q_seqs || !r_seqs ||
         !out)
         return set_error(SW_EINVAL, "sw_autotune: bad argument");
+    // the candidates run the kernels the timed plans will run: the same
+    // arithmetic form and passes (the inputs here are one byte per residue)
+    flags &= SW_PLAN_ENDS_ONLY | SW_PLAN_NO_S16X2;
     char gpu[256];
     int32_t sms = 0;
     sw_ctx_sm_count(ctx, &sms);
@@ -150,8 +153,9 @@ extern "C" int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t 
             return set_error(SW_ECUDA, "sw_autotune: device properties");
         snprintf(gpu, sizeof gpu, "%s", prop.name);
     }
-    const std::string key = batch_key(gpu, sms, q_offsets, r_offsets, n_pairs, score_matrix,
-                                      alphabet_size, gap_open, gap_extend);
+    std::string key = batch_key(gpu, sms, q_offsets, r_offsets, n_pairs, score_matrix,
+                                alphabet_size, gap_open, gap_extend);
+    if (flags) key += "/flags" + std::to_string(flags);
     std::vector<Entry> cache;
     if (cache_path && *cache_path) {
         cache = read_cache(cache_path);
@@ -184,7 +188,7 @@ extern "C" int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t 
         if ((rc = sw_ctx_set_tuning(ctx, c.lg, c.frac)) != SW_OK) break;
         sw_plan *plan = nullptr;
         rc = sw_plan_create(ctx, q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size,
-                            gap_open, gap_extend, SW_MODE_BATCHED, 0u, &plan);
+                            gap_open, gap_extend, SW_MODE_BATCHED, flags, &plan);
         if (rc != SW_OK) break;
         float total = 0.f;
         for (int it = 0; it < 3 && rc == SW_OK; ++it) {
@@ -218,4 +222,15 @@ extern "C" int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t 
             return set_error(SW_EINVAL, "sw_autotune: cannot write the cache file");
     }
     return SW_OK;
+}
+
+extern "C" int sw_autotune(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offsets,
+                           int32_t n_pairs, const int8_t *score_matrix, int32_t alphabet_size,
+                           int32_t gap_open, int32_t gap_extend, const uint8_t *q_seqs,
+                           const uint8_t *r_seqs, int32_t *out, const char *cache_path,
+                           void *stream, int32_t *chosen_log2g, double *chosen_frac,
+                           double *chosen_ms) {
+    return sw_autotune_ex(ctx, q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size,
+                          gap_open, gap_extend, q_seqs, r_seqs, out, 0u, cache_path, stream,
+                          chosen_log2g, chosen_frac, chosen_ms);
 }

@@ -68,3 +68,36 @@ def test_autotune_cache_miss_then_hit(gpu_lib, tmp_path):
         assert len({e["key"] for e in doc["entries"]}) == 2
     finally:
         swgb.sw_ctx_destroy(ctx)
+
+
+def test_autotune_with_plan_flags(gpu_lib, tmp_path):
+    """sw_autotune_ex plans its candidates with the caller's ENDS_ONLY /
+    NO_S16X2 bits: each flag set gets its own cache entry, and the ends-only
+    candidates leave exact score/end outputs (no start outputs written)."""
+    import torch
+    swgb = gpu_lib
+    b = wl.gen_config(1, n_pairs=4000)
+    dev = torch.device("cuda:0")
+    q = torch.from_numpy(b.q_seqs).to(dev)
+    r = torch.from_numpy(b.r_seqs).to(dev)
+    out = torch.full((5, b.n_pairs), -7, dtype=torch.int32, device=dev)
+    ctx = swgb.sw_ctx_create(0)
+    cache = tmp_path / "tune.json"
+    idx = np.arange(0, b.n_pairs, 17)
+    expect = oracle.align_workload(b, idx=idx)
+    try:
+        swgb.sw_autotune(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open, b.gap_extend,
+                         q, r, out, cache_path=str(cache), flags=swgb.SW_PLAN_ENDS_ONLY)
+        got = out.cpu().numpy().T
+        assert np.array_equal(got[idx, :3], expect[:, :3])
+        assert np.all(got[:, 3:] == -7)
+        swgb.sw_autotune(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open, b.gap_extend,
+                         q, r, out, cache_path=str(cache), flags=swgb.SW_PLAN_NO_S16X2)
+        swgb.sw_autotune(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open, b.gap_extend,
+                         q, r, out, cache_path=str(cache))
+        assert np.array_equal(out.cpu().numpy().T[idx], expect)
+        doc = json.loads(cache.read_text())
+        assert len(doc["entries"]) == 3
+        assert len({e["key"] for e in doc["entries"]}) == 3
+    finally:
+        swgb.sw_ctx_destroy(ctx)
