@@ -519,7 +519,10 @@ def run_ours(args, rank, world, local):
     swgb.sw_plan_destroy(eplan)
     e2e = {"value": job_cells * args.steps / e2e_t / 1e9, "unit": "GCUPS",
            "h2d_bytes_per_step": int(q_in.nbytes + r_in.nbytes),
-           "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same}
+           "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same,
+           "inputs": ("page-locked host buffers read in place by the kernels over the "
+                      "coherent host link" if swgb.sw_ctx_host_in_place(ctx)
+                      else "page-locked host buffers copied to the device each step")}
 
     swgb.sw_plan_destroy(plan)
 

@@ -116,6 +116,12 @@ int sw_ctx_destroy(sw_ctx *ctx);
 /* Number of streaming multiprocessors of the context's device. */
 int sw_ctx_sm_count(const sw_ctx *ctx, int32_t *out);
 
+/* *yes = 1 when the context's device reads host memory through the host's
+ * page tables over a coherent link (cudaDevAttrPageableMemoryAccessUses-
+ * HostPageTables), so sw_plan_execute_host reads page-locked inputs in
+ * place; 0 otherwise. */
+int sw_ctx_host_in_place(const sw_ctx *ctx, int32_t *yes);
+
 /* Synchronise the context's device, return its device status word in
  * *status (0 = no inconsistency detected by any kernel; bit 0 = a reverse
  * pass did not reproduce its forward score) and clear it. */
@@ -171,6 +177,11 @@ int sw_plan_execute(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_seqs,
  * int32: all scores, then all qend, rend, qstart, rstart) and synchronises
  * `stream`.  Page-locked host memory makes the copies asynchronous DMA.
  * The staging buffers are allocated on the first call and kept by the plan.
+ * When the context's device reads host memory over a coherent link
+ * (sw_ctx_host_in_place says 1: NVLink-C2C on Grace) and both sequence
+ * buffers are page-locked (cudaHostAlloc / cudaHostRegister), the kernels
+ * read them in place instead: each residue crosses the link once, while the
+ * alignment runs, and no input copy precedes the kernels.
  */
 int sw_plan_execute_host(sw_plan *plan, const uint8_t *q_seqs, const uint8_t *r_seqs,
                          int32_t *out_host, void *stream);

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sw_ctx_destroy": ([_P], ctypes.c_int),
     "sw_ctx_sm_count": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_status": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_ctx_host_in_place": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
     "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
     "sw_plan_execute": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -193,6 +194,13 @@ def sw_plan_execute(plan: int, q_seqs, r_seqs, out, stream=None) -> None:
     outs = [out[k] for k in range(5)]
     _check(load().sw_plan_execute(plan, _addr(q_seqs), _addr(r_seqs), *[_addr(o) for o in outs],
                                   _stream(stream)), "sw_plan_execute")
+
+
+def sw_ctx_host_in_place(ctx: int) -> bool:
+    """Whether sw_plan_execute_host reads page-locked inputs in place."""
+    v = _I32()
+    _check(load().sw_ctx_host_in_place(ctx, ctypes.byref(v)), "sw_ctx_host_in_place")
+    return bool(v.value)
 
 
 def sw_plan_execute_host(plan: int, q_seqs, r_seqs, out_host, stream=None) -> None:

@@ -79,6 +79,9 @@ struct sw_ctx {
     int32_t *d_status = nullptr;
     int narrow_log2g = -1;      // planner override: bulk lane-group width (log2), -1 = auto
     double cap_fraction = 0.5;  // planner override: long-pair cap (used with narrow_log2g)
+    // the device reads host memory through the host's page tables over a
+    // coherent link (NVLink-C2C on Grace): pinned host inputs are read in place
+    bool host_in_place = false;
     std::mutex mu;
     std::vector<std::pair<sw_plan *, cudaEvent_t>> retired;
 };
@@ -166,6 +169,13 @@ int sw_ctx_create(int32_t device, sw_ctx **out) {
     }
     ctx->sm_count = prop.multiProcessorCount;
     snprintf(ctx->name, sizeof ctx->name, "%s", prop.name);
+    int ats = 0;
+    if (cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        ats = 0;
+    }
+    ctx->host_in_place = ats != 0;
     if (cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -328,6 +338,25 @@ int sw_plan_execute(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seqs,
     return SW_OK;
 }
 
+// The device address of a pinned (page-locked, registered) host buffer when
+// the context reads host inputs in place, else NULL.
+static const uint8_t *host_view(const sw_ctx *ctx, const uint8_t *h) {
+    if (!ctx->host_in_place || !h) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<const uint8_t *>(a.devicePointer);
+}
+
+int sw_ctx_host_in_place(const sw_ctx *ctx, int32_t *yes) {
+    if (!ctx || !yes) return fail(SW_EINVAL, "sw_ctx_host_in_place: NULL argument");
+    *yes = ctx->host_in_place ? 1 : 0;
+    return SW_OK;
+}
+
 int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seqs,
                          int32_t *out_host, void *stream) {
     if (!p) return fail(SW_EINVAL, "sw_plan_execute_host: plan is NULL");
@@ -354,10 +383,18 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (qb > 0) SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, qb, cudaMemcpyHostToDevice, s));
-    if (rb > 0) SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, rb, cudaMemcpyHostToDevice, s));
+    // Pinned host inputs on a coherent host link are read by the kernels in
+    // place (each residue crosses the link once, during the alignment);
+    // otherwise they are copied into the plan's staging buffers first.
+    const uint8_t *q_in = host_view(p->ctx, q_seqs), *r_in = host_view(p->ctx, r_seqs);
+    if (!q_in || !r_in) {
+        if (qb > 0) SW_CUDA_TRY(cudaMemcpyAsync(p->d_q, q_seqs, qb, cudaMemcpyHostToDevice, s));
+        if (rb > 0) SW_CUDA_TRY(cudaMemcpyAsync(p->d_r, r_seqs, rb, cudaMemcpyHostToDevice, s));
+        q_in = p->d_q;
+        r_in = p->d_r;
+    }
     const int64_t n = p->n_pairs;
-    int rc = sw_plan_execute(p, p->d_q, p->d_r, p->d_out, p->d_out + n, p->d_out + 2 * n,
+    int rc = sw_plan_execute(p, q_in, r_in, p->d_out, p->d_out + n, p->d_out + 2 * n,
                              p->d_out + 3 * n, p->d_out + 4 * n, stream);
     if (rc != SW_OK) return rc;
     // with SW_PLAN_ENDS_ONLY the start rows are not computed and not copied

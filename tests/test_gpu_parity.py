@@ -349,3 +349,25 @@ def test_ends_only_plans(gpu_lib, ctx, k):
         assert np.all(host[:, 3:] == -9)
         al.close()
     assert gpu_lib.sw_ctx_status(ctx) == 0
+
+
+def test_host_buffer_execution_pinned_and_pageable(gpu_lib, ctx):
+    """sw_plan_execute_host on page-locked inputs (read in place when the
+    device reads host memory over a coherent link) and on pageable inputs
+    (copied): the same outputs as the oracle either way, repeated runs too."""
+    import torch
+    b = wl.gen_config(1, n_pairs=3000)
+    expect = oracle.align_workload(b)
+    plan = gpu_lib.sw_plan_create(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
+                                  b.gap_extend, gpu_lib.SW_MODE_BATCHED, gpu_lib.SW_PLAN_GRAPH)
+    try:
+        pinned = (torch.from_numpy(b.q_seqs).pin_memory(), torch.from_numpy(b.r_seqs).pin_memory())
+        pageable = (torch.from_numpy(b.q_seqs.copy()), torch.from_numpy(b.r_seqs.copy()))
+        for q, r in (pinned, pageable, pinned):
+            out = torch.full((5, b.n_pairs), -9, dtype=torch.int32).pin_memory()
+            for _ in range(2):
+                gpu_lib.sw_plan_execute_host(plan, q, r, out)
+            assert_same(out.numpy().T, expect, f"host buffers, pinned={q.is_pinned()}")
+    finally:
+        gpu_lib.sw_plan_destroy(plan)
+    assert isinstance(gpu_lib.sw_ctx_host_in_place(ctx), bool)
