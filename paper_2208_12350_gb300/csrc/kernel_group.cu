@@ -70,10 +70,11 @@
 // sums stay below 2^15, so no carry crosses from the low half to the high
 // one; s' comes from two profile words (low-half rows against column j's
 // residue, high-half rows against column j - 1's) whose other halves are 0.
-// The end cell: the low 3 bits of every Hs are 0, so a chain
-// acc = viaddmax2(Hs_k, 7 - k, acc) over a lane's 8 words gives, per half,
-// the column's largest score with the smallest row holding it (row code
-// 7 - k).  The chain starts from a threshold T = (8 best + 7): acc differs
+// The end cell: the low 3 bits of every Hs are 0, so Hs_k + (7 - k) is a
+// carry-free 32-bit add and a chain acc = vimax3_2(Hs_k + 7 - k,
+// Hs_k+1 + 6 - k, acc) over a lane's 8 words (one three-way max per pair of
+// words) gives, per half, the column's largest score with the smallest row
+// holding it (row code 7 - k).  The chain starts from a threshold T = (8 best + 7): acc differs
 // from T in a half exactly when that half's best score grew at this column,
 // and the (column, acc) pair of that step is recorded, so each half ends
 // with its largest score, the first column reaching it and the smallest row
@@ -131,6 +132,23 @@ __host__ __device__ constexpr int unroll_of() {
 #endif
 #ifndef SWGB_SPLIT_ROWS
 #define SWGB_SPLIT_ROWS 0
+#endif
+// Packed form, end-key chain of a column: 0 = one viaddmax per word
+// (acc = max(h_k + code_k, acc)); 1 = words in pairs, the sums h_k + code_k
+// as plain adds and one three-way max per pair (half the ALU-pipe maxes);
+// 2 = as 1 with the adds forced onto the FMA pipe (multiply-add by a one
+// the compiler cannot see).  Measured with the same tuning on one GB300:
+// 1 is 1.9 % faster than 0 on 100k DNA pairs and 4.7 % on 20k protein
+// pairs; 2 is no faster than 0 on DNA.
+#ifndef SWGB_KEY_PAIRS
+#define SWGB_KEY_PAIRS 1
+#endif
+// Packed form, boundary-out word: 0 = stored only for columns inside the
+// strip (a range check per step); 1 = stored on every step (the words of
+// columns outside [0, m) land in ring slots that are overwritten before
+// they are flushed, or never flushed).
+#ifndef SWGB_BOUT_ANY_COLUMN
+#define SWGB_BOUT_ANY_COLUMN 1
 #endif
 // A lane's R rows as two halves a column apart (2: two independent row
 // chains per step) or one block of R rows (1).  Measured on 100k and 200k
@@ -378,6 +396,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
     // F = go (F - go = 0), which gives the row below the same values
     const uint32_t kNoBound = PK ? 0u : (0xC0000000u | ((uint32_t)go & 0xFFFFu));
     constexpr int NT = kGroupWarps * 32;
+    // 1 (blocks have NT threads), unknown to the compiler
+    [[maybe_unused]] const uint32_t one_opaque = blockDim.x / NT;
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
     const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * R : (size_t)(A + 1) * (R / 4) * 32 * 16;
@@ -711,6 +731,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                     uint32_t F = LIN ? 0u : __viaddmax_s16x2(upF, geP, upH);
                     uint32_t hprev = upH;
                     uint32_t acc[NC];
+                    uint32_t hc_even = 0u;  // h + row code of the pair's first word
 #pragma unroll
                     for (int c = 0; c < NC; ++c) acc[c] = Tw[c];
 #pragma unroll
@@ -730,12 +751,27 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                         diag = Hw[k];
                         Hw[k] = h;
                         hprev = h;
-                        acc[k / CL] = __viaddmax_s16x2(h, (uint32_t)(CL - 1 - k % CL) * 0x10001u,
-                                                       acc[k / CL]);
+                        const uint32_t code = (uint32_t)(CL - 1 - k % CL) * 0x10001u;
+                        if constexpr (SWGB_KEY_PAIRS == 0) {
+                            acc[k / CL] = __viaddmax_s16x2(h, code, acc[k / CL]);
+                        } else {
+                            // the low CB bits of both halves of h are 0 and the
+                            // code is below 2^CB, so the 32-bit add is per half
+                            uint32_t hc;
+                            if constexpr (SWGB_KEY_PAIRS == 2)
+                                asm("mad.lo.u32 %0, %1, %2, %3;"
+                                    : "=r"(hc) : "r"(h), "r"(one_opaque), "r"(code));
+                            else
+                                hc = h + code;
+                            if (k & 1)
+                                acc[k / CL] = __vimax3_s16x2(hc_even, hc, acc[k / CL]);
+                            else
+                                hc_even = hc;
+                        }
                     }
                     outHw = hprev;
                     outFw = F;
-                    if (gl == G - 1 && has_out && in1)
+                    if (gl == G - 1 && has_out && (SWGB_BOUT_ANY_COLUMN || in1))
                         bout_ring[j1 & 31] = __byte_perm(outHw, outFw, 0x7632);
                     diag0w = upH;
                     // a half whose best score grew records (step, acc half); the
