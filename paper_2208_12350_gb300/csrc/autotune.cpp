@@ -36,7 +36,7 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
 
 // Part of every cache key: a tuning measured on another kernel build is not
 // reused.  Changed whenever the batched kernel's code changes.
-constexpr char kKernelRevision[] = "group-kernel-r12 H+go / transposed reverse / linear / score tables / warp-built profiles / packed 16-bit / half-width tails / paired end-key chain";
+constexpr char kKernelRevision[] = "group-kernel-r12 H+go / transposed reverse / linear / score tables / warp-built profiles / packed 16-bit / half-width tails / paired end-key chain / strip-start cost in the planner";
 
 std::string batch_key(const char *gpu, int sms, const int64_t *qo, const int64_t *ro, int n_pairs,
                       const int8_t *mat, int A, int go, int ge) {

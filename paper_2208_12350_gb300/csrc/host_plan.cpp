@@ -22,6 +22,15 @@ static int plan_err(std::string *msg, int code, const char *fmt, long long a = 0
     return code;
 }
 
+// Planner cost of one strip start, in wavefront steps of the whole warp
+// (the strip's profile build and its first staging wait).  A term per
+// residue code (the build writes A + 1 profile columns) sent 20k protein
+// pairs to wider groups, measured slower, so the cost is one constant.
+#ifndef SWGB_STRIP_OV_STEPS
+#define SWGB_STRIP_OV_STEPS 12
+#endif
+static double strip_overhead_steps(int /*A*/) { return (double)SWGB_STRIP_OV_STEPS; }
+
 static int smax_of(const int8_t *mat, int A, int *smin_out) {
     int smax = -128, smin = 127;
     for (int i = 0; i < A * A; ++i) {
@@ -159,7 +168,8 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     }
     const std::vector<PlannedClass> planned =
         plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction, sample_cap,
-                     out->kind == ProfileKind::kPacked16, rows_of(out->kind));
+                     out->kind == ProfileKind::kPacked16, rows_of(out->kind),
+                     strip_overhead_steps(A));
     out->pairs.reserve(gp.size());
     int warp_begin = 0;
     for (const PlannedClass &pc : planned) {

@@ -5,7 +5,14 @@
 // A pair aligned by a group of G lanes with R rows per lane takes
 // ceil(n / (G R)) strips of (m + G - 1) wavefront steps (rounded up to the
 // kernel's 4-step blocks); its reverse pass is estimated at a quarter of
-// that.  Narrow groups waste the fewest cells on padding and fill but make
+// that.  Each strip start also stalls the group's whole warp (its 32 / G
+// groups) while the warp builds the strip's query profile, so a strip is
+// charged a fixed number of steps times 32 / G besides its columns.  The
+// fixed cost is 12 steps: measured on 100k DNA pairs with the host-only
+// plan preview, every value from 4 to 20 makes the planner's own choice the
+// measured best (bulk groups of 8 lanes with half-width tails, 2,221 GCUPS,
+// against 1,995 for the all-2-lane plan it chose without the charge), and
+// from 24 up it sends 20k protein pairs to wider groups, measured slower.  Narrow groups waste the fewest cells on padding and fill but make
 // a pair's serial sweep long, so a batch with a long tail finishes late.
 // The planner therefore keeps a narrow width Gn for the bulk and sends each
 // pair whose sweep under Gn exceeds a cap (a fraction of the mean load per
@@ -46,12 +53,20 @@ struct Costs {
     double operator()(int lg, int32_t id) const { return at[lg][(size_t)id]; }
 };
 
-Costs compute_costs(const std::vector<PlanPair> &pairs, int rows) {
+Costs compute_costs(const std::vector<PlanPair> &pairs, int rows, double strip_overhead) {
     Costs c;
     for (int lg = kMinLog2G; lg <= 5; ++lg) {
+        const int G = 1 << lg;
         c.at[lg].resize(pairs.size());
-        for (size_t i = 0; i < pairs.size(); ++i)
-            c.at[lg][i] = 1.25 * (double)sweep_steps(pairs[i].n, pairs[i].m, 1 << lg, rows);
+        for (size_t i = 0; i < pairs.size(); ++i) {
+            const PlanPair &p = pairs[i];
+            const int64_t strips =
+                (p.n > 0 && p.m > 0) ? (p.n + (int64_t)G * rows - 1) / ((int64_t)G * rows) : 0;
+            // a strip start stalls the whole warp (its 32 / G groups) for the
+            // profile build: charged to the pair as group steps
+            c.at[lg][i] = 1.25 * ((double)sweep_steps(p.n, p.m, G, rows) +
+                                  (double)strips * strip_overhead * (double)(32 >> lg));
+        }
     }
     return c;
 }
@@ -187,10 +202,11 @@ void sort_classes(std::vector<PlannedClass> &cls, const Costs &cost) {
 
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
                                        int narrow_log2g_hint, double cap_fraction_hint,
-                                       int sample_cap, bool half_tails, int rows) {
+                                       int sample_cap, bool half_tails, int rows,
+                                       double strip_overhead) {
     if (pairs.empty()) return {};
     n_warps = std::max(1, n_warps);
-    const Costs cost = compute_costs(pairs, rows);
+    const Costs cost = compute_costs(pairs, rows, strip_overhead);
     if (narrow_log2g_hint >= 0) {
         auto cls = build(pairs, cost, n_warps, std::max(narrow_log2g_hint, kMinLog2G),
                          cap_fraction_hint, half_tails, rows);

@@ -139,7 +139,7 @@ struct PlannedClass {
 std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n_warps,
                                        int narrow_log2g_hint, double cap_fraction_hint,
                                        int sample_cap = 8192, bool half_tails = false,
-                                       int rows = kRows);
+                                       int rows = kRows, double strip_overhead = 0.0);
 int64_t sweep_steps(int n, int m, int G, int rows = kRows);
 
 // Arithmetic and profile element width of the group kernel: scaled int32

@@ -51,7 +51,9 @@ def test_form_selection(lib):
 def test_every_pair_planned_once_longest_first(lib):
     """Every pair has one lane-group width (or the plain kernel), each width
     class's queue positions are a permutation, and a queue hands pairs out
-    longest first by the planner's estimate (strips x columns)."""
+    longest first by the planner's estimate, which grows with the pair's
+    strips and with its columns (strips x (columns + a fixed cost per strip
+    start)): no pair is queued after one it dominates in both."""
     b = wl.gen_config(3, n_pairs=3000)
     for tuning in ((-1, 0.5), (1, 0.05), (2, 1e9), (3, 0.25)):
         kind, lg, rank = preview(lib, b, narrow_log2g=tuning[0], cap_fraction=tuning[1])
@@ -63,11 +65,21 @@ def test_every_pair_planned_once_longest_first(lib):
             sel = np.flatnonzero(lg == g)
             assert np.array_equal(np.sort(rank[sel]), np.arange(len(sel)))
             G = 1 << int(g)
-            cost = np.ceil(n[sel] / (16 * G)) * ((m[sel] + G - 1 + 3) // 4 * 4)
             order = sel[np.argsort(rank[sel])]
-            c = np.ceil(n[order] / (16 * G)) * ((m[order] + G - 1 + 3) // 4 * 4)
-            assert np.all(np.diff(c) <= 0), (tuning, g)
-            assert cost.sum() == c.sum()
+            strips = np.ceil(n[order] / (16 * G)).astype(np.int64)
+            cols = (m[order] + G - 1 + 3) // 4 * 4
+            # for every queue position, the most columns among the later pairs
+            # with at least as many strips must not exceed its own, and a later
+            # pair with more strips must not have as many columns
+            for lvl in np.unique(strips):
+                later_max = np.maximum.accumulate(
+                    np.where(strips >= lvl, cols, -1)[::-1])[::-1]
+                nxt = np.append(later_max[1:], -1)
+                at = strips == lvl
+                assert np.all(nxt[at] <= cols[at]), (tuning, g, int(lvl))
+                more = np.maximum.accumulate(np.where(strips > lvl, cols, -1)[::-1])[::-1]
+                nxt_more = np.append(more[1:], -1)
+                assert np.all(nxt_more[at] < cols[at]), (tuning, g, int(lvl))
 
 
 def test_half_width_tails(lib):
