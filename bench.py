@@ -208,31 +208,36 @@ def run_reference(args, rank):
 
 # ------------------------------------------------------------ ncu traffic
 
-def profiled_traffic(batch, tune, arith="s16x2") -> int | None:
+def profiled_traffic(batch, tune, arith="s16x2", flags=0, sms=152) -> int | None:
     """DRAM bytes per launch of the group kernel from the committed ncu
     summary, if that capture was of this workload, this arithmetic, this
-    tuning and this kernel source (else None: the counters are stale)."""
+    kernel source and a plan with the same lane-group widths per pair (else
+    None: the counters are stale)."""
     import hashlib
     import re
     form = "" if arith == "s16x2" else "s32_"
     path = os.path.join(ROOT, "profiles", f"sw_group_kernel_{form}{batch.name}.md")
     src = os.path.join(ROOT, "paper_2208_12350_gb300", "csrc", "kernel_group.cu")
-    if not os.path.exists(path) or tune is None:
+    import paper_2208_12350_gb300 as swgb
+    # captures are of the default plan (starts and ends, one byte per residue)
+    if not os.path.exists(path) or tune is None or flags & ~swgb.SW_PLAN_NO_S16X2:
         return None
     text = open(path).read()
     sha = re.search(r"kernel_sha256: ([0-9a-f]{64})", text)
-    tun = re.search(r"tuning: narrow_log2g=(-?\d+) cap_fraction=([0-9.e+]+|any)", text)
+    wid = re.search(r"widths: ([0-9,]+)", text)
     byt = re.search(r"dram_bytes_per_launch: (\d+)", text)
-    if not (sha and tun and byt):
+    if not (sha and wid and byt):
         return None
     if sha.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
         return None
     ar = re.search(r"arith: (\w+)", text)
     if (ar.group(1) if ar else "s32") != arith:
         return None
-    if int(tun.group(1)) != tune["narrow_log2g"]:
-        return None
-    if tun.group(2) != "any" and abs(float(tun.group(2)) - tune["cap_fraction"]) > 1e-9:
+    _, lg, _ = swgb.sw_plan_preview(batch.q_offsets, batch.r_offsets, batch.matrix,
+                                    batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED, flags,
+                                    sms, tune["narrow_log2g"], tune["cap_fraction"])
+    hist = np.bincount(lg[lg >= 0], minlength=6)[:6].tolist() + [int(np.sum(lg < 0))]
+    if hist != [int(x) for x in wid.group(1).split(",")]:
         return None
     return int(byt.group(1))
 
@@ -478,7 +483,7 @@ def run_ours(args, rank, world, local):
     mb_rate, _ = swgb.sw_microbench_int(peak_op, local, 2048)
     peak_measured = mb_rate / 1e12
     sm_mhz = clk.get("sm_mhz")
-    traffic = profiled_traffic(batch, tune, info["arith"]) \
+    traffic = profiled_traffic(batch, tune, info["arith"], flags, sms) \
         if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
             "frac": achieved / peak_measured if peak_measured else None, "traffic": traffic,
