@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--serve-rate0", type=float, default=250.0, help="first offered rate, req/s")
     ap.add_argument("--serve-points", type=int, default=14)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
+    ap.add_argument("--serve-clients", type=int, default=4,
+                    help="client threads submitting the Poisson arrival schedule")
     return ap.parse_args()
 
 
@@ -277,6 +279,7 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
         out = swgb.sw_server_wait(srv, submit(rq), rq.batch.n_pairs, timeout_ms=120000)
         identical &= check(rq, out)
     points = []
+    n_sub = max(1, args.serve_clients)
     rate = args.serve_rate0
     try:
         for _ in range(args.serve_points):
@@ -286,21 +289,25 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
             arrival = np.zeros(n, dtype=np.int64)
             ids: queue.Queue = queue.Queue()
             t0 = time.monotonic_ns() + 20_000_000
+            for i, rq in enumerate(todo):
+                arrival[i] = t0 + int(rq.arrival_s / rate * 1e9)
 
-            def submitter():
+            def submitter(k):
+                # client thread k submits requests k, k + S, ... at their
+                # scheduled arrivals (the copy into the server's staging runs
+                # outside the interpreter lock, so clients overlap)
                 try:
-                    for i, rq in enumerate(todo):
-                        at = t0 + int(rq.arrival_s / rate * 1e9)
-                        arrival[i] = at
-                        delay = (at - time.monotonic_ns()) / 1e9
+                    for i in range(k, n, n_sub):
+                        delay = (arrival[i] - time.monotonic_ns()) / 1e9
                         if delay > 0:
                             time.sleep(delay)
-                        ids.put((i, submit(rq)))
+                        ids.put((i, submit(todo[i])))
                 except Exception as e:  # surfaced by the waiter
                     ids.put((-1, e))
 
-            th = threading.Thread(target=submitter)
-            th.start()
+            ths = [threading.Thread(target=submitter, args=(k,)) for k in range(n_sub)]
+            for th in ths:
+                th.start()
             lat = np.zeros(n)
             done_last = 0
             cells = 0
@@ -315,7 +322,8 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
                 lat[i] = (done_ns - arrival[i]) / 1e6
                 done_last = max(done_last, done_ns)
                 cells += rq.batch.cells
-            th.join()
+            for th in ths:
+                th.join()
             lc1 = swgb.sw_server_launches(srv)
             span = (done_last - t0) / 1e9
             served = n / span
@@ -340,6 +348,7 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
             "max_sustained_rps": best["served_rps"] if best else None,
             "peak_gcups": max(p["gcups"] for p in points) if points else None,
             "identical_outputs": identical, "budget_gb": args.serve_budget_gb, "streams": 8,
+            "client_threads": n_sub,
             "device_bytes_peak": st["device_bytes_peak"],
             "requests": "Poisson arrivals; floor(log-uniform[1,4096]) pairs; 50% dna-100k, "
                         "50% protein-20k pairs",
