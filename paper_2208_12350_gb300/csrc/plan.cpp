@@ -105,23 +105,52 @@ double simulate(const Costs &cost, const std::vector<PlannedClass> &cls, int n_w
     // An event is k idle groups of warp w, free from time t, on the warp's
     // v-th class visit: one entry stands for all of a warp's groups that
     // fall idle together, so a warp costs one entry, not one per group.
+    // The heap is a vector ordered by std::greater (earliest time first,
+    // then warp, visit, groups).
     using Ev = std::tuple<double, int, int, int>;  // time, warp, visit, groups
-    std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> ev;
+    std::vector<Ev> heap;
+    heap.reserve((size_t)sw + 64);
+    const std::greater<Ev> later;
+    auto push = [&](double t, int w, int v, int k) {
+        heap.emplace_back(t, w, v, k);
+        std::push_heap(heap.begin(), heap.end(), later);
+    };
     std::vector<int> pos(nc, 0), visit(sw, 0), busy(sw, 0);
     std::vector<double> wend(sw, 0.0);
+    size_t left = 0;  // sampled pairs not yet handed out
+    for (int c = 0; c < nc; ++c) left += q[c].size();
     for (int w = 0; w < sw; ++w) {
         busy[w] = 32 >> cls[start[w]].log2g;
-        ev.emplace(0.0, w, 0, busy[w]);
+        heap.emplace_back(0.0, w, 0, busy[w]);
     }
+    std::make_heap(heap.begin(), heap.end(), later);
     double makespan = 0;
-    while (!ev.empty()) {
-        auto [t, w, v, k] = ev.top();
-        ev.pop();
+    while (!heap.empty()) {
+        if (left == 0) {
+            // every queue is empty: the remaining events only walk idle
+            // groups through the classes, and each warp then ends at the
+            // latest of its wend and its pending events' times
+            for (int w = 0; w < sw; ++w) makespan = std::max(makespan, wend[w]);
+            for (const Ev &e : heap)
+                if (std::get<2>(e) == visit[std::get<1>(e)]) makespan = std::max(makespan, std::get<0>(e));
+            break;
+        }
+        std::pop_heap(heap.begin(), heap.end(), later);
+        auto [t, w, v, k] = heap.back();
+        heap.pop_back();
         if (v != visit[w]) continue;
         const int c = (start[w] + v) % nc;
-        if (pos[c] < (int)q[c].size()) {
-            ev.emplace(t + q[c][pos[c]++], w, v, 1);
-            if (k > 1) ev.emplace(t, w, v, k - 1);
+        // the warp's idle groups take pairs one after another: each time the
+        // rest of them would be the next event popped (every other pending
+        // event is later in the heap order and costs are positive)
+        while (k > 0 && pos[c] < (int)q[c].size()) {
+            push(t + q[c][pos[c]++], w, v, 1);
+            --left;
+            --k;
+        }
+        if (k == 0) continue;
+        if (left == 0) {
+            push(t, w, v, k);
             continue;
         }
         wend[w] = std::max(wend[w], t);
@@ -131,7 +160,7 @@ double simulate(const Costs &cost, const std::vector<PlannedClass> &cls, int n_w
             if (++visit[w] < nc) {
                 const int c2 = (start[w] + visit[w]) % nc;
                 busy[w] = 32 >> cls[c2].log2g;
-                ev.emplace(wend[w], w, visit[w], busy[w]);
+                push(wend[w], w, visit[w], busy[w]);
             }
         }
     }
