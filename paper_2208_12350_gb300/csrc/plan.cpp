@@ -71,37 +71,78 @@ Costs compute_costs(const std::vector<PlanPair> &pairs, int rows, double strip_o
     return c;
 }
 
-struct Candidate {
-    std::vector<PlannedClass> classes;
-    double makespan = 0;
+
+// The sampled pairs in descending order of their estimated cost under each
+// lane-group width: sorted once per width and shared by every candidate.
+struct SampleOrder {
+    std::vector<int32_t> at[6];
 };
+SampleOrder sample_order(const Costs &cost, const std::vector<char> &sampled) {
+    SampleOrder o;
+    std::vector<int32_t> ids;
+    for (size_t i = 0; i < sampled.size(); ++i)
+        if (sampled[i]) ids.push_back((int32_t)i);
+    for (int lg = kMinLog2G; lg <= 5; ++lg) {
+        o.at[lg] = ids;
+        std::sort(o.at[lg].begin(), o.at[lg].end(),
+                  [&](int32_t a, int32_t b) { return cost(lg, a) > cost(lg, b); });
+    }
+    return o;
+}
+
+// A candidate's schedule before it is simulated: each class's queue of
+// sampled pair costs, longest first; the class each simulated warp starts
+// on; and a lower bound on the makespan: no group finishes before the
+// longest pair it runs, and a pair of cost x in a class of width G keeps
+// G / 32 of a warp busy for x, so the W simulated warps need at least
+// sum(x G / 32) / W.
+struct SimSetup {
+    std::vector<std::vector<double>> q;
+    std::vector<int> start;
+    double lower = 0;
+};
+SimSetup sim_setup(const Costs &cost, const std::vector<PlannedClass> &cls, int n_warps,
+                   const SampleOrder &order, size_t n_pairs, double scale) {
+    SimSetup S;
+    const int nc = (int)cls.size();
+    if (nc == 0) return S;
+    std::vector<int8_t> cls_of(n_pairs, -1);
+    for (int c = 0; c < nc; ++c)
+        for (int32_t id : cls[c].pairs) cls_of[(size_t)id] = (int8_t)c;
+    S.q.resize(nc);
+    double warp_time = 0, longest = 0;
+    for (int c = 0; c < nc; ++c) {
+        const int lg = cls[c].log2g;
+        for (int32_t id : order.at[lg])
+            if (cls_of[(size_t)id] == c) S.q[c].push_back(cost(lg, id));
+        double sum = 0;
+        for (double v : S.q[c]) sum += v;
+        warp_time += sum * (double)(1 << lg) / 32.0;
+        if (!S.q[c].empty()) longest = std::max(longest, S.q[c].front());
+    }
+    const int sw = std::max(1, (int)std::lround(n_warps * scale));
+    int tot = 0;
+    for (int c = 0; c < nc; ++c) tot += cls[c].warps;
+    for (int c = 0; c < nc; ++c) {
+        int k = tot > 0 ? (int)std::lround((double)cls[c].warps * sw / tot) : 0;
+        if (cls[c].warps > 0 && k == 0) k = 1;
+        for (int w = 0; w < k; ++w) S.start.push_back(c);
+    }
+    if (S.start.empty()) S.start.push_back(0);
+    // the average load per warp, less a margin for rounding
+    S.lower = std::max(longest, warp_time / (double)S.start.size() * (1.0 - 1e-9));
+    return S;
+}
 
 // Longest-first schedule of every class on its warps' groups, over a sample
 // of the pairs (with the warp count scaled by the same factor); returns the
 // time the last warp finishes (in wavefront steps).
-double simulate(const Costs &cost, const std::vector<PlannedClass> &cls, int n_warps,
-                const std::vector<char> &sampled, double scale) {
+double simulate(const SimSetup &S, const std::vector<PlannedClass> &cls) {
     const int nc = (int)cls.size();
     if (nc == 0) return 0;
-    std::vector<std::vector<double>> q(nc);
-    for (int c = 0; c < nc; ++c) {
-        for (int32_t id : cls[c].pairs)
-            if (sampled[(size_t)id]) q[c].push_back(cost(cls[c].log2g, id));
-        std::sort(q[c].begin(), q[c].end(), std::greater<double>());
-    }
-    int sw = std::max(1, (int)std::lround(n_warps * scale));
-    std::vector<int> start;
-    {
-        int tot = 0;
-        for (int c = 0; c < nc; ++c) tot += cls[c].warps;
-        for (int c = 0; c < nc; ++c) {
-            int k = tot > 0 ? (int)std::lround((double)cls[c].warps * sw / tot) : 0;
-            if (cls[c].warps > 0 && k == 0) k = 1;
-            for (int w = 0; w < k; ++w) start.push_back(c);
-        }
-        if (start.empty()) start.push_back(0);
-    }
-    sw = (int)start.size();
+    const std::vector<std::vector<double>> &q = S.q;
+    const std::vector<int> &start = S.start;
+    const int sw = (int)start.size();
     // An event is k idle groups of warp w, free from time t, on the warp's
     // v-th class visit: one entry stands for all of a warp's groups that
     // fall idle together, so a warp costs one entry, not one per group.
@@ -248,21 +289,47 @@ std::vector<PlannedClass> plan_classes(const std::vector<PlanPair> &pairs, int n
     size_t n_sampled = 0;
     for (size_t k = 0; k < pairs.size(); k += step, ++n_sampled) sampled[k] = 1;
     const double scale = (double)n_sampled / (double)pairs.size();
-    Candidate best;
-    bool have = false;
-    for (int gn = kMinLog2G; gn <= 3; ++gn) {
+    const SampleOrder order = sample_order(cost, sampled);
+    // Candidates in a fixed order; the plan is the one with the smallest
+    // simulated makespan, the earliest in that order among equals.  They
+    // are simulated in order of their lower bounds, and one whose bound
+    // already exceeds the best makespan found (or equals it, coming later
+    // in the order) is not simulated: it could not be chosen.
+    struct Cand {
+        std::vector<PlannedClass> classes;
+        SimSetup setup;
+        int idx;
+    };
+    std::vector<Cand> cands;
+    for (int gn = kMinLog2G; gn <= 3; ++gn)
         for (double frac : {0.25, 0.5, 1.0}) {
-            Candidate c;
+            Cand c;
             c.classes = build(pairs, cost, n_warps, gn, frac, half_tails, rows);
-            c.makespan = simulate(cost, c.classes, n_warps, sampled, scale);
-            if (!have || c.makespan < best.makespan) {
-                best = std::move(c);
-                have = true;
-            }
+            c.setup = sim_setup(cost, c.classes, n_warps, order, pairs.size(), scale);
+            c.idx = (int)cands.size();
+            cands.push_back(std::move(c));
+        }
+    std::vector<int> by_bound(cands.size());
+    for (size_t k = 0; k < cands.size(); ++k) by_bound[k] = (int)k;
+    std::sort(by_bound.begin(), by_bound.end(), [&](int a, int b) {
+        return cands[a].setup.lower < cands[b].setup.lower ||
+               (cands[a].setup.lower == cands[b].setup.lower && a < b);
+    });
+    int best = -1;
+    double best_ms = 0;
+    for (int k : by_bound) {
+        const Cand &c = cands[k];
+        if (best >= 0 && (c.setup.lower > best_ms || (c.setup.lower == best_ms && c.idx > best)))
+            continue;
+        const double ms = simulate(c.setup, c.classes);
+        if (best < 0 || ms < best_ms || (ms == best_ms && c.idx < best)) {
+            best = c.idx;
+            best_ms = ms;
         }
     }
-    sort_classes(best.classes, cost);
-    return best.classes;
+    std::vector<PlannedClass> chosen = std::move(cands[(size_t)best].classes);
+    sort_classes(chosen, cost);
+    return chosen;
 }
 
 }  // namespace swgb
