@@ -107,12 +107,34 @@ def oracle_rate(batch, n_pairs: int, threads: int, gpu_res=None, cols: int = 5) 
     out = {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
            "sample": f"first {n_pairs} pairs of {batch.name} ({cells / 1e9:.3f} G forward cells), "
                      f"{dt:.2f} s on {threads} host threads",
-           "seconds": dt}
+           "seconds": dt, "pairs": n_pairs}
     if gpu_res is not None:
         a, b = ref[:, :cols], gpu_res[:n_pairs, :cols]
         out["gpu_identical_pairs"] = int(np.sum(np.all(a == b, axis=1)))
         out["gpu_identical"] = bool(np.array_equal(a, b))
     return out
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def single_core_rate(batch, multi: dict, target_s: float = 2.0) -> dict:
+    """The oracle on one host thread, over the first pairs of the workload
+    (about target_s seconds, sized from the multi-threaded run)."""
+    per_pair_1 = multi["seconds"] * multi["cores"] / max(1, multi["pairs"])
+    n1 = int(max(50, min(multi["pairs"], target_s / max(per_pair_1, 1e-9))))
+    r = oracle_rate(batch, n1, 1)
+    return {"value": r["value"], "unit": "GCUPS", "cores": 1, "sample": r["sample"]}
 
 
 def auto_cpu_pairs(batch, threads: int, target_s: float = 12.0) -> int:
@@ -202,7 +224,8 @@ def run_reference(args, rank):
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": batch.name, "pairs_per_step": n, "threads": threads},
             "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads, "kind": "oracle",
-                             "sample": f"first {n} pairs of {batch.name} per step"},
+                             "sample": f"first {n} pairs of {batch.name} per step",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -578,7 +601,10 @@ def run_ours(args, rank, world, local):
         threads = cpu_cores()
         n = args.cpu_pairs or auto_cpu_pairs(batch, threads)
         cpu = oracle_rate(batch, n, threads, gpu_res=res, cols=3 if args.ends_only else 5)
+        cpu["single_core"] = single_core_rate(batch, cpu)
+        cpu["cpu_model"] = cpu_model()
         cpu.pop("seconds")
+        cpu.pop("pairs")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,

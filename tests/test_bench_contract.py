@@ -43,7 +43,7 @@ def test_reference_arm_line():
     assert d["config"]["workload"] == "dna-1k" and d["config"]["pairs_per_step"] == 120
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
-    assert "120" in cb["sample"]
+    assert "120" in cb["sample"] and cb["cpu_model"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == "GCUPS"
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
@@ -95,3 +95,15 @@ def test_roofline_traffic_only_for_the_captured_plan(bench_mod):
     assert bench_mod.profiled_traffic(b, {"narrow_log2g": -1, "cap_fraction": 0.5}, "s16x2",
                                       swgb.SW_PLAN_ENDS_ONLY, 152) is None
     assert bench_mod.profiled_traffic(b, None, "s16x2", 0, 152) is None
+
+
+def test_single_core_oracle_rate(bench_mod):
+    """The CPU baseline's single-thread figure: the oracle on one thread over
+    a sample sized from the multi-threaded run."""
+    import workloads as wl
+    b = wl.gen_config(0)
+    multi = bench_mod.oracle_rate(b, 60, 2)
+    one = bench_mod.single_core_rate(b, multi, target_s=0.2)
+    assert one["cores"] == 1 and one["unit"] == "GCUPS" and one["value"] > 0
+    assert "1 host threads" in one["sample"]
+    assert isinstance(bench_mod.cpu_model(), str) and bench_mod.cpu_model()
