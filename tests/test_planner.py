@@ -138,3 +138,27 @@ def test_preview_rejects_bad_arguments(lib):
         preview(lib, b, narrow_log2g=6)
     with pytest.raises(lib.SwError):
         lib.sw_plan_preview(b.q_offsets, b.r_offsets, b.matrix, 0, -1)
+
+
+def test_default_plans_take_the_measured_best_widths(lib):
+    """Without autotuning, the planner's own choice (its simulated schedule,
+    with each strip start charged to the whole warp) lands where measurement
+    on a GB300 put the best plans: on the 100k DNA workload 8-lane bulk groups
+    with 4-lane tails (2,228 GCUPS, against 1,995 for the all-2-lane plan the
+    planner chose without the strip charge), on the 20k protein workload
+    8-lane groups (1,922), and on the 200k skewed DNA workload 8- and 4-lane
+    groups (2,073).  A change to the cost model that moves these plans must
+    be re-measured."""
+    sms = 152
+    b1 = wl.gen_config(1)
+    _, lg, _ = preview(lib, b1, sm_count=sms)
+    h = np.bincount(lg[lg >= 0], minlength=6)
+    assert h[3] >= 0.4 * b1.n_pairs and h[2] + h[3] == b1.n_pairs, h.tolist()
+    b2 = wl.gen_config(2)
+    _, lg, _ = preview(lib, b2, sm_count=sms)
+    h = np.bincount(lg[lg >= 0], minlength=6)
+    assert h[3] >= 0.95 * b2.n_pairs and h[1] == h[2] == 0, h.tolist()
+    b3 = wl.gen_config(3)
+    _, lg, _ = preview(lib, b3, sm_count=sms)
+    h = np.bincount(lg[lg >= 0], minlength=6)
+    assert h[2] + h[3] >= 0.99 * b3.n_pairs and h[1] == 0, h.tolist()
