@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--cigar", action="store_true",
                     help="also time the traceback (CIGAR) of every aligned pair")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the secondary workloads (1,000 DNA, 20k protein, 200k skewed DNA)")
+    ap.add_argument("--config-steps", type=int, default=6,
+                    help="timed steps of each secondary workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the planner's own lane-group choice instead of measuring candidates")
     ap.add_argument("--tune-cache", default=os.path.join(ROOT, ".swgb_tune_cache.json"))
@@ -420,6 +424,122 @@ def time_plan(swgb, torch, plan, q, r, out, stream, steps, warmup, flush):
     return [a.elapsed_time(b) * 1e-3 for a, b in ev]
 
 
+def nominal_peak(sms: int, mhz: float | None, lanes_per_clk: int = 64) -> float | None:
+    """Integer ALU lane-instructions per second (T/s) of the whole device at
+    the sampled clock: lanes_per_clk per SM (64 = 4 sub-partitions x 16
+    lanes of the ALU pipe that issues the max forms)."""
+    return lanes_per_clk * sms * mhz * 1e6 / 1e12 if mhz else None
+
+
+def roofline_fracs(ops_per_cell: int, max_ops_per_cell: int, cells_total: int, seconds: float,
+                   sms: int, mhz: float | None) -> dict:
+    """The alternative roofline fractions beside the measured-peak one:
+    frac_nominal against 64 lanes/clk/SM at the sampled clock, frac_survey_128
+    against 128 lanes/clk/SM, frac_max_only counting only the max-type
+    algorithmic ops per cell (E, F, the three-way H max, the end key; the two
+    adds issue on the FMA pipe) against 64 lanes/clk/SM."""
+    nom = nominal_peak(sms, mhz)
+    s128 = nominal_peak(sms, mhz, 128)
+    ach = ops_per_cell * cells_total / seconds / 1e12
+    ach_max = max_ops_per_cell * cells_total / seconds / 1e12
+    return {"frac_nominal": ach / nom if nom else None,
+            "frac_survey_128": ach / s128 if s128 else None,
+            "frac_max_only": ach_max / nom if nom else None,
+            "peak_nominal": nom, "max_ops_per_cell": max_ops_per_cell}
+
+
+def time_one_shot(swgb, torch, batch, dev, stream, steps, warmup):
+    """End to end through sw_align_batch: every step copies the sequences and
+    offsets from page-locked host buffers to the device, plans on the device
+    (no offset read-back, no host planning), runs both passes and copies the
+    five result rows back; host-timed, synchronised at the end of each step."""
+    qh = torch.from_numpy(batch.q_seqs).pin_memory()
+    rh = torch.from_numpy(batch.r_seqs).pin_memory()
+    qoh = torch.from_numpy(batch.q_offsets).pin_memory()
+    roh = torch.from_numpy(batch.r_offsets).pin_memory()
+    q = torch.empty_like(qh, device=dev)
+    r = torch.empty_like(rh, device=dev)
+    qo = torch.empty_like(qoh, device=dev)
+    ro = torch.empty_like(roh, device=dev)
+    out = torch.empty((5, batch.n_pairs), dtype=torch.int32, device=dev)
+    oh = torch.empty((5, batch.n_pairs), dtype=torch.int32).pin_memory()
+
+    def step():
+        with torch.cuda.stream(stream):
+            q.copy_(qh, non_blocking=True)
+            r.copy_(rh, non_blocking=True)
+            qo.copy_(qoh, non_blocking=True)
+            ro.copy_(roh, non_blocking=True)
+            swgb.sw_align_batch(q, qo, r, ro, batch.matrix, batch.gap_open, batch.gap_extend,
+                                out, stream)
+            oh.copy_(out, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    h2d = int(qh.numel() + rh.numel() + 8 * (qoh.numel() + roh.numel()))
+    return dt, oh.numpy().T.copy(), h2d, int(oh.numel() * 4)
+
+
+def measure_config(swgb, torch, ctx, k, dev, stream, flush, steps, tune_cache, sms):
+    """Secondary workload k: the batched form (autotuned, CUDA graph), the
+    plain one-block-per-pair form, the roofline fractions, the clocks of the
+    timed region and the whole workload compared with the oracle."""
+    import oracle
+    batch = wl.gen_config(k)
+    q = torch.from_numpy(batch.q_seqs).to(dev)
+    r = torch.from_numpy(batch.r_seqs).to(dev)
+    out = torch.zeros((5, batch.n_pairs), dtype=torch.int32, device=dev)
+    tune = swgb.sw_autotune(ctx, batch.q_offsets, batch.r_offsets, batch.matrix, batch.gap_open,
+                            batch.gap_extend, q, r, out, cache_path=tune_cache, stream=stream)
+    plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                               batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED,
+                               swgb.SW_PLAN_GRAPH)
+    info = swgb.sw_plan_info(plan)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    times = time_plan(swgb, torch, plan, q, r, out, stream, steps, 3, flush)
+    clk = clocks.stop()
+    swgb.sw_plan_destroy(plan)
+    res = out.T.contiguous().cpu().numpy()
+    t = sum(times) / len(times)
+    cells = batch.cells
+    rcells = reverse_cells(res)
+    packed16 = info["arith"] == "s16x2"
+    opc = OPS_PER_CELL // 2 if packed16 else OPS_PER_CELL
+    pplan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
+                                batch.gap_open, batch.gap_extend, swgb.SW_MODE_PLAIN, 0)
+    out2 = torch.zeros_like(out)
+    pt = time_plan(swgb, torch, pplan, q, r, out2, stream, max(2, steps // 2), 1, flush)
+    swgb.sw_plan_destroy(pplan)
+    plain_same = bool(torch.equal(out, out2))
+    threads = cpu_cores()
+    t0 = time.perf_counter()
+    ref = oracle.align_workload(batch, threads=threads)
+    odt = time.perf_counter() - t0
+    same = np.all(ref == res, axis=1)
+    v = cells / t / 1e9
+    pv = cells * len(pt) / sum(pt) / 1e9
+    mb_rate, _ = swgb.sw_microbench_int("viaddmax_s16x2" if packed16 else "viaddmax_s32",
+                                        dev.index, 2048)
+    entry = {"workload": batch.name, "pairs": batch.n_pairs, "forward_cells": cells,
+             "reverse_cells": rcells, "arith": info["arith"], "tuning": tune,
+             "batched_gcups": v, "ms_per_step": t * 1e3, "steps": len(times),
+             "plain_gcups": pv, "plain_identical_outputs": plain_same,
+             "batched_over_plain": v / pv,
+             "frac": opc * (cells + rcells) / t / mb_rate if mb_rate else None,
+             "oracle_identical_pairs": int(same.sum()), "oracle_identical": bool(same.all()),
+             "oracle_gcups": cells / odt / 1e9, "oracle_threads": threads, "clocks": clk}
+    entry.update(roofline_fracs(opc, 2 if packed16 else 4, cells + rcells, t, sms,
+                                clk.get("sm_mhz")))
+    return entry
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2208_12350_gb300 as swgb
@@ -512,13 +632,15 @@ def run_ours(args, rank, world, local):
     peak_op = "viaddmax_s16x2" if packed16 else "viaddmax_s32"
     ops = ops_per_cell * (cells + rcells)
     achieved = ops / per_launch / 1e12
+    sm_mhz = clk.get("sm_mhz")
     mb_rate, _ = swgb.sw_microbench_int(peak_op, local, 2048)
     peak_measured = mb_rate / 1e12
-    sm_mhz = clk.get("sm_mhz")
     traffic = profiled_traffic(batch, tune, info["arith"], flags, sms) \
         if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
             "frac": achieved / peak_measured if peak_measured else None, "traffic": traffic,
+            **roofline_fracs(ops_per_cell, 2 if packed16 else 4, cells + rcells, per_launch,
+                             sms, sm_mhz),
             "peak_kind": f"measured __{peak_op} issue rate, whole device, this run",
             "ops_per_cell": ops_per_cell, "cells_forward": cells, "cells_reverse": rcells,
             "traffic_unit": "DRAM bytes per launch (ncu, committed summary)",
@@ -563,6 +685,19 @@ def run_ours(args, rank, world, local):
 
     swgb.sw_plan_destroy(plan)
 
+    # --- end to end through the one-shot call, planning on the device inside
+    # the timed region (fresh offsets uploaded every step)
+    e2e_oneshot = None
+    if not (args.packed or args.ends_only or args.no_s16x2 or world > 1):
+        ot, ores, oh2d, od2h = time_one_shot(swgb, torch, batch, dev, stream, args.steps,
+                                             args.warmup)
+        e2e_oneshot = {"value": job_cells * args.steps / ot / 1e9, "unit": "GCUPS",
+                       "ms_per_step": ot / args.steps * 1e3,
+                       "h2d_bytes_per_step": oh2d, "d2h_bytes_per_step": od2h,
+                       "identical_outputs": bool(np.array_equal(ores, res)),
+                       "call": "sw_align_batch (device offsets; planned on the device)",
+                       "inputs": "page-locked host buffers copied to the device each step"}
+
     cigar = None
     if args.cigar and not args.ends_only:
         # traceback of every aligned pair: cells = the spans' global DP
@@ -586,8 +721,15 @@ def run_ours(args, rank, world, local):
                  "ops": int(nops.sum().item()),
                  "note": "host-timed blocking call incl. scratch allocation"}
 
-    serve = None
     overridden = bool(args.gaps or args.dna_scores or args.ends_only or args.pairs or args.packed)
+    configs = None
+    if not args.no_configs and rank == 0 and world == 1 and not overridden and args.config == 1:
+        configs = {}
+        for k in (0, 2, 3):
+            configs[str(k)] = measure_config(swgb, torch, ctx, k, dev, stream, flush,
+                                             args.config_steps, args.tune_cache, sms)
+
+    serve = None
     if not args.no_serve and rank == 0 and world == 1 and not overridden:
         if args.config == 1:
             serve = serve_sweep(swgb, ctx, batch, res, args)
@@ -622,7 +764,8 @@ def run_ours(args, rank, world, local):
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serve": serve, "cigar": cigar,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_oneshot": e2e_oneshot,
+                "configs": configs, "serve": serve, "cigar": cigar,
                 "clocks": clk,
                 "gpu_launches": info["launches"] * args.steps}
         print(json.dumps(line), flush=True)

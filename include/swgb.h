@@ -99,6 +99,15 @@ typedef enum {
  * or k = 4 (a byte profile; also smax - gap_open <= 31); the results are
  * the same either way (sw_plan_arith says which form a plan took). */
 #define SW_PLAN_NO_S16X2 8u
+/* Strip-boundary scratch per pair instead of per lane group.  A pair whose
+ * query or reference spans more than one row strip passes each strip's last
+ * row to the next strip through global memory.  By default each lane group
+ * of the batched kernel owns one slot of such words, sized for the batch's
+ * largest need, and reuses it for every pair it aligns, so the words a
+ * launch touches stay few and mostly in L2.  With this flag every such pair
+ * gets words of its own (less memory for small batches of long pairs, more
+ * DRAM traffic). */
+#define SW_PLAN_PAIR_SCRATCH 16u
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_plan sw_plan;
@@ -124,8 +133,15 @@ int sw_ctx_host_in_place(const sw_ctx *ctx, int32_t *yes);
 
 /* Synchronise the context's device, return its device status word in
  * *status (0 = no inconsistency detected by any kernel; bit 0 = a reverse
- * pass did not reproduce its forward score) and clear it. */
+ * pass did not reproduce its forward score; bit 1 = a one-shot call met
+ * device offsets that were negative, decreasing or more than SW_MAX_LEN
+ * apart, and gave those pairs the "no alignment" outputs) and clear it. */
 int sw_ctx_status(sw_ctx *ctx, int32_t *status);
+
+/* The context sw_align_batch uses on `device` (created on first use, owned
+ * by the library until the process exits: do not destroy it).  Its status
+ * word reports on sw_align_batch's work (sw_ctx_status). */
+int sw_default_ctx(int32_t device, sw_ctx **out);
 
 /* Batched-path tuning for plans created afterwards.  narrow_log2g = -1
  * (default): the planner chooses the lane-group width of the bulk of the
@@ -255,11 +271,32 @@ int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
 
 /*
  * One-shot alignment of a batch whose sequences AND offsets are on the
- * DEVICE (score_matrix on the HOST).  Reads the offsets back to plan the
- * batch, which synchronises `stream` once, then enqueues the work on
- * `stream` and returns; the temporary plan is released when the work is
- * done.  Uses a per-device default context.  For repeated batches of the
- * same shape, plan once with sw_plan_create and call sw_plan_execute.
+ * DEVICE (score_matrix on the HOST): the forward and reverse passes of
+ * every pair, as ADEPT's batch call (Section III-B), planned on the device.
+ *
+ * Asynchronous: the call checks its arguments, enqueues everything on
+ * `stream` and returns SW_OK without waiting for the device or reading
+ * anything back.  The kernels it enqueues read the offsets, give every pair
+ * its route and lane-group width (the same rules and cost model as
+ * sw_plan_create's planner, with the bulk width and cap of the context's
+ * tuning, else 8 lanes and half the mean load, instead of its simulated
+ * candidate search), sort the pairs longest first per width with a radix
+ * sort, build the queue tables and run the alignment kernels.  Device
+ * offsets that are negative, decreasing or more than SW_MAX_LEN apart give
+ * the pair the "no alignment" outputs and set bit 1 of the context's status
+ * word (sw_ctx_status; for sw_align_batch, the context sw_default_ctx
+ * returns).
+ *
+ * Workspace: tables and sort buffers of about 52 bytes per pair plus the
+ * strip-boundary slots of the lane groups (1028 words per lane, about 240 MB
+ * on a GB300), taken stream-ordered from a memory pool of the context that
+ * keeps freed memory for later calls; a pair whose longer sequence has
+ * more than about 16,400 residues (beyond the widest group's slot) takes
+ * the plain kernel.  Calls on different streams may overlap.  For repeated batches of
+ * one shape, sw_plan_create + sw_plan_execute plan once on the host.
+ * Errors (host-side, before anything is enqueued): SW_EINVAL for NULL
+ * pointers, n_pairs < 0, a bad alphabet size, gaps or mode; SW_ENOMEM when
+ * the workspace cannot be had; SW_ECUDA.
  */
 int sw_align_batch(const uint8_t *q_seqs, const int64_t *q_offsets,
                    const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
@@ -269,7 +306,9 @@ int sw_align_batch(const uint8_t *q_seqs, const int64_t *q_offsets,
                    int32_t *out_qstart, int32_t *out_rstart, void *stream);
 
 /*
- * As sw_align_batch with an explicit context and mode (sw_mode).
+ * As sw_align_batch with an explicit context (its tuning, status word and
+ * workspace pool) and mode (sw_mode; SW_MODE_PLAIN sends every pair to the
+ * one-block-per-pair kernel).
  */
 int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
                       const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
@@ -308,12 +347,16 @@ int sw_check_residues(const uint8_t *seqs, int64_t n, int32_t alphabet_size,
  * either is rejected with SW_ERANGE before anything is enqueued (split it).
  *
  * The first call on a device resolves the array's device address on that
- * device; make that first call before capturing any stream on the device.
- * Every call uses the same array (it keeps the previous call's contents and
- * clears what must start at zero), so calls whose GPU work overlaps - on
- * different streams or threads - race with each other: order them, e.g. on
- * one stream.  The work is enqueued on `stream` and the call returns;
- * the host arrays may be reused once it has returned.
+ * device and keeps it for the life of the process; after cudaDeviceReset
+ * (or from another CUDA context on that device) the kept address is no
+ * longer valid, so use this entry point only from the context that made the
+ * first call.  Every call uses the same array (it keeps the previous call's
+ * contents and clears what must start at zero), so calls whose GPU work
+ * overlaps - on different streams or threads - race with each other: order
+ * them, e.g. on one stream.  The work is enqueued on `stream` and the call
+ * returns; the host arrays may be reused once it has returned.  The call
+ * copies its pair tables from host memory it frees on return, so it cannot
+ * be captured into a CUDA graph: on a capturing stream it returns SW_EINVAL.
  */
 #define SW_STATIC_MAX_PAIRS 65536
 #define SW_STATIC_MAX_BOUNDARY_WORDS (8 << 20)
@@ -323,6 +366,14 @@ int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_offsets,
                           int32_t gap_open, int32_t gap_extend,
                           int32_t *out_score, int32_t *out_qend, int32_t *out_rend,
                           int32_t *out_qstart, int32_t *out_rstart, void *stream);
+
+/* Status word of sw_align_batch_static's kernels (bit 0 = a reverse pass
+ * did not reproduce its forward score; 0 = no inconsistency), collected
+ * over every call since it was last read: waits for `stream`, copies the
+ * word from the fixed module array into *status (a HOST word) and clears it
+ * on `stream`.  Allocates nothing.  Call it on the stream of the calls it
+ * reports on. */
+int sw_static_status(int32_t *status, void *stream);
 
 /*
  * Serving: continuous batching of alignment requests (one device, blocking

@@ -26,6 +26,7 @@ SW_PLAN_GRAPH = 1
 SW_PLAN_ENDS_ONLY = 2
 SW_PLAN_PACKED_2BIT = 4
 SW_PLAN_NO_S16X2 = 8
+SW_PLAN_PAIR_SCRATCH = 16
 SW_ARITH_S32, SW_ARITH_S16X2 = 0, 1
 SW_MAX_LEN = 65535
 
@@ -39,6 +40,7 @@ SIGNATURES = {
     "sw_ctx_destroy": ([_P], ctypes.c_int),
     "sw_ctx_sm_count": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_status": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_default_ctx": ([_I32, _PP], ctypes.c_int),
     "sw_ctx_host_in_place": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
     "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
@@ -55,6 +57,7 @@ SIGNATURES = {
     "sw_align_batch_ex": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P,
                            _P, _P], ctypes.c_int),
     "sw_check_residues": ([_P, _I64, _I32, _P, _P], ctypes.c_int),
+    "sw_static_status": ([ctypes.POINTER(_I32), _P], ctypes.c_int),
     "sw_align_batch_static": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
                               ctypes.c_int),
     "sw_autotune": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, ctypes.c_char_p, _P,
@@ -164,6 +167,17 @@ def sw_ctx_status(ctx: int) -> int:
     v = _I32()
     _check(load().sw_ctx_status(ctx, ctypes.byref(v)), "sw_ctx_status")
     return v.value
+
+
+def sw_default_ctx(device: int = 0) -> int:
+    """The library-owned context sw_align_batch uses on `device` (never destroy it)."""
+    h = ctypes.c_void_p()
+    _check(load().sw_default_ctx(device, ctypes.byref(h)), "sw_default_ctx")
+    return h.value
+
+
+STATUS_REVERSE_MISMATCH = 1
+STATUS_BAD_OFFSETS = 2
 
 
 def sw_ctx_set_tuning(ctx: int, narrow_log2g: int = -1, cap_fraction: float = 0.5) -> None:
@@ -304,6 +318,13 @@ def sw_align_batch_static(q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, ga
                                         mat.shape[0], gap_open, gap_extend,
                                         *[_addr(o) for o in outs], _stream(stream)),
            "sw_align_batch_static")
+
+
+def sw_static_status(stream=None) -> int:
+    """Status word of sw_align_batch_static's kernels on `stream` (read and cleared)."""
+    v = _I32()
+    _check(load().sw_static_status(ctypes.byref(v), _stream(stream)), "sw_static_status")
+    return v.value
 
 
 def sw_check_residues(seqs, n: int, alphabet_size: int, bad_count, stream=None) -> None:

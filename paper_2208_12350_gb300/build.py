@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libswgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "kernel_group.cu", "kernel_plain.cu", "microbench.cu", "plan.cpp", "static_scratch.cu", "autotune.cpp",
+SOURCES = ["api.cu", "device_plan.cu", "kernel_group.cu", "kernel_plain.cu", "microbench.cu", "plan.cpp", "static_scratch.cu", "autotune.cpp",
            "host_plan.cpp", "serve.cpp", "cigar.cu", "packed.cu"]
 
 

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "device_plan.h"
 #include "sw_internal.h"
 #include "swgb.h"
 
@@ -84,6 +85,9 @@ struct sw_ctx {
     bool host_in_place = false;
     std::mutex mu;
     std::vector<std::pair<sw_plan *, cudaEvent_t>> retired;
+    // stream-ordered workspaces of the one-shot calls (created on first use;
+    // keeps freed memory for the next call instead of returning it)
+    cudaMemPool_t pool = nullptr;
 };
 
 namespace swgb {
@@ -193,6 +197,8 @@ int sw_ctx_destroy(sw_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaFree(ctx->d_status);
+        // outstanding one-shot workspaces are released when their frees complete
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
     return SW_OK;
@@ -235,7 +241,8 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     std::string msg;
     int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
                             gap_extend, mode, ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
-                            &p->hp, &msg, 1, 8192, (flags & SW_PLAN_NO_S16X2) == 0);
+                            &p->hp, &msg, 1, 8192, (flags & SW_PLAN_NO_S16X2) == 0,
+                            group_blocks_per_sm, (flags & SW_PLAN_PAIR_SCRATCH) == 0);
     if (rc != SW_OK) {
         delete p;
         return fail(rc, "sw_plan_create: %s", msg.c_str());
@@ -428,6 +435,29 @@ int sw_plan_destroy(sw_plan *p) {
     return SW_OK;
 }
 
+// The context's pool of one-shot workspaces (created on first use).
+static int ctx_pool(sw_ctx *ctx, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->pool) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        cudaMemPool_t pool = nullptr;
+        SW_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = UINT64_MAX;
+        const cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return fail(SW_ECUDA, "cudaMemPoolSetAttribute: %s", cudaGetErrorString(e));
+        }
+        ctx->pool = pool;
+    }
+    *out = ctx->pool;
+    return SW_OK;
+}
+
 int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
                       const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
                       const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
@@ -438,39 +468,63 @@ int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offse
     if (n_pairs < 0) return fail(SW_EINVAL, "sw_align_batch_ex: n_pairs < 0");
     if (n_pairs == 0) return SW_OK;
     if (!q_offsets || !r_offsets) return fail(SW_EINVAL, "sw_align_batch_ex: offsets are NULL");
+    if (!q_seqs || !r_seqs || !out_score || !out_qend || !out_rend || !out_qstart || !out_rstart)
+        return fail(SW_EINVAL, "sw_align_batch_ex: NULL device pointer");
+    if (!score_matrix) return fail(SW_EINVAL, "sw_align_batch_ex: score_matrix is NULL");
+    if (alphabet_size < 1 || alphabet_size > SW_MAX_ALPHABET)
+        return fail(SW_EINVAL, "sw_align_batch_ex: alphabet_size %d not in [1, %d]", alphabet_size,
+                    SW_MAX_ALPHABET);
+    if (gap_extend > 0 || gap_open > gap_extend || gap_open < -SW_MAX_GAP)
+        return fail(SW_EINVAL, "sw_align_batch_ex: need -%d <= gap_open <= gap_extend <= 0",
+                    SW_MAX_GAP);
+    if (mode != SW_MODE_AUTO && mode != SW_MODE_PLAIN && mode != SW_MODE_BATCHED)
+        return fail(SW_EINVAL, "sw_align_batch_ex: unknown mode %d", mode);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    reap_retired(ctx, false);
+    DevicePlanShape shape;
+    std::string msg;
+    int rc = device_plan_shape(n_pairs, score_matrix, alphabet_size, gap_open, gap_extend, mode,
+                               ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
+                               kOneShotSlotWords, &shape, &msg);
+    if (rc != SW_OK) return fail(rc, "sw_align_batch_ex: %s", msg.c_str());
+    cudaMemPool_t pool = nullptr;
+    if ((rc = ctx_pool(ctx, &pool)) != SW_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<int64_t> hq((size_t)n_pairs + 1), hr((size_t)n_pairs + 1);
-    SW_CUDA_TRY(cudaMemcpyAsync(hq.data(), q_offsets, hq.size() * sizeof(int64_t),
-                                cudaMemcpyDeviceToHost, s));
-    SW_CUDA_TRY(cudaMemcpyAsync(hr.data(), r_offsets, hr.size() * sizeof(int64_t),
-                                cudaMemcpyDeviceToHost, s));
-    SW_CUDA_TRY(cudaStreamSynchronize(s));
-    sw_plan *p = nullptr;
-    int rc = sw_plan_create(ctx, hq.data(), hr.data(), n_pairs, score_matrix, alphabet_size,
-                            gap_open, gap_extend, mode, 0u, &p);
-    if (rc != SW_OK) return rc;
-    rc = sw_plan_execute(p, q_seqs, r_seqs, out_score, out_qend, out_rend, out_qstart,
-                         out_rstart, stream);
-    cudaEvent_t ev = nullptr;
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventRecord(ev, s) != cudaSuccess) {
+    void *ws = nullptr;
+    const size_t bytes = device_plan_workspace_bytes(shape);
+    if (cudaMallocFromPoolAsync(&ws, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
-        if (ev) cudaEventDestroy(ev);
-        cudaStreamSynchronize(s);
-        plan_free(p);
-        return rc != SW_OK ? rc : fail(SW_ECUDA, "sw_align_batch: event record failed");
+        return fail(SW_ENOMEM, "sw_align_batch_ex: workspace of %zu bytes", bytes);
     }
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        ctx->retired.emplace_back(p, ev);
-    }
-    return rc;
+    const Outputs o{out_score, out_qend, out_rend, out_qstart, out_rstart};
+    const cudaError_t e =
+        enqueue_device_plan(shape, ws, q_offsets, r_offsets, q_seqs, r_seqs, o, ctx->d_status, s);
+    // stream-ordered: released after the kernels that use it, also on failure
+    cudaFreeAsync(ws, s);
+    if (e != cudaSuccess) return fail(SW_ECUDA, "sw_align_batch_ex: %s", cudaGetErrorString(e));
+    return SW_OK;
 }
 
 static std::mutex g_default_mu;
 static std::vector<sw_ctx *> g_default_ctx;
+
+int sw_default_ctx(int32_t device, sw_ctx **out) {
+    if (!out) return fail(SW_EINVAL, "sw_default_ctx: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    SW_CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count)
+        return fail(SW_EINVAL, "sw_default_ctx: device %d not in [0, %d)", device, count);
+    std::lock_guard<std::mutex> lk(g_default_mu);
+    if ((int)g_default_ctx.size() <= device) g_default_ctx.resize(device + 1, nullptr);
+    if (!g_default_ctx[device]) {
+        const int rc = sw_ctx_create(device, &g_default_ctx[device]);
+        if (rc != SW_OK) return rc;
+    }
+    *out = g_default_ctx[device];
+    return SW_OK;
+}
 
 int sw_align_batch(const uint8_t *q_seqs, const int64_t *q_offsets, const uint8_t *r_seqs,
                    const int64_t *r_offsets, int32_t n_pairs, const int8_t *score_matrix,
@@ -480,15 +534,8 @@ int sw_align_batch(const uint8_t *q_seqs, const int64_t *q_offsets, const uint8_
     int dev = 0;
     SW_CUDA_TRY(cudaGetDevice(&dev));
     sw_ctx *ctx = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_default_mu);
-        if ((int)g_default_ctx.size() <= dev) g_default_ctx.resize(dev + 1, nullptr);
-        if (!g_default_ctx[dev]) {
-            const int rc = sw_ctx_create(dev, &g_default_ctx[dev]);
-            if (rc != SW_OK) return rc;
-        }
-        ctx = g_default_ctx[dev];
-    }
+    const int rc = sw_default_ctx(dev, &ctx);
+    if (rc != SW_OK) return rc;
     return sw_align_batch_ex(ctx, q_seqs, q_offsets, r_seqs, r_offsets, n_pairs, score_matrix,
                              alphabet_size, gap_open, gap_extend, SW_MODE_AUTO, out_score,
                              out_qend, out_rend, out_qstart, out_rstart, stream);

@@ -141,7 +141,7 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
         return set_error(SW_EINVAL, "sw_autotune: bad argument");
     // the candidates run the kernels the timed plans will run: the same
     // arithmetic form and passes (the inputs here are one byte per residue)
-    flags &= SW_PLAN_ENDS_ONLY | SW_PLAN_NO_S16X2;
+    flags &= SW_PLAN_ENDS_ONLY | SW_PLAN_NO_S16X2 | SW_PLAN_PAIR_SCRATCH;
     char gpu[256];
     int32_t sms = 0;
     sw_ctx_sm_count(ctx, &sms);

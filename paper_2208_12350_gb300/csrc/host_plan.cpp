@@ -77,7 +77,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp, int sample_cap,
-                   bool allow_packed, BlocksPerSmFn blocks_per_sm) {
+                   bool allow_packed, BlocksPerSmFn blocks_per_sm, bool group_slots) {
     *out = HostPlan();
     int rc = check_batch(q_offsets, r_offsets, n_pairs, mat, A, go, ge, nullptr, nullptr,
                          nullptr, msg);
@@ -180,15 +180,23 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         for (int32_t k : pc.pairs) {
             const int32_t i = gid[k];
             PairInfo pi{q_offsets[i], r_offsets[i], -1, n[i], m[i], i, 0};
-            const int64_t w =
-                n[i] > 0 && m[i] > 0 ? pair_scratch_words(n[i], m[i], G, rows_of(out->kind)) : 0;
-            if (w > 0) {
-                pi.scratch = out->scratch_words;
-                out->scratch_words += w;
+            if (n[i] > 0 && m[i] > 0) {
+                if (group_slots) {
+                    out->slot_words = std::max(out->slot_words,
+                                               pair_slot_words(n[i], m[i], G, rows_of(out->kind)));
+                } else {
+                    const int64_t w = pair_scratch_words(n[i], m[i], G, rows_of(out->kind));
+                    if (w > 0) {
+                        pi.scratch = out->scratch_words;
+                        out->scratch_words += w;
+                    }
+                }
             }
             out->pairs.push_back(pi);
         }
     }
+    // one slot per lane of every warp of the launch
+    if (group_slots) out->scratch_words = (int64_t)out->n_warps * 32 * out->slot_words;
     if (!out->plain.empty()) {
         if (plain_max_n <= 1024) {
             out->plain_threads = std::max(32, ((plain_max_n + 31) / 32) * 32);
@@ -218,6 +226,7 @@ cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_
         gp.counters = t.counters;
         gp.n_warps = hp.n_warps;
         gp.scratch = t.scratch;
+        gp.slot_words = hp.slot_words;
         gp.status = t.status;
         gp.out = o;
         gp.alphabet = A;

@@ -621,7 +621,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                     live = true;
                     rev = false;
                     cold.id[t] = pi.id;
-                    cold.bnd[t] = p.scratch + (pi.scratch >= 0 ? pi.scratch : 0);
+                    cold.bnd[t] =
+                        p.scratch + (p.slot_words > 0
+                                         ? ((size_t)wid * 32 + gbase) * (size_t)p.slot_words
+                                         : (size_t)(pi.scratch >= 0 ? pi.scratch : 0));
                     begin_sweep(p.q + pi.q, p.r + pi.r, pi.n, pi.m, 1);
                 }
             }

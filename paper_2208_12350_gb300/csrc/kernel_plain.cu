@@ -129,6 +129,10 @@ __device__ uint64_t plain_sweep(const uint8_t *a, int a_step, int n, const uint8
 }
 
 template <int KMAX>
+__device__ __forceinline__ void plain_pair(const PlainParams &p, const PairInfo &pi,
+                                           const int *smat, int *xH, int *xF, uint64_t *red);
+
+template <int KMAX>
 __global__ void __launch_bounds__(KMAX == 1 ? 1024 : kPlainWideThreads)
     sw_plain_kernel(const __grid_constant__ PlainParams p) {
     extern __shared__ __align__(16) int smem_plain[];
@@ -142,7 +146,20 @@ __global__ void __launch_bounds__(KMAX == 1 ? 1024 : kPlainWideThreads)
     for (int i = threadIdx.x; i < A * A; i += T) smat[i] = p.mat[i];
     __syncthreads();
 
-    const PairInfo pi = p.pairs[blockIdx.x];
+    int first = 0, count = p.n_pairs;
+    if (p.range) {
+        first = p.range[0];
+        count = p.range[1];
+    }
+    // block-uniform loop: every barrier inside is reached by the whole block
+    for (int b = blockIdx.x; b < count; b += gridDim.x)
+        plain_pair<KMAX>(p, p.pairs[first + b], smat, xH, xF, red);
+}
+
+template <int KMAX>
+__device__ __forceinline__ void plain_pair(const PlainParams &p, const PairInfo &pi,
+                                           const int *smat, int *xH, int *xF, uint64_t *red) {
+    const int A = p.alphabet;
     const uint8_t *q = p.q + pi.q;
     const uint8_t *r = p.r + pi.r;
     const uint64_t key = plain_sweep<KMAX>(q, 1, pi.n, r, 1, pi.m, smat, A, p.gap_open,
@@ -205,6 +222,18 @@ cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_
         sw_plain_kernel<1><<<p.n_pairs, threads, smem, s>>>(p);
     else
         sw_plain_kernel<kPlainMaxRows><<<p.n_pairs, kPlainWideThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_range(const PlainParams &p, int threads, int rows_per_thread_max,
+                               int grid, cudaStream_t s) {
+    if (grid <= 0) return cudaSuccess;
+    if (rows_per_thread_max <= 1) {
+        sw_plain_kernel<1><<<grid, threads, plain_smem_bytes(threads, p.alphabet), s>>>(p);
+    } else {
+        sw_plain_kernel<kPlainMaxRows>
+            <<<grid, kPlainWideThreads, plain_smem_bytes(kPlainWideThreads, p.alphabet), s>>>(p);
+    }
     return cudaGetLastError();
 }
 

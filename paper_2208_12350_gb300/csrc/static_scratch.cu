@@ -99,6 +99,16 @@ extern "C" int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_off
         return err(SW_EINVAL, "sw_align_batch_static: NULL pointer argument");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return err(SW_ECUDA, "sw_align_batch_static: no device");
+    {
+        // the pair tables are copied from host memory that is freed when the
+        // call returns, so a captured copy would read freed memory on replay
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess)
+            return err(SW_ECUDA, "sw_align_batch_static: cudaStreamIsCapturing failed");
+        if (cs != cudaStreamCaptureStatusNone)
+            return err(SW_EINVAL, "sw_align_batch_static: the stream is being captured; "
+                                  "this call cannot be captured into a CUDA graph");
+    }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return err(SW_ECUDA, "sw_align_batch_static: cannot read the SM count");
@@ -124,10 +134,10 @@ extern "C" int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_off
     t.pairs = reinterpret_cast<PairInfo *>(base + kOffPairs);
     t.plain = reinterpret_cast<PairInfo *>(base + kOffPlain);
     t.scratch = reinterpret_cast<uint32_t *>(base + kOffBoundary);
-    // the status word must start at zero on every call (enqueue_plan zeroes
-    // the queue heads itself)
-    cudaError_t e = cudaMemsetAsync(base + kOffStatus, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess && !hp.classes.empty())
+    // enqueue_plan zeroes the queue heads itself; the status word (zero at
+    // load) collects the bits of every call until sw_static_status reads it
+    cudaError_t e = cudaSuccess;
+    if (!hp.classes.empty())
         e = cudaMemcpyAsync(const_cast<ClassInfo *>(t.classes), hp.classes.data(),
                             hp.classes.size() * sizeof(ClassInfo), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !hp.pairs.empty())
@@ -143,5 +153,26 @@ extern "C" int sw_align_batch_static(const uint8_t *q_seqs, const int64_t *q_off
                      s);
     if (e != cudaSuccess)
         return err(SW_ECUDA, "sw_align_batch_static: launch: %s", cudaGetErrorString(e));
+    return SW_OK;
+}
+
+// The status word the kernels of sw_align_batch_static set (bit 0: a reverse
+// pass did not reproduce its forward score), read after the stream's work and
+// cleared; nothing is allocated (the copy lands in the caller's host word).
+extern "C" int sw_static_status(int32_t *status, void *stream) {
+    if (!status) return err(SW_EINVAL, "sw_static_status: status is NULL");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return err(SW_ECUDA, "sw_static_status: no device");
+    unsigned char *base = nullptr;
+    int rc = static_address(dev, &base);
+    if (rc != SW_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, base + kOffStatus, sizeof word, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffStatus, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess)
+        return err(SW_ECUDA, "sw_static_status: %s", cudaGetErrorString(e));
+    *status = word;
     return SW_OK;
 }

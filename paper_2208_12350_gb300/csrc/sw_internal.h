@@ -43,7 +43,8 @@ constexpr int kPlainMaxRows = 256;             // rows per thread there (n <= 65
 struct PairInfo {
     int64_t q;        // offset of the first query residue
     int64_t r;        // offset of the first reference residue
-    int64_t scratch;  // offset (uint32 units) of 2*m boundary words, or -1
+    int64_t scratch;  // offset (uint32 units) of the pair's boundary words, or -1
+                      // (used only when the launch has no per-group slots)
     int32_t n, m;     // lengths
     int32_t id;       // output position in the caller's batch
     int32_t pad;
@@ -74,6 +75,11 @@ struct GroupParams {
     int32_t *counters;  // queue heads, one per class, zeroed before each launch
     int32_t n_warps;    // warps of the launch (grid x warps per block)
     uint32_t *scratch;  // strip-boundary words
+    // Strip-boundary words per lane of each lane group's own slot (a multiple
+    // of 4): the group of lanes [b, b + G) of warp w owns words
+    // [(32 w + b) s, (32 w + b + G) s) and reuses them for each pair it
+    // aligns.  0: each pair has its own words at PairInfo::scratch.
+    int32_t slot_words;
     int32_t *status;    // device status word (0 = ok)
     Outputs out;
     int32_t alphabet;
@@ -87,6 +93,10 @@ struct PlainParams {
     const uint8_t *r;
     const PairInfo *pairs;  // one block per entry
     int32_t n_pairs;
+    // NULL: pairs[0 .. n_pairs), one per block.  Otherwise the device pair
+    // {first, count}: pairs[first .. first + count), taken by the blocks of
+    // the grid in turn (the count is known only on the device).
+    const int32_t *range;
     int32_t *status;
     Outputs out;
     int32_t alphabet;
@@ -113,6 +123,13 @@ inline int64_t pair_scratch_words(int n, int m, int G, int rows_per_lane) {
     return boundary_words(n > m ? n : m);
 }
 
+// Words per lane that a G-lane group's slot needs for a pair (0 when the
+// pair fits one strip in both sweeps), rounded up to whole 16-byte chunks.
+inline int32_t pair_slot_words(int n, int m, int G, int rows_per_lane) {
+    const int64_t w = pair_scratch_words(n, m, G, rows_per_lane);
+    return (int32_t)(((w + G - 1) / G + 3) & ~(int64_t)3);
+}
+
 // Whether a pair can take the batched kernel's scaled int32 arithmetic.
 // Both sweeps index columns below kColBase (the forward one the reference,
 // the transposed reverse one the query).
@@ -125,6 +142,7 @@ inline bool group_path_eligible(int n, int m, int smax, int gap_open, int gap_ex
 
 // Device status bits.
 constexpr int32_t kStatusReverseMismatch = 1;  // reverse pass lost the score
+constexpr int32_t kStatusBadOffsets = 2;       // device offsets decreasing, negative or too long
 
 // Host planning of the persistent kernel (plan.cpp): which lane-group width
 // each pair gets and how many warps start on each width class.
@@ -180,6 +198,7 @@ struct HostPlan {
     std::vector<PairInfo> plain;     // one-block-per-pair kernel
     int grid = 0, n_warps = 0;
     int64_t scratch_words = 0;       // strip-boundary words the pairs need
+    int32_t slot_words = 0;          // per lane of a group slot (0: per-pair scratch)
     int plain_threads = 32, plain_kmax = 1;
     int64_t q_bytes = 0, r_bytes = 0;  // residues the offsets span
     bool linear = false;     // gap_open == gap_extend: the kernel without E and F
@@ -204,6 +223,9 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet);
 
 cudaError_t launch_plain(const PlainParams &p, int threads, int rows_per_thread_max,
                          cudaStream_t s);
+// The plain kernel over a device range (p.range set) with a fixed grid.
+cudaError_t launch_plain_range(const PlainParams &p, int threads, int rows_per_thread_max,
+                               int grid, cudaStream_t s);
 size_t plain_smem_bytes(int threads, int alphabet);
 
 int set_error(int code, const char *msg);  // message for sw_last_error()
@@ -232,11 +254,14 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
 // gaps, alphabet) (default: the CUDA occupancy query on the current device;
 // the host-only plan preview passes an estimate from shared memory).
 using BlocksPerSmFn = int (*)(ProfileKind, bool, int, int *);
+// group_slots: strip-boundary words in one slot per lane group, sized for
+// the batch's largest need (HostPlan::slot_words), instead of per pair.
 int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192,
-                   bool allow_packed = true, BlocksPerSmFn blocks_per_sm = group_blocks_per_sm);
+                   bool allow_packed = true, BlocksPerSmFn blocks_per_sm = group_blocks_per_sm,
+                   bool group_slots = false);
 // Enqueues the kernels of a planned batch on s (queue-head reset included).
 cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
                          const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,

@@ -65,6 +65,79 @@ def test_static_entry_matches_planned_path(gpu_lib):
         bad = np.flatnonzero(np.any(got != expect, axis=0))
         assert len(bad) == 0, (f"call {call}: {len(bad)} pairs differ, first {int(bad[0])}: "
                                f"{got[:, bad[0]].tolist()} vs {expect[:, bad[0]].tolist()}")
+        # no kernel of the call found its reverse pass inconsistent
+        assert swgb.sw_static_status(stream) == 0
+
+
+def _long_pairs(seed, shapes):
+    rng = np.random.default_rng(seed)
+    qs, rs = [], []
+    for n, m in shapes:
+        q = rng.integers(0, 4, n).astype(np.uint8)
+        r = rng.integers(0, 4, m).astype(np.uint8)
+        k = min(n, m) // 3
+        if k:
+            off = int(rng.integers(0, m - k + 1))
+            r[off:off + k] = q[n - k:]
+        qs.append(q)
+        rs.append(r)
+    return wl.make_batch(f"static-long-{seed}", qs, rs, wl.dna_matrix(), -6, -1)
+
+
+def test_static_entry_large_then_small_batch(gpu_lib):
+    """A large batch of long pairs, then a smaller batch of other long pairs:
+    the second call must not read the strip-boundary words or tables that
+    the first left in the shared array (each call writes what it reads)."""
+    import torch
+    swgb = gpu_lib
+    dev = torch.device("cuda", 0)
+    big = _long_pairs(71, [(int(n), int(m)) for n, m in
+                           np.random.default_rng(5).integers(200, 3000, size=(300, 2))])
+    small = _long_pairs(72, [(2500, 1800), (900, 2900), (1700, 1700), (3000, 600), (40, 2000)])
+    ctx = swgb.sw_ctx_create(0)
+    stream = torch.cuda.Stream(device=dev)
+    try:
+        for b in (big, small, big, small):
+            q = torch.from_numpy(b.q_seqs).to(dev)
+            r = torch.from_numpy(b.r_seqs).to(dev)
+            plan = swgb.sw_plan_create(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
+                                       b.gap_extend)
+            ref = torch.full((5, b.n_pairs), -9, dtype=torch.int32, device=dev)
+            swgb.sw_plan_execute(plan, q, r, ref, stream)
+            stream.synchronize()
+            swgb.sw_plan_destroy(plan)
+            out = torch.full((5, b.n_pairs), -3, dtype=torch.int32, device=dev)
+            swgb.sw_align_batch_static(q, b.q_offsets, r, b.r_offsets, b.matrix, b.gap_open,
+                                       b.gap_extend, out, stream)
+            stream.synchronize()
+            assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy()), b.name
+            assert swgb.sw_static_status(stream) == 0
+    finally:
+        swgb.sw_ctx_destroy(ctx)
+
+
+def test_static_entry_refuses_stream_capture(gpu_lib):
+    """The call copies its tables from host memory it frees on return, so
+    it refuses a capturing stream before enqueueing anything."""
+    import torch
+    swgb = gpu_lib
+    dev = torch.device("cuda", 0)
+    b = wl.gen_config(0, n_pairs=16)
+    q = torch.from_numpy(b.q_seqs).to(dev)
+    r = torch.from_numpy(b.r_seqs).to(dev)
+    out = torch.zeros((5, b.n_pairs), dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    caught = None
+    with torch.cuda.graph(g, stream=stream):
+        try:
+            swgb.sw_align_batch_static(q, b.q_offsets, r, b.r_offsets, b.matrix, b.gap_open,
+                                       b.gap_extend, out, stream)
+        except swgb.SwError as e:
+            caught = e
+        out.add_(0)  # something to capture
+    assert caught is not None and caught.code == swgb.SW_EINVAL
 
 
 def test_static_entry_matches_on_wide_scores(gpu_lib):
@@ -98,6 +171,7 @@ def test_static_entry_matches_on_wide_scores(gpu_lib):
                                    b.gap_extend, out)
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
+        assert swgb.sw_static_status() == 0
 
 
 def test_static_entry_rejects_oversize_batches(gpu_lib):
