@@ -478,7 +478,7 @@ int device_plan_shape(int32_t n_pairs, const int8_t *mat, int32_t A, int32_t go,
     S.all_plain = mode == SW_MODE_PLAIN;
     S.bulk_log2g = narrow_log2g >= 0 ? std::max(narrow_log2g, kMinLog2G) : 3;
     S.cap_fraction = narrow_log2g >= 0 ? cap_fraction : 0.5;
-    S.strip_ov = 12;
+    S.strip_ov = 18;  // the host planner's strip-start charge
     S.slot_words = slot_words;
     int smax = -128, smin = 127;
     for (int i = 0; i < A * A; ++i) {

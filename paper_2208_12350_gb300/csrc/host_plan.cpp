@@ -26,8 +26,11 @@ static int plan_err(std::string *msg, int code, const char *fmt, long long a = 0
 // (the strip's profile build and its first staging wait).  A term per
 // residue code (the build writes A + 1 profile columns) sent 20k protein
 // pairs to wider groups, measured slower, so the cost is one constant.
+// With branch-free steady-state staging (cheaper steps, so a strip start
+// weighs more) 18 measured 0.6-0.8 % faster than 12 on 100k DNA and 20k
+// protein pairs and no slower on 200k skewed pairs; 6 was 17 % slower there.
 #ifndef SWGB_STRIP_OV_STEPS
-#define SWGB_STRIP_OV_STEPS 12
+#define SWGB_STRIP_OV_STEPS 18
 #endif
 static double strip_overhead_steps(int /*A*/) { return (double)SWGB_STRIP_OV_STEPS; }
 

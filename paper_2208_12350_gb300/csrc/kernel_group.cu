@@ -189,9 +189,6 @@ __device__ __forceinline__ void lds16_if(uint4 &v, const uint32_t *ssrc, bool p)
         : "r"((int)p), "r"(sa)
         : "memory");
 }
-#ifndef SWGB_SEL_ASM
-#define SWGB_SEL_ASM 0
-#endif
 // cp_async16 issued only where p holds: a predicated instruction, no branch
 // (an address formed for a lane with p false is never accessed)
 __device__ __forceinline__ void cp_async16_if(void *smem_dst, const void *gsrc, bool p) {
@@ -489,7 +486,6 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
         // packed form: the halves of word 0's row above (lane 0 takes the
         // boundary word's low half, the others the high half of a shuffle)
         const uint32_t selH = gl == 0 ? 0x5410u : 0x5432u;
-        [[maybe_unused]] const uint32_t lane0_mask = gl == 0 ? 0xFFFFFFFFu : 0u;
         const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << gbase);
         uint8_t *res_ring = reinterpret_cast<uint8_t *>(rings) + gid * kRingBytes;
         uint32_t *bin_ring =
@@ -766,18 +762,11 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                     const bool in1 = (unsigned)j1 < (unsigned)mcols;
                     uint32_t inH = __shfl_up_sync(kFull, outHw, 1, G);
                     uint32_t inF = LIN ? 0u : __shfl_up_sync(kFull, outFw, 1, G);
-#if SWGB_SEL_ASM
-                    // previous strip's last row (H low, F - go high), or (0, 0),
-                    // merged by mask (one three-input logic operation)
-                    inH = (bws[u] & lane0_mask) | (inH & ~lane0_mask);
-                    inF = (bws[u] & lane0_mask) | (inF & ~lane0_mask);
-#else
                     if (gl == 0) {
                         // previous strip's last row (H low, F - go high), or (0, 0)
                         inH = bws[u];
                         inF = bws[u];
                     }
-#endif
                     // word 0's row above: the lane above's last row (high half of
                     // its last word; lane 0: the boundary word's halves) and this
                     // lane's row R/2 - 1 of the step before

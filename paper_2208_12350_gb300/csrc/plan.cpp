@@ -7,12 +7,13 @@
 // kernel's 4-step blocks); its reverse pass is estimated at a quarter of
 // that.  Each strip start also stalls the group's whole warp (its 32 / G
 // groups) while the warp builds the strip's query profile, so a strip is
-// charged a fixed number of steps times 32 / G besides its columns.  The
-// fixed cost is 12 steps: measured on 100k DNA pairs with the host-only
-// plan preview, every value from 4 to 20 makes the planner's own choice the
-// measured best (bulk groups of 8 lanes with half-width tails, 2,221 GCUPS,
-// against 1,995 for the all-2-lane plan it chose without the charge), and
-// from 24 up it sends 20k protein pairs to wider groups, measured slower.  Narrow groups waste the fewest cells on padding and fill but make
+// charged a fixed number of steps times 32 / G besides its columns (the
+// charge is set in host_plan.cpp: 18 steps; measured on 100k DNA pairs with
+// the host-only plan preview, every value from 4 to 20 made the planner's
+// own choice the measured best, bulk groups of 8 lanes with half-width
+// tails, against the all-2-lane plan it chose without the charge, and from
+// 24 up it sends 20k protein pairs to wider groups, measured slower).
+// Narrow groups waste the fewest cells on padding and fill but make
 // a pair's serial sweep long, so a batch with a long tail finishes late.
 // The planner therefore keeps a narrow width Gn for the bulk and sends each
 // pair whose sweep under Gn exceeds a cap (a fraction of the mean load per
