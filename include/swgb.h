@@ -108,6 +108,13 @@ typedef enum {
  * gets words of its own (less memory for small batches of long pairs, more
  * DRAM traffic). */
 #define SW_PLAN_PAIR_SCRATCH 16u
+/* Guard regions (a test aid): every device buffer the plan allocates (pair
+ * and class tables, queue heads, strip-boundary scratch, host-call staging)
+ * gets 4 KiB of a known pattern before and after it, and each execution
+ * enqueues, after the alignment kernels, a check that sets bit 2 of the
+ * context's status word (sw_ctx_status) if any guard word changed.  Results
+ * are unchanged; nothing traps. */
+#define SW_PLAN_GUARDS 32u
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_plan sw_plan;
@@ -135,8 +142,15 @@ int sw_ctx_host_in_place(const sw_ctx *ctx, int32_t *yes);
  * *status (0 = no inconsistency detected by any kernel; bit 0 = a reverse
  * pass did not reproduce its forward score; bit 1 = a one-shot call met
  * device offsets that were negative, decreasing or more than SW_MAX_LEN
- * apart, and gave those pairs the "no alignment" outputs) and clear it. */
+ * apart, and gave those pairs the "no alignment" outputs; bit 2 = a guard
+ * word of a plan made with SW_PLAN_GUARDS, or of a one-shot workspace with
+ * guards on, changed) and clear it. */
 int sw_ctx_status(sw_ctx *ctx, int32_t *status);
+
+/* Guard regions around the one-shot calls' workspace parts (tables, sort
+ * buffers, strip-boundary slots), checked after each call's kernels as for
+ * SW_PLAN_GUARDS (on = 1; 0 = off, the default).  A test aid. */
+int sw_ctx_set_guards(sw_ctx *ctx, int32_t on);
 
 /* The context sw_align_batch uses on `device` (created on first use, owned
  * by the library until the process exits: do not destroy it).  Its status
@@ -216,6 +230,14 @@ int sw_plan_info(const sw_plan *plan, int32_t *n_group_pairs, int32_t *n_plain,
 #define SW_ARITH_S32 0
 #define SW_ARITH_S16X2 1
 int sw_plan_arith(const sw_plan *plan, int32_t *arith);
+
+/* Test aid for plans made with SW_PLAN_GUARDS: overwrite one word in the
+ * middle of guard region `region` (0 .. 2 x the plan's guarded buffers - 1)
+ * with a value other than the guard pattern (a host-side copy into the
+ * plan's own allocation, after synchronising the device), so that the next
+ * execution's check must report it.  SW_EINVAL if the plan has no such
+ * region. */
+int sw_plan_poison_guard(sw_plan *plan, int32_t region);
 
 int sw_plan_destroy(sw_plan *plan);
 

@@ -27,6 +27,7 @@ SW_PLAN_ENDS_ONLY = 2
 SW_PLAN_PACKED_2BIT = 4
 SW_PLAN_NO_S16X2 = 8
 SW_PLAN_PAIR_SCRATCH = 16
+SW_PLAN_GUARDS = 32
 SW_ARITH_S32, SW_ARITH_S16X2 = 0, 1
 SW_MAX_LEN = 65535
 
@@ -41,6 +42,7 @@ SIGNATURES = {
     "sw_ctx_sm_count": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_status": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_default_ctx": ([_I32, _PP], ctypes.c_int),
+    "sw_ctx_set_guards": ([_P, _I32], ctypes.c_int),
     "sw_ctx_host_in_place": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
     "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
@@ -52,6 +54,7 @@ SIGNATURES = {
     "sw_plan_preview": ([_P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _I32, _I32,
                          ctypes.c_double, ctypes.POINTER(_I32), _P, _P], ctypes.c_int),
     "sw_plan_destroy": ([_P], ctypes.c_int),
+    "sw_plan_poison_guard": ([_P, _I32], ctypes.c_int),
     "sw_align_batch": ([_P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P],
                        ctypes.c_int),
     "sw_align_batch_ex": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P,
@@ -178,6 +181,12 @@ def sw_default_ctx(device: int = 0) -> int:
 
 STATUS_REVERSE_MISMATCH = 1
 STATUS_BAD_OFFSETS = 2
+STATUS_GUARD = 4
+
+
+def sw_ctx_set_guards(ctx: int, on: bool = True) -> None:
+    """Guard regions around the one-shot calls' workspace parts (test aid)."""
+    _check(load().sw_ctx_set_guards(ctx, 1 if on else 0), "sw_ctx_set_guards")
 
 
 def sw_ctx_set_tuning(ctx: int, narrow_log2g: int = -1, cap_fraction: float = 0.5) -> None:
@@ -254,6 +263,11 @@ def sw_plan_preview(q_offsets, r_offsets, score_matrix, gap_open: int, gap_exten
                                   cap_fraction, ctypes.byref(kind), _addr(lg), _addr(rank)),
            "sw_plan_preview")
     return PLAN_KINDS[kind.value], lg[:n], rank[:n]
+
+
+def sw_plan_poison_guard(plan: int, region: int) -> None:
+    """Test aid: break one word of guard region `region` of a SW_PLAN_GUARDS plan."""
+    _check(load().sw_plan_poison_guard(plan, region), "sw_plan_poison_guard")
 
 
 def sw_plan_destroy(plan: int) -> None:

@@ -50,19 +50,6 @@ struct DeviceGuard {
     }
 };
 
-template <class T>
-int upload(T **dst, const std::vector<T> &src) {
-    *dst = nullptr;
-    if (src.empty()) return SW_OK;
-    if (cudaMalloc(dst, src.size() * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(SW_ENOMEM, "cudaMalloc of %zu bytes failed", src.size() * sizeof(T));
-    }
-    SW_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return SW_OK;
-}
-
-
 }  // namespace
 
 namespace swgb {
@@ -88,6 +75,7 @@ struct sw_ctx {
     // stream-ordered workspaces of the one-shot calls (created on first use;
     // keeps freed memory for the next call instead of returning it)
     cudaMemPool_t pool = nullptr;
+    bool guards = false;  // guard regions around one-shot workspace parts
 };
 
 namespace swgb {
@@ -114,23 +102,60 @@ struct sw_plan {
     // graph replay
     cudaGraphExec_t gexec = nullptr;
     const void *gkey[8] = {nullptr};
+    // every device allocation (the pointers above are views into them), and
+    // with SW_PLAN_GUARDS the guard regions around them
+    std::vector<void *> raw;
+    GuardList guards{};
 };
 
 static void plan_free(sw_plan *p) {
     if (!p) return;
-    DeviceGuard g(p->ctx->device);
+    DeviceGuard g(p->ctx ? p->ctx->device : 0);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
-    cudaFree(p->d_pairs);
-    cudaFree(p->d_classes);
-    cudaFree(p->d_counter);
-    cudaFree(p->d_scratch);
-    cudaFree(p->d_plain);
-    cudaFree(p->d_q);
-    cudaFree(p->d_r);
-    cudaFree(p->d_unq);
-    cudaFree(p->d_unr);
-    cudaFree(p->d_out);
+    for (void *a : p->raw) cudaFree(a);
     delete p;
+}
+
+// A device buffer of `bytes` for plan p; with SW_PLAN_GUARDS, between two
+// guard regions filled with the guard pattern.
+static int plan_alloc(sw_plan *p, void **out, size_t bytes, const char *what) {
+    *out = nullptr;
+    const bool guarded = (p->flags & SW_PLAN_GUARDS) != 0;
+    const size_t body = (bytes + 255) & ~(size_t)255;
+    void *raw = nullptr;
+    if (cudaMalloc(&raw, guarded ? body + 2 * kGuardBytes : std::max<size_t>(bytes, 1)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return fail(SW_ENOMEM, "sw_plan: allocation of %zu bytes (%s) failed", bytes, what);
+    }
+    p->raw.push_back(raw);
+    if (!guarded) {
+        *out = raw;
+        return SW_OK;
+    }
+    unsigned char *b = static_cast<unsigned char *>(raw);
+    if (p->guards.n + 2 > kMaxGuards) return fail(SW_EINVAL, "sw_plan: too many guarded buffers");
+    SW_CUDA_TRY(cudaMemset(b, 0xA5, kGuardBytes));
+    SW_CUDA_TRY(cudaMemset(b + kGuardBytes + body, 0xA5, kGuardBytes));
+    for (unsigned char *g : {b, b + kGuardBytes + body}) {
+        p->guards.ptr[p->guards.n] = reinterpret_cast<uint32_t *>(g);
+        p->guards.words[p->guards.n] = (int32_t)(kGuardBytes / 4);
+        ++p->guards.n;
+    }
+    *out = b + kGuardBytes;
+    return SW_OK;
+}
+
+template <class T>
+static int plan_upload(sw_plan *p, T **dst, const std::vector<T> &src, const char *what) {
+    *dst = nullptr;
+    if (src.empty()) return SW_OK;
+    void *d = nullptr;
+    const int rc = plan_alloc(p, &d, src.size() * sizeof(T), what);
+    if (rc != SW_OK) return rc;
+    *dst = static_cast<T *>(d);
+    SW_CUDA_TRY(cudaMemcpy(d, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SW_OK;
 }
 
 static void reap_retired(sw_ctx *ctx, bool wait) {
@@ -219,6 +244,12 @@ int sw_ctx_status(sw_ctx *ctx, int32_t *status) {
     return SW_OK;
 }
 
+int sw_ctx_set_guards(sw_ctx *ctx, int32_t on) {
+    if (!ctx || (on != 0 && on != 1)) return fail(SW_EINVAL, "sw_ctx_set_guards: bad argument");
+    ctx->guards = on != 0;
+    return SW_OK;
+}
+
 int sw_ctx_set_tuning(sw_ctx *ctx, int32_t narrow_log2g, double cap_fraction) {
     if (!ctx || narrow_log2g < -1 || narrow_log2g > 5 || !(cap_fraction > 0))
         return fail(SW_EINVAL, "sw_ctx_set_tuning: bad argument");
@@ -238,6 +269,8 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
     reap_retired(ctx, false);
     auto *p = new sw_plan();
+    p->ctx = ctx;
+    p->flags = flags;
     std::string msg;
     int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
                             gap_extend, mode, ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
@@ -260,27 +293,31 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
             plan_free(p);
             return fail(SW_EINVAL, "sw_plan_create: SW_PLAN_PACKED_2BIT needs alphabet_size <= 4");
         }
-        if (cudaMalloc(&p->d_unq, (size_t)std::max<int64_t>(p->hp.q_bytes, 4)) != cudaSuccess ||
-            cudaMalloc(&p->d_unr, (size_t)std::max<int64_t>(p->hp.r_bytes, 4)) != cudaSuccess) {
-            cudaGetLastError();
+        void *uq = nullptr, *ur = nullptr;
+        if ((rc = plan_alloc(p, &uq, (size_t)std::max<int64_t>(p->hp.q_bytes, 4), "inputs")) ||
+            (rc = plan_alloc(p, &ur, (size_t)std::max<int64_t>(p->hp.r_bytes, 4), "inputs"))) {
             plan_free(p);
-            return fail(SW_ENOMEM, "sw_plan_create: allocation of the unpacked inputs failed");
+            return rc;
         }
+        p->d_unq = static_cast<uint8_t *>(uq);
+        p->d_unr = static_cast<uint8_t *>(ur);
     }
     std::memcpy(p->mat, score_matrix, (size_t)alphabet_size * alphabet_size);
-    if ((rc = upload(&p->d_pairs, p->hp.pairs)) || (rc = upload(&p->d_classes, p->hp.classes)) ||
-        (rc = upload(&p->d_plain, p->hp.plain))) {
+    if ((rc = plan_upload(p, &p->d_pairs, p->hp.pairs, "pair table")) ||
+        (rc = plan_upload(p, &p->d_classes, p->hp.classes, "class table")) ||
+        (rc = plan_upload(p, &p->d_plain, p->hp.plain, "plain table"))) {
         plan_free(p);
         return rc;
     }
-    if (cudaMalloc(&p->d_counter, kMaxClasses * sizeof(int32_t)) != cudaSuccess ||
+    void *cnt = nullptr, *scr = nullptr;
+    if ((rc = plan_alloc(p, &cnt, kMaxClasses * sizeof(int32_t), "queue heads")) ||
         (p->hp.scratch_words > 0 &&
-         cudaMalloc(&p->d_scratch, p->hp.scratch_words * sizeof(uint32_t)) != cudaSuccess)) {
-        cudaGetLastError();
+         (rc = plan_alloc(p, &scr, p->hp.scratch_words * sizeof(uint32_t), "scratch")))) {
         plan_free(p);
-        return fail(SW_ENOMEM, "sw_plan_create: scratch allocation (%lld words) failed",
-                    (long long)p->hp.scratch_words);
+        return rc;
     }
+    p->d_counter = static_cast<int32_t *>(cnt);
+    p->d_scratch = static_cast<uint32_t *>(scr);
     p->dev.pairs = p->d_pairs;
     p->dev.classes = p->d_classes;
     p->dev.plain = p->d_plain;
@@ -300,6 +337,8 @@ static int enqueue(sw_plan *p, const uint8_t *q, const uint8_t *r, const Outputs
         r = p->d_unr;
     }
     SW_CUDA_TRY(enqueue_plan(p->hp, p->dev, q, r, o, p->mat, p->A, p->go, p->ge, s));
+    // SW_PLAN_GUARDS: every guard word still holds the pattern
+    if (p->guards.n) SW_CUDA_TRY(launch_guard_check(p->guards, p->ctx->d_status, s));
     return SW_OK;
 }
 
@@ -377,17 +416,15 @@ int sw_plan_execute_host(sw_plan *p, const uint8_t *q_seqs, const uint8_t *r_seq
     const int64_t qb = packed ? (p->hp.q_bytes + 3) / 4 : p->hp.q_bytes;
     const int64_t rb = packed ? (p->hp.r_bytes + 3) / 4 : p->hp.r_bytes;
     if (!p->d_out) {
-        if (cudaMalloc(&p->d_q, (size_t)std::max<int64_t>(qb, 1)) != cudaSuccess ||
-            cudaMalloc(&p->d_r, (size_t)std::max<int64_t>(rb, 1)) != cudaSuccess ||
-            cudaMalloc(&p->d_out, (size_t)5 * p->n_pairs * sizeof(int32_t)) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(p->d_q);
-            cudaFree(p->d_r);
-            cudaFree(p->d_out);
-            p->d_q = p->d_r = nullptr;
-            p->d_out = nullptr;
-            return fail(SW_ENOMEM, "sw_plan_execute_host: staging allocation failed");
-        }
+        void *dq = nullptr, *dr = nullptr, *dout = nullptr;
+        int rc0;
+        if ((rc0 = plan_alloc(p, &dq, (size_t)std::max<int64_t>(qb, 1), "staging")) ||
+            (rc0 = plan_alloc(p, &dr, (size_t)std::max<int64_t>(rb, 1), "staging")) ||
+            (rc0 = plan_alloc(p, &dout, (size_t)5 * p->n_pairs * sizeof(int32_t), "staging")))
+            return rc0;
+        p->d_q = static_cast<uint8_t *>(dq);
+        p->d_r = static_cast<uint8_t *>(dr);
+        p->d_out = static_cast<int32_t *>(dout);
     }
     cudaStream_t s = (cudaStream_t)stream;
     // Pinned host inputs on a coherent host link are read by the kernels in
@@ -427,6 +464,17 @@ int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int
 int sw_plan_arith(const sw_plan *p, int32_t *arith) {
     if (!p || !arith) return fail(SW_EINVAL, "sw_plan_arith: NULL argument");
     *arith = (!p->hp.pairs.empty() && is_packed(p->hp.kind)) ? SW_ARITH_S16X2 : SW_ARITH_S32;
+    return SW_OK;
+}
+
+int sw_plan_poison_guard(sw_plan *p, int32_t region) {
+    if (!p || region < 0 || region >= p->guards.n)
+        return fail(SW_EINVAL, "sw_plan_poison_guard: no guard region %d", region);
+    DeviceGuard g(p->ctx->device);
+    const uint32_t word = ~kGuardWord;
+    SW_CUDA_TRY(cudaDeviceSynchronize());
+    SW_CUDA_TRY(cudaMemcpy(p->guards.ptr[region] + p->guards.words[region] / 2, &word,
+                           sizeof word, cudaMemcpyHostToDevice));
     return SW_OK;
 }
 
@@ -488,6 +536,7 @@ int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offse
                                ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
                                kOneShotSlotWords, &shape, &msg);
     if (rc != SW_OK) return fail(rc, "sw_align_batch_ex: %s", msg.c_str());
+    shape.guards = ctx->guards ? 1 : 0;
     cudaMemPool_t pool = nullptr;
     if ((rc = ctx_pool(ctx, &pool)) != SW_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;

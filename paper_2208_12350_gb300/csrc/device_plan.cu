@@ -78,14 +78,21 @@ struct Header {
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Byte offsets of the workspace parts for n pairs.
+// Byte offsets of the workspace parts for n pairs; with guards, a guard
+// region before every part and after the last (offsets in guard[]).
 struct WsLayout {
     size_t hdr, counts1, counts2, keys0, keys1, vals1, pairs, scratch, total;
+    size_t guard[9];
+    int n_guards = 0;
 };
-__host__ WsLayout ws_layout(int64_t n, int64_t tiles, int64_t scratch_words) {
+__host__ WsLayout ws_layout(int64_t n, int64_t tiles, int64_t scratch_words, bool guards = false) {
     WsLayout L;
     size_t at = 0;
     auto take = [&](size_t bytes) {
+        if (guards) {
+            L.guard[L.n_guards++] = at;
+            at += kGuardBytes;
+        }
         const size_t o = at;
         at = align256(at + bytes);
         return o;
@@ -98,6 +105,10 @@ __host__ WsLayout ws_layout(int64_t n, int64_t tiles, int64_t scratch_words) {
     L.vals1 = take((size_t)n * 4);
     L.pairs = take((size_t)n * sizeof(PairInfo));
     L.scratch = take((size_t)scratch_words * 4);
+    if (guards) {
+        L.guard[L.n_guards++] = at;
+        at += kGuardBytes;
+    }
     L.total = at;
     return L;
 }
@@ -461,7 +472,7 @@ __global__ void __launch_bounds__(kThreads) dp_scatter2(const DevicePlanShape S,
 
 size_t device_plan_workspace_bytes(const DevicePlanShape &S) {
     const int64_t tiles = std::max<int64_t>(1, ((int64_t)S.n_pairs + kTile - 1) / kTile);
-    return ws_layout(S.n_pairs, tiles, S.scratch_words).total;
+    return ws_layout(S.n_pairs, tiles, S.scratch_words, S.guards != 0).total;
 }
 
 int device_plan_shape(int32_t n_pairs, const int8_t *mat, int32_t A, int32_t go, int32_t ge,
@@ -542,7 +553,7 @@ cudaError_t enqueue_device_plan(const DevicePlanShape &S, void *workspace, const
                                 const Outputs &o, int32_t *status, cudaStream_t s) {
     if (S.n_pairs <= 0) return cudaSuccess;
     const int tiles = (int)std::max<int64_t>(1, ((int64_t)S.n_pairs + kTile - 1) / kTile);
-    const WsLayout L = ws_layout(S.n_pairs, tiles, S.scratch_words);
+    const WsLayout L = ws_layout(S.n_pairs, tiles, S.scratch_words, S.guards != 0);
     unsigned char *base = static_cast<unsigned char *>(workspace);
     Header *hdr = reinterpret_cast<Header *>(base + L.hdr);
     uint32_t *counts1 = reinterpret_cast<uint32_t *>(base + L.counts1);
@@ -553,9 +564,25 @@ cudaError_t enqueue_device_plan(const DevicePlanShape &S, void *workspace, const
     PairInfo *pairs = reinterpret_cast<PairInfo *>(base + L.pairs);
     uint32_t *scratch = reinterpret_cast<uint32_t *>(base + L.scratch);
 
-    // header and both count arrays start at zero (they are contiguous)
-    cudaError_t e = cudaMemsetAsync(base, 0, L.keys0, s);
+    GuardList guards{};
+    for (int k = 0; k < L.n_guards; ++k) {
+        guards.ptr[k] = reinterpret_cast<uint32_t *>(base + L.guard[k]);
+        guards.words[k] = (int32_t)(kGuardBytes / 4);
+    }
+    guards.n = L.n_guards;
+    cudaError_t e = launch_guard_fill(guards, s);
     if (e != cudaSuccess) return e;
+    // header and both count arrays start at zero (contiguous unless guarded)
+    if (guards.n) {
+        if ((e = cudaMemsetAsync(base + L.hdr, 0, sizeof(Header), s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(base + L.counts1, 0, (size_t)kDigits * tiles * 4, s)) !=
+                cudaSuccess ||
+            (e = cudaMemsetAsync(base + L.counts2, 0, (size_t)kDigits * tiles * 4, s)) !=
+                cudaSuccess)
+            return e;
+    } else if ((e = cudaMemsetAsync(base, 0, L.keys0, s)) != cudaSuccess) {
+        return e;
+    }
     const int cgrid = (int)std::min<int64_t>(((int64_t)S.n_pairs + kThreads - 1) / kThreads, 1024);
     dp_classify<<<cgrid, kThreads, 0, s>>>(S, qo, ro, hdr, status, o);
     dp_keys<<<tiles, kThreads, 0, s>>>(S, qo, ro, hdr, keys0, counts1, tiles);
@@ -610,7 +637,8 @@ cudaError_t enqueue_device_plan(const DevicePlanShape &S, void *workspace, const
                                     k == 0 ? 1 : kPlainMaxRows, S.plain_grid, s)) != cudaSuccess)
             return e;
     }
-    return cudaSuccess;
+    // guards: every guard word still holds the pattern
+    return launch_guard_check(guards, status, s);
 }
 
 }  // namespace swgb

@@ -29,6 +29,7 @@ struct DevicePlanShape {
     int32_t slot_words;     // strip-boundary words per lane of a group slot
     int32_t plain_grid;     // blocks of the plain kernel's launches
     int64_t scratch_words;  // slot words of the larger grid
+    int32_t guards;         // guard regions around every workspace part (test aid)
     int8_t mat[kMaxAlphabet * kMaxAlphabet];
 };
 

@@ -206,7 +206,35 @@ __global__ void check_residues_kernel(const uint8_t *s, int64_t n, int A,
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(bad, local);
 }
 
+__global__ void guard_fill_kernel(const GuardList g) {
+    for (int r = blockIdx.y; r < g.n; r += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.words[r];
+             i += gridDim.x * blockDim.x)
+            g.ptr[r][i] = kGuardWord;
+}
+
+__global__ void guard_check_kernel(const GuardList g, int32_t *status) {
+    bool bad = false;
+    for (int r = blockIdx.y; r < g.n; r += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.words[r];
+             i += gridDim.x * blockDim.x)
+            bad |= g.ptr[r][i] != kGuardWord;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusGuard);
+}
+
 }  // namespace
+
+cudaError_t launch_guard_fill(const GuardList &g, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    guard_fill_kernel<<<dim3(4, g.n), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guard_check(const GuardList &g, int32_t *status, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    guard_check_kernel<<<dim3(4, g.n), 256, 0, s>>>(g, status);
+    return cudaGetLastError();
+}
 
 size_t plain_smem_bytes(int threads, int alphabet) {
     const int mat_words = (alphabet * alphabet + 3) & ~3;

@@ -143,6 +143,21 @@ inline bool group_path_eligible(int n, int m, int smax, int gap_open, int gap_ex
 // Device status bits.
 constexpr int32_t kStatusReverseMismatch = 1;  // reverse pass lost the score
 constexpr int32_t kStatusBadOffsets = 2;       // device offsets decreasing, negative or too long
+constexpr int32_t kStatusGuard = 4;            // a guard word around a device buffer changed
+
+// Guard regions (test aid): kGuardBytes of kGuardWord before and after a
+// device buffer; a check kernel after the alignment kernels sets
+// kStatusGuard when any word of them changed (no trap, no assert).
+constexpr uint32_t kGuardWord = 0xA5A5A5A5u;
+constexpr size_t kGuardBytes = 4096;
+constexpr int kMaxGuards = 32;
+struct GuardList {
+    uint32_t *ptr[kMaxGuards];
+    int32_t words[kMaxGuards];
+    int32_t n;
+};
+cudaError_t launch_guard_fill(const GuardList &g, cudaStream_t s);
+cudaError_t launch_guard_check(const GuardList &g, int32_t *status, cudaStream_t s);
 
 // Host planning of the persistent kernel (plan.cpp): which lane-group width
 // each pair gets and how many warps start on each width class.
