@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--cigar", action="store_true",
                     help="also time the traceback (CIGAR) of every aligned pair")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-serve-staged", action="store_true",
+                    help="skip the serving sweep with per-request staged sequences")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the secondary workloads (1,000 DNA, 20k protein, 200k skewed DNA)")
     ap.add_argument("--config-steps", type=int, default=6,
@@ -273,32 +275,39 @@ def profiled_traffic(batch, tune, arith="s16x2", flags=0, sms=152) -> int | None
 
 # ------------------------------------------------------------------- serving
 
-def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
+def serve_sweep(swgb, ctx, pools, expect, args, resident: bool) -> dict:
     """Open-loop serving: Poisson arrivals of requests of floor(log-uniform
     [1, 4096]) pairs, half from the DNA workload and half from the protein
     workload, offered at rates growing x1.5 per point until the server no
     longer keeps up (served rate below 90% of offered, or p99 above 1 s).
-    Latency = completion on the GPU (server clock) - scheduled arrival, so
-    a late submitter counts against the server, as a real client would.
-    Every request's results are compared with the same pairs run as one
-    whole batch."""
+    resident: both workloads are uploaded once as resident pools and each
+    request names its pair range (sequences stay on the device); otherwise
+    each request brings its sequences, staged at submission.  Latency =
+    completion on the GPU (server clock) - scheduled arrival, so a late
+    submitter counts against the server, as a real client would.  Every
+    request's results are compared with the CPU oracle's results for those
+    pairs (expect)."""
     import queue
     import threading
-    protein = wl.gen_config(2)
-    prot_res = _batch_results(swgb, ctx, protein)
-    pools = {"dna": dna, "protein": protein}
-    pool_res = {"dna": dna_res, "protein": prot_res}
     reqs = wl.serving_requests(args.serve_requests, 1.0, pools=pools)
     budget = int(args.serve_budget_gb * (1 << 30))
     srv = swgb.sw_server_create(ctx, budget, streams=8, staging_bytes=2 << 30)
     identical = True
+    pid = {}
+    if resident:
+        for kind, b in pools.items():
+            pid[kind] = swgb.sw_server_add_pool(srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets,
+                                                b.matrix, b.gap_open, b.gap_extend)
 
     def check(rq, out):
-        exp = pool_res[rq.kind][rq.first:rq.first + rq.batch.n_pairs]
+        exp = expect[rq.kind][rq.first:rq.first + rq.batch.n_pairs]
         return bool(np.array_equal(out, exp))
 
     def submit(rq):
         b = rq.batch
+        if resident:
+            return swgb.sw_server_submit_pool(srv, pid[rq.kind], rq.first, b.n_pairs,
+                                              timeout_ms=120000)
         return swgb.sw_server_submit(srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix,
                                      b.gap_open, b.gap_extend, timeout_ms=120000)
 
@@ -374,27 +383,15 @@ def serve_sweep(swgb, ctx, dna, dna_res, args) -> dict:
             "at_rps": best["offered_rps"] if best else None,
             "max_sustained_rps": best["served_rps"] if best else None,
             "peak_gcups": max(p["gcups"] for p in points) if points else None,
-            "identical_outputs": identical, "budget_gb": args.serve_budget_gb, "streams": 8,
+            "oracle_identical": identical, "budget_gb": args.serve_budget_gb, "streams": 8,
             "client_threads": n_sub,
+            "sequences": ("resident pools on the device (requests name pair ranges)" if resident
+                          else "staged per request (each request brings its sequences)"),
             "device_bytes_peak": st["device_bytes_peak"],
             "requests": "Poisson arrivals; floor(log-uniform[1,4096]) pairs; 50% dna-100k, "
-                        "50% protein-20k pairs",
+                        "50% protein-20k pairs; every result compared with the CPU oracle",
             "points": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in p.items()}
                        for p in points]}
-
-
-def _batch_results(swgb, ctx, batch) -> np.ndarray:
-    """(n, 5) results of a whole batch in one planned launch."""
-    import torch
-    q = torch.from_numpy(batch.q_seqs).cuda()
-    r = torch.from_numpy(batch.r_seqs).cuda()
-    out = torch.zeros((5, batch.n_pairs), dtype=torch.int32, device=q.device)
-    plan = swgb.sw_plan_create(ctx, batch.q_offsets, batch.r_offsets, batch.matrix,
-                               batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED, 0)
-    swgb.sw_plan_execute(plan, q, r, out, None)
-    torch.cuda.synchronize()
-    swgb.sw_plan_destroy(plan)
-    return out.T.contiguous().cpu().numpy()
 
 
 # ------------------------------------------------------------------- our arm
@@ -477,12 +474,17 @@ def time_one_shot(swgb, torch, batch, dev, stream, steps, warmup):
 
     for _ in range(warmup):
         step()
+    step_t = []
     t0 = time.perf_counter()
     for _ in range(steps):
+        t1 = time.perf_counter()
         step()
+        step_t.append(time.perf_counter() - t1)
     dt = time.perf_counter() - t0
     h2d = int(qh.numel() + rh.numel() + 8 * (qoh.numel() + roh.numel()))
-    return dt, oh.numpy().T.copy(), h2d, int(oh.numel() * 4)
+    stats = {"min": min(step_t) * 1e3, "median": statistics.median(step_t) * 1e3,
+             "max": max(step_t) * 1e3}
+    return dt, oh.numpy().T.copy(), h2d, int(oh.numel() * 4), stats
 
 
 def measure_config(swgb, torch, ctx, k, dev, stream, flush, steps, tune_cache, sms):
@@ -669,9 +671,12 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         swgb.sw_plan_execute_host(eplan, qh, rh, oh, stream)
     barrier()
+    step_t = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         swgb.sw_plan_execute_host(eplan, qh, rh, oh, stream)
+        step_t.append(time.perf_counter() - t1)
     barrier()
     e2e_t = time.perf_counter() - t0
     e2e_same = bool(np.array_equal(oh.numpy().T, res))
@@ -679,6 +684,8 @@ def run_ours(args, rank, world, local):
     e2e = {"value": job_cells * args.steps / e2e_t / 1e9, "unit": "GCUPS",
            "h2d_bytes_per_step": int(q_in.nbytes + r_in.nbytes),
            "d2h_bytes_per_step": int(5 * 4 * batch.n_pairs), "identical_outputs": e2e_same,
+           "step_ms": {"min": min(step_t) * 1e3, "median": statistics.median(step_t) * 1e3,
+                       "max": max(step_t) * 1e3},
            "inputs": ("page-locked host buffers read in place by the kernels over the "
                       "coherent host link" if swgb.sw_ctx_host_in_place(ctx)
                       else "page-locked host buffers copied to the device each step")}
@@ -689,10 +696,10 @@ def run_ours(args, rank, world, local):
     # the timed region (fresh offsets uploaded every step)
     e2e_oneshot = None
     if not (args.packed or args.ends_only or args.no_s16x2 or world > 1):
-        ot, ores, oh2d, od2h = time_one_shot(swgb, torch, batch, dev, stream, args.steps,
-                                             args.warmup)
+        ot, ores, oh2d, od2h, ostats = time_one_shot(swgb, torch, batch, dev, stream, args.steps,
+                                                     args.warmup)
         e2e_oneshot = {"value": job_cells * args.steps / ot / 1e9, "unit": "GCUPS",
-                       "ms_per_step": ot / args.steps * 1e3,
+                       "ms_per_step": ot / args.steps * 1e3, "step_ms": ostats,
                        "h2d_bytes_per_step": oh2d, "d2h_bytes_per_step": od2h,
                        "identical_outputs": bool(np.array_equal(ores, res)),
                        "call": "sw_align_batch (device offsets; planned on the device)",
@@ -729,13 +736,16 @@ def run_ours(args, rank, world, local):
             configs[str(k)] = measure_config(swgb, torch, ctx, k, dev, stream, flush,
                                              args.config_steps, args.tune_cache, sms)
 
-    serve = None
+    serve = serve_staged = None
     if not args.no_serve and rank == 0 and world == 1 and not overridden:
-        if args.config == 1:
-            serve = serve_sweep(swgb, ctx, batch, res, args)
-        else:
-            dna = wl.gen_config(1)
-            serve = serve_sweep(swgb, ctx, dna, _batch_results(swgb, ctx, dna), args)
+        import oracle
+        dna = batch if args.config == 1 else wl.gen_config(1)
+        protein = wl.gen_config(2)
+        pools = {"dna": dna, "protein": protein}
+        expect = {k: oracle.align_workload(b, threads=cpu_cores()) for k, b in pools.items()}
+        serve = serve_sweep(swgb, ctx, pools, expect, args, resident=True)
+        if not args.no_serve_staged:
+            serve_staged = serve_sweep(swgb, ctx, pools, expect, args, resident=False)
     swgb.sw_ctx_destroy(ctx)
 
     cpu = None
@@ -765,7 +775,7 @@ def run_ours(args, rank, world, local):
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_oneshot": e2e_oneshot,
-                "configs": configs, "serve": serve, "cigar": cigar,
+                "configs": configs, "serve": serve, "serve_staged": serve_staged, "cigar": cigar,
                 "clocks": clk,
                 "gpu_launches": info["launches"] * args.steps}
         print(json.dumps(line), flush=True)

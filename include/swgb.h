@@ -402,23 +402,31 @@ int sw_static_status(int32_t *status, void *stream);
  * calls are bounded by timeouts).
  *
  * sw_server_create: a server on ctx's device with a device-memory budget of
- * budget_bytes (allocated once, at creation, as the arena that holds every
- * launch's sequences, tables, scratch and outputs), at most `streams`
- * launches on the GPU at a time (one stream each, 1..64), and a pinned host
- * staging pool of staging_bytes.  A worker thread forms launches whenever a
- * stream slot is free: the oldest queued request plus the later queued
- * requests with the same scoring (matrix, gap costs), up to 262144 pairs and
- * 4e9 cells per launch and what the arena has left.  Each launch is planned
- * as one batch of the batched path; launches on different slots overlap on
- * the device.  A request's device footprint is bounded at submission by its
- * sequences, 40 B of pair record and 20 B of outputs per pair, and the
- * strip-boundary scratch of its pairs at the narrowest lane-group width.
+ * budget_bytes (allocated once, at creation, as the arena that holds the
+ * resident pools and every launch's sequences, offsets, planning workspace
+ * and outputs), at most `streams` launches on the GPU at a time (one stream
+ * each, 1..64), and a pinned host staging pool of staging_bytes.  A worker
+ * thread forms launches whenever a stream slot is free: the oldest queued
+ * request plus the later queued requests from the same source (the same
+ * resident pool, or staged sequences with the same matrix and gap costs),
+ * up to 262144 pairs and 4e9 cells per launch and what the arena has left.
+ * Each launch is planned on the device, as sw_align_batch plans (no host
+ * planning); launches on different slots overlap on the device.
  *
  * sw_server_submit: queue a request given as HOST arrays (sequences,
  * offsets, matrix; copied into the staging pool before the call returns, so
  * the caller may reuse them).  Waits up to timeout_ms for staging space.
  * Errors: SW_EINVAL/SW_ERANGE as sw_plan_create; SW_EBUDGET if the request
- * alone needs more than the whole budget or staging pool; SW_ETIMEOUT.
+ * alone needs more than the budget (less the pools) or the staging pool;
+ * SW_ETIMEOUT.
+ *
+ * sw_server_add_pool: upload a batch (HOST arrays, as sw_server_submit) into
+ * the budget once, as resident pool *pool_id, for the server's lifetime
+ * (blocking copy).  SW_EBUDGET if it does not fit the free budget.
+ * sw_server_submit_pool: queue a request for pairs [first_pair, first_pair +
+ * n_pairs) of a resident pool, aligned with the pool's scoring; only the
+ * pairs' offsets go up and the results come back.  SW_ERANGE for a range
+ * outside the pool; otherwise as sw_server_submit.
  *
  * sw_server_wait: wait up to timeout_ms for a request, copy its results to
  * out_host (5 x n_pairs int32: scores, qend, rend, qstart, rstart) and
@@ -439,13 +447,20 @@ int sw_server_submit(sw_server *server, const uint8_t *q_seqs, const int64_t *q_
                      const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
                      const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
                      int32_t gap_extend, int32_t timeout_ms, int64_t *request_id);
+int sw_server_add_pool(sw_server *server, const uint8_t *q_seqs, const int64_t *q_offsets,
+                       const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                       const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                       int32_t gap_extend, int32_t *pool_id);
+int sw_server_submit_pool(sw_server *server, int32_t pool_id, int64_t first_pair,
+                          int32_t n_pairs, int32_t timeout_ms, int64_t *request_id);
 int sw_server_poll(sw_server *server, int64_t request_id, int32_t *done);
 int sw_server_wait(sw_server *server, int64_t request_id, int32_t timeout_ms, int32_t *out_host,
                    int64_t *done_ns);
 int sw_server_stats(sw_server *server, int64_t *completed, int64_t *in_flight, int64_t *queued,
                     int64_t *device_bytes_in_use, int64_t *device_bytes_peak);
 /* Launches the worker has started so far, the pairs they held and the host
- * milliseconds spent planning them (any pointer may be NULL). */
+ * milliseconds spent preparing them (offsets, copies and enqueueing; the
+ * planning itself runs on the device) (any pointer may be NULL). */
 int sw_server_launches(sw_server *server, int64_t *launches, int64_t *pairs_launched,
                        double *plan_ms);
 int sw_server_destroy(sw_server *server);

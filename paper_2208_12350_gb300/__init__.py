@@ -72,6 +72,9 @@ SIGNATURES = {
     "sw_server_create": ([_P, _I64, _I32, _I64, _PP], ctypes.c_int),
     "sw_server_submit": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32,
                           ctypes.POINTER(_I64)], ctypes.c_int),
+    "sw_server_add_pool": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32,
+                            ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_server_submit_pool": ([_P, _I32, _I64, _I32, _I32, ctypes.POINTER(_I64)], ctypes.c_int),
     "sw_server_poll": ([_P, _I64, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_server_wait": ([_P, _I64, _I32, _P, ctypes.POINTER(_I64)], ctypes.c_int),
     "sw_server_stats": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
@@ -381,6 +384,30 @@ def sw_server_submit(server: int, q_seqs, q_offsets, r_seqs, r_offsets, score_ma
                                    r.ctypes.data if r.size else None, ro.ctypes.data, len(qo) - 1,
                                    mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
                                    timeout_ms, ctypes.byref(rid)), "sw_server_submit")
+    return rid.value
+
+
+def sw_server_add_pool(server: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix,
+                       gap_open: int, gap_extend: int) -> int:
+    """Upload a batch (host arrays) as a resident pool; returns its id."""
+    q = np.ascontiguousarray(q_seqs, dtype=np.uint8)
+    r = np.ascontiguousarray(r_seqs, dtype=np.uint8)
+    qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
+    mat = _host_i8(score_matrix)
+    pid = _I32()
+    _check(load().sw_server_add_pool(server, q.ctypes.data if q.size else None, qo.ctypes.data,
+                                     r.ctypes.data if r.size else None, ro.ctypes.data,
+                                     len(qo) - 1, mat.ctypes.data, mat.shape[0], gap_open,
+                                     gap_extend, ctypes.byref(pid)), "sw_server_add_pool")
+    return pid.value
+
+
+def sw_server_submit_pool(server: int, pool_id: int, first_pair: int, n_pairs: int,
+                          timeout_ms: int = 60000) -> int:
+    """Queue pairs [first_pair, first_pair + n_pairs) of a resident pool; returns the request id."""
+    rid = _I64()
+    _check(load().sw_server_submit_pool(server, pool_id, first_pair, n_pairs, timeout_ms,
+                                        ctypes.byref(rid)), "sw_server_submit_pool")
     return rid.value
 
 

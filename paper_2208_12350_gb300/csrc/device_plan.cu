@@ -119,10 +119,18 @@ struct PairView {
     int route;  // 0 packed, 1 int32, 2 plain, 3 none
 };
 
-__device__ __forceinline__ PairView view_pair(const DevicePlanShape &S, const int64_t *qo,
-                                              const int64_t *ro, int i, bool *bad) {
+// Pair i's sequences: [qo[i], qe[i]) and [ro[i], re[i]), or CSR
+// ([qo[i], qo[i + 1]) ...) when the end arrays are NULL.
+struct Offsets {
+    const int64_t *qo, *ro, *qe, *re;
+};
+
+__device__ __forceinline__ PairView view_pair(const DevicePlanShape &S, const Offsets &off, int i,
+                                              bool *bad) {
     PairView v;
-    const int64_t q0 = qo[i], q1 = qo[i + 1], r0 = ro[i], r1 = ro[i + 1];
+    const int64_t q0 = off.qo[i], r0 = off.ro[i];
+    const int64_t q1 = off.qe ? off.qe[i] : off.qo[i + 1];
+    const int64_t r1 = off.re ? off.re[i] : off.ro[i + 1];
     const int64_t n = q1 - q0, m = r1 - r0;
     *bad = q0 < 0 || r0 < 0 || n < 0 || m < 0 || n > SW_MAX_LEN || m > SW_MAX_LEN;
     v.q = q0;
@@ -180,9 +188,8 @@ __device__ __forceinline__ void write_none(const Outputs &o, int id, bool ends_o
 }
 
 // 1. Routes, status, outputs of pairs with nothing to align, route cost sums.
-__global__ void __launch_bounds__(kThreads) dp_classify(const DevicePlanShape S, const int64_t *qo,
-                                                        const int64_t *ro, Header *hdr,
-                                                        int32_t *status, Outputs o) {
+__global__ void __launch_bounds__(kThreads) dp_classify(const DevicePlanShape S, const Offsets off,
+                                                        Header *hdr, int32_t *status, Outputs o) {
     __shared__ unsigned long long tot[2];
     if (threadIdx.x < 2) tot[threadIdx.x] = 0;
     __syncthreads();
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) dp_classify(const DevicePlanShape S,
     bool any_bad = false;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < S.n_pairs; i += gridDim.x * kThreads) {
         bool bad = false;
-        const PairView v = view_pair(S, qo, ro, i, &bad);
+        const PairView v = view_pair(S, off, i, &bad);
         any_bad |= bad;
         if (v.route == 3)
             write_none(o, i, S.ends_only);
@@ -250,9 +257,9 @@ __device__ __forceinline__ void tile_counts(int n, int shift, KeyFn key, uint32_
 
 // 2. Width classes, sort keys, per-bucket counts and work; digit counts of
 // the first radix pass.
-__global__ void __launch_bounds__(kThreads) dp_keys(const DevicePlanShape S, const int64_t *qo,
-                                                    const int64_t *ro, Header *hdr, uint16_t *keys0,
-                                                    uint32_t *counts1, int tiles) {
+__global__ void __launch_bounds__(kThreads) dp_keys(const DevicePlanShape S, const Offsets off,
+                                                    Header *hdr, uint16_t *keys0, uint32_t *counts1,
+                                                    int tiles) {
     __shared__ uint32_t hist[kWarps][kDigits];
     __shared__ unsigned long long bwork[kNumBuckets];
     __shared__ int32_t bcount[kNumBuckets];
@@ -264,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) dp_keys(const DevicePlanShape S, con
     const int lo = blockIdx.x * kTile, hi = min(S.n_pairs, lo + kTile);
     for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
         bool bad = false;
-        const PairView v = view_pair(S, qo, ro, i, &bad);
+        const PairView v = view_pair(S, off, i, &bad);
         int bucket = kBucketNone;
         uint32_t cost = 0;
         if (v.route < 2) {
@@ -453,8 +460,7 @@ __global__ void __launch_bounds__(kScanThreads) dp_scan_tables(const DevicePlanS
 __global__ void __launch_bounds__(kThreads) dp_scatter2(const DevicePlanShape S, int tiles,
                                                         const uint16_t *keys1, const uint32_t *vals1,
                                                         const uint32_t *offsets2,
-                                                        const int64_t *qo, const int64_t *ro,
-                                                        PairInfo *pairs) {
+                                                        const Offsets off, PairInfo *pairs) {
     __shared__ uint32_t hist[kWarps][kDigits];
     tile_scatter(
         S.n_pairs, 8, tiles, offsets2, [&](int k) { return (uint32_t)keys1[k]; },
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) dp_scatter2(const DevicePlanShape S,
             if ((int)(key >> 12) >= kBucketNone) return;
             const int i = (int)vals1[k];
             bool bad = false;
-            const PairView v = view_pair(S, qo, ro, i, &bad);
+            const PairView v = view_pair(S, off, i, &bad);
             pairs[pos] = PairInfo{v.q, v.r, -1, v.n, v.m, i, 0};
         },
         hist);
@@ -477,7 +483,8 @@ size_t device_plan_workspace_bytes(const DevicePlanShape &S) {
 
 int device_plan_shape(int32_t n_pairs, const int8_t *mat, int32_t A, int32_t go, int32_t ge,
                       int32_t mode, int sm_count, int narrow_log2g, double cap_fraction,
-                      int slot_words, DevicePlanShape *out, std::string *msg) {
+                      int slot_words, DevicePlanShape *out, std::string *msg,
+                      int min_pairs_per_warp) {
     DevicePlanShape S;
     std::memset(&S, 0, sizeof S);
     S.n_pairs = n_pairs;
@@ -497,7 +504,8 @@ int device_plan_shape(int32_t n_pairs, const int8_t *mat, int32_t A, int32_t go,
         smin = std::min(smin, (int)mat[i]);
     }
     const int sp = std::max(smax, 0);
-    const int64_t want_grid = std::max<int64_t>(1, ((int64_t)n_pairs + kGroupWarps - 1) / kGroupWarps);
+    const int64_t per_block = (int64_t)kGroupWarps * std::max(1, min_pairs_per_warp);
+    const int64_t want_grid = std::max<int64_t>(1, ((int64_t)n_pairs + per_block - 1) / per_block);
     // route 0: packed 16-bit form (32-bit profile words, else bytes)
     if (!S.all_plain && smin >= go && -go <= kMaxScaledGap && -ge <= kMaxScaledGap) {
         for (ProfileKind k : {ProfileKind::kPacked16, ProfileKind::kPacked16Bytes}) {
@@ -550,7 +558,9 @@ int device_plan_shape(int32_t n_pairs, const int8_t *mat, int32_t A, int32_t go,
 
 cudaError_t enqueue_device_plan(const DevicePlanShape &S, void *workspace, const int64_t *qo,
                                 const int64_t *ro, const uint8_t *q, const uint8_t *r,
-                                const Outputs &o, int32_t *status, cudaStream_t s) {
+                                const Outputs &o, int32_t *status, cudaStream_t s,
+                                const int64_t *qe, const int64_t *re) {
+    const Offsets off{qo, ro, qe, re};
     if (S.n_pairs <= 0) return cudaSuccess;
     const int tiles = (int)std::max<int64_t>(1, ((int64_t)S.n_pairs + kTile - 1) / kTile);
     const WsLayout L = ws_layout(S.n_pairs, tiles, S.scratch_words, S.guards != 0);
@@ -584,12 +594,12 @@ cudaError_t enqueue_device_plan(const DevicePlanShape &S, void *workspace, const
         return e;
     }
     const int cgrid = (int)std::min<int64_t>(((int64_t)S.n_pairs + kThreads - 1) / kThreads, 1024);
-    dp_classify<<<cgrid, kThreads, 0, s>>>(S, qo, ro, hdr, status, o);
-    dp_keys<<<tiles, kThreads, 0, s>>>(S, qo, ro, hdr, keys0, counts1, tiles);
+    dp_classify<<<cgrid, kThreads, 0, s>>>(S, off, hdr, status, o);
+    dp_keys<<<tiles, kThreads, 0, s>>>(S, off, hdr, keys0, counts1, tiles);
     dp_scan<<<1, kScanThreads, 0, s>>>(counts1, kDigits * tiles);
     dp_scatter1<<<tiles, kThreads, 0, s>>>(S.n_pairs, tiles, keys0, counts1, keys1, vals1, counts2);
     dp_scan_tables<<<1, kScanThreads, 0, s>>>(S, counts2, kDigits * tiles, hdr);
-    dp_scatter2<<<tiles, kThreads, 0, s>>>(S, tiles, keys1, vals1, counts2, qo, ro, pairs);
+    dp_scatter2<<<tiles, kThreads, 0, s>>>(S, tiles, keys1, vals1, counts2, off, pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     for (int rt = 0; rt < 2; ++rt) {

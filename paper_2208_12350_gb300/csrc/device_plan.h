@@ -35,18 +35,25 @@ struct DevicePlanShape {
 
 // Fills *out from the host-known arguments (queries the group kernels'
 // occupancy on the current device).  Arguments must already be checked.
+// min_pairs_per_warp: the grid gets at most one warp per this many pairs
+// (1: lowest latency; more: leave room for other launches on the GPU).
 int device_plan_shape(int32_t n_pairs, const int8_t *mat, int32_t A, int32_t go, int32_t ge,
                       int32_t mode, int sm_count, int narrow_log2g, double cap_fraction,
-                      int slot_words, DevicePlanShape *out, std::string *msg);
+                      int slot_words, DevicePlanShape *out, std::string *msg,
+                      int min_pairs_per_warp = 1);
 
 // Device bytes of the planning workspace (tables, sort buffers, slots).
 size_t device_plan_workspace_bytes(const DevicePlanShape &S);
 
 // Enqueues planning and alignment on s: workspace (256-byte aligned, at
 // least device_plan_workspace_bytes) is used for the call's duration on s.
+// Pair i's sequences are q[qo[i] .. qo[i + 1]) and r[ro[i] .. ro[i + 1])
+// (CSR), or q[qo[i] .. qe[i]) and r[ro[i] .. re[i]) when qe and re are given
+// (pairs gathered from anywhere in q and r).
 cudaError_t enqueue_device_plan(const DevicePlanShape &S, void *workspace, const int64_t *qo,
                                 const int64_t *ro, const uint8_t *q, const uint8_t *r,
-                                const Outputs &o, int32_t *status, cudaStream_t s);
+                                const Outputs &o, int32_t *status, cudaStream_t s,
+                                const int64_t *qe = nullptr, const int64_t *re = nullptr);
 
 // Strip-boundary words per lane of the one-shot call's group slots: a group
 // of G lanes holds the boundary rows of sequences up to about 514 G

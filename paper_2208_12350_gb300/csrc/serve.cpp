@@ -1,27 +1,28 @@
 // Serving loop: continuous batching of alignment requests.
 //
-// A request is a batch of pairs on the host.  sw_server_submit checks it,
-// copies its sequences into a pinned staging pool and queues it.  A worker
-// thread turns the queue into launches: whenever a stream slot is free it
-// takes the oldest queued request together with the later queued requests
-// that share its scoring (matrix and gap costs), up to a cap on pairs and
-// cells and to what the device arena has left, plans them as one batch
-// (pairs are independent, so a pair's results do not depend on its batch
-// mates) and runs that batch on the slot's stream: sequences copied into
-// one arena block, the persistent kernel, each request's outputs copied
-// back into its staging area.  The arena is one device allocation of the
-// server's memory budget, made at creation.  Under light load a launch
-// holds one request and is planned for latency (up to one warp per pair);
-// while other launches are in flight it is planned to fill lane groups
-// instead, and under heavy load the queue grows between launches, so each
-// launch takes many requests and runs at the batched kernel's throughput.
-// Forming a launch is the worker's; planning and enqueueing it (milliseconds
-// of host work for tens of thousands of pairs) is done by one of eight
-// planner threads, so launches are planned in parallel.  When a launch's
-// completion event fires the worker frees its arena block and slot and
-// wakes the waiters.
+// A request is a batch of pairs: either given on the host (sw_server_submit
+// checks it and copies its sequences into a pinned staging pool) or a range
+// of pairs of a resident pool (sw_server_add_pool uploads a batch once into
+// the device budget; sw_server_submit_pool names a pair range of it, so only
+// offsets and results move).  A worker thread turns the queue into
+// launches: whenever a stream slot is free it takes the oldest queued
+// request together with the later queued requests from the same source (the
+// same pool, or staged sequences with the same scoring), up to a cap on
+// pairs and cells and to what the device arena has left, and runs them as
+// one batch (pairs are independent, so a pair's results do not depend on
+// its batch mates) on the slot's stream: the merged offsets and any staged
+// sequences copied into one arena block, the device planner's kernels (the
+// one-shot call's: routes, lane-group widths, longest-first radix sort,
+// queue tables) and the alignment kernels, then each request's outputs
+// copied back into its staging area.  The host does no planning: it only
+// sizes the grid, for latency (up to one warp per pair) on an idle GPU and
+// for throughput (sixteen pairs per warp) while other launches run.  Under
+// heavy load the queue grows between launches, so each launch takes many
+// requests and runs at the batched kernel's throughput.  Launches are
+// enqueued by eight helper threads; when a launch's completion event fires
+// the worker frees its arena block and slot and wakes the waiters.
 //
-// Every wait is bounded: sw_server_wait and sw_server_submit take a timeout
+// Every wait is bounded: sw_server_wait and the submit calls take a timeout
 // and return SW_ETIMEOUT instead of blocking forever.
 #include <cuda_runtime.h>
 
@@ -38,6 +39,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "device_plan.h"
 #include "sw_internal.h"
 #include "swgb.h"
 
@@ -101,9 +103,6 @@ class Arena {
 // enough cells that a small request merged into it still returns quickly.
 constexpr int64_t kLaunchMaxPairs = 1 << 18;
 constexpr double kLaunchMaxCells = 4e9;
-// The worker plans every launch itself, so its schedule simulation looks at
-// fewer pairs than a one-off plan's.
-constexpr int kLaunchPlanSample = 1024;
 
 struct Request {
     int64_t id = 0;
@@ -113,12 +112,16 @@ struct Request {
     std::vector<int64_t> q_off, r_off;  // the request's own CSR offsets
     int64_t q_bytes = 0, r_bytes = 0;
     double cells = 0;
-    size_t dev_bound = 0;  // device bytes the request can add to a launch
     // staging pool layout: q | r | out (5 x n_pairs int32)
     size_t stage_off = 0, st_q = 0, st_r = 0, st_out = 0, st_total = 0;
     bool done = false;
     int status = SW_OK;
     int64_t done_ns = 0;  // CLOCK_MONOTONIC when the worker saw it finish
+    // resident-pool request: pairs [first, first + n_pairs) of pool `pool`
+    // (-1: the request's own sequences, staged at submission)
+    int pool = -1;
+    int64_t first = 0;
+    int64_t lmax = 0;  // longest sequence of the request's pairs
 };
 
 bool same_scoring(const Request &a, const Request &b) {
@@ -126,13 +129,34 @@ bool same_scoring(const Request &a, const Request &b) {
            std::memcmp(a.mat, b.mat, (size_t)a.A * a.A) == 0;
 }
 
-// Byte layout of one launch's arena block.
-struct Layout {
-    size_t q = 0, r = 0, pairs = 0, classes = 0, plain = 0, counters = 0, scratch = 0, out = 0,
-           tables_end = 0, total = 0;
+// Requests that one launch can merge: the same resident pool, or both with
+// staged sequences and the same scoring.
+bool same_source(const Request &a, const Request &b) {
+    return a.pool == b.pool && (a.pool >= 0 || same_scoring(a, b));
+}
+
+// A batch of pairs kept on the device for the server's lifetime, in one
+// arena block (query residues, then reference residues); requests name
+// pair ranges of it and move only offsets and results.
+struct Pool {
+    int A = 0, go = 0, ge = 0;
+    int8_t mat[kMaxAlphabet * kMaxAlphabet] = {0};
+    size_t dev_off = 0, dev_bytes = 0;
+    size_t r_at = 0;                    // reference residues' offset in the block
+    std::vector<int64_t> q_off, r_off;  // n_pairs + 1 each, from the block's q / r start
+    int64_t n_pairs = 0;
 };
 
-Layout layout_of(const HostPlan &hp, int64_t n_pairs) {
+// Byte layout of one launch's arena block: staged sequences, the pairs'
+// start (and, for pool launches, end) offsets, the device planner's
+// workspace (tables, sort buffers, strip-boundary slots) and the outputs.
+struct Layout {
+    size_t q = 0, r = 0, qo = 0, ro = 0, qe = 0, re = 0, ws = 0, out = 0, total = 0;
+    size_t offsets_bytes = 0;  // the offset arrays, contiguous from qo
+};
+
+Layout layout_of(const DevicePlanShape &shape, int64_t n_pairs, size_t q_bytes, size_t r_bytes,
+                 bool pooled) {
     Layout L;
     size_t at = 0;
     auto take = [&](size_t bytes) {
@@ -140,28 +164,36 @@ Layout layout_of(const HostPlan &hp, int64_t n_pairs) {
         at = align_up(at + bytes);
         return o;
     };
-    L.q = take((size_t)hp.q_bytes);
-    L.r = take((size_t)hp.r_bytes);
-    L.pairs = take(hp.pairs.size() * sizeof(PairInfo));
-    L.classes = take(hp.classes.size() * sizeof(ClassInfo));
-    L.plain = take(hp.plain.size() * sizeof(PairInfo));
-    L.tables_end = at;
-    L.counters = take(kMaxClasses * sizeof(int32_t));
-    L.scratch = take((size_t)hp.scratch_words * sizeof(uint32_t));
+    L.q = take(q_bytes);
+    L.r = take(r_bytes);
+    const size_t arr = (size_t)(n_pairs + 1) * sizeof(int64_t);
+    L.qo = take(arr);
+    L.ro = take(arr);
+    if (pooled) {
+        L.qe = take(arr);
+        L.re = take(arr);
+    }
+    L.offsets_bytes = at - L.qo;
+    L.ws = take(device_plan_workspace_bytes(shape));
     L.out = take((size_t)5 * n_pairs * sizeof(int32_t));
     L.total = at;
     return L;
 }
 
-// Upper bound on what a request adds to a launch's block: its sequences,
-// pair records, worst-case strip scratch, outputs and alignment slack.  The
-// classes table and counters (fixed, small) are covered by kLaunchFixed.
-size_t request_bound(int64_t q_bytes, int64_t r_bytes, int64_t n_pairs, int64_t scratch_words) {
-    return (size_t)q_bytes + (size_t)r_bytes + (size_t)n_pairs * sizeof(PairInfo) +
-           (size_t)scratch_words * sizeof(uint32_t) + (size_t)n_pairs * 5 * sizeof(int32_t) +
-           8 * kAlign;
+// Launches are planned on the device; the host only sizes the grid and the
+// strip-boundary slots: up to one warp per pair on an idle GPU (latency:
+// the planner then gives pairs wide groups, so slots sized for 32-lane
+// groups of the launch's longest sequence), sixteen pairs per warp while
+// other launches run (throughput: slots for 2-lane groups, at most the
+// one-shot call's).  A pair whose need exceeds the slots takes wider groups.
+int launch_shape(const Request &head, int64_t n_pairs, int64_t lmax, int sms, bool gpu_busy,
+                 DevicePlanShape *shape, std::string *msg) {
+    const int64_t bw = 2 * ((lmax + 3) & ~(int64_t)3) + 4;
+    const int G = gpu_busy ? 2 : 32;
+    const int64_t slot = std::min<int64_t>(((bw + G - 1) / G + 3) & ~(int64_t)3, kOneShotSlotWords);
+    return device_plan_shape((int32_t)n_pairs, head.mat, head.A, head.go, head.ge, SW_MODE_AUTO,
+                             sms, -1, 0.5, (int)slot, shape, msg, gpu_busy ? (32 >> kMinLog2G) : 1);
 }
-constexpr size_t kLaunchFixed = 8 * kAlign + kMaxClasses * (sizeof(ClassInfo) + sizeof(int32_t));
 
 struct Launch {
     std::vector<std::shared_ptr<Request>> reqs;
@@ -186,12 +218,13 @@ struct sw_server {
     int device = 0, sms = 0;
     unsigned char *d_arena = nullptr, *h_pool = nullptr;
     int32_t *d_status = nullptr;
-    std::unique_ptr<Arena> arena, pool;
+    std::unique_ptr<Arena> arena, staging;  // device budget, pinned staging pool
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
     std::vector<std::unique_ptr<Launch>> slots;  // in flight, by slot
-    std::vector<unsigned char *> h_tables;       // pinned per-slot table buffers
+    std::vector<unsigned char *> h_tables;       // pinned per-slot offset buffers
     std::vector<size_t> h_tables_cap;
+    std::vector<std::unique_ptr<Pool>> pools;   // resident pools, by id
     std::deque<std::shared_ptr<Request>> queue;  // oldest first
     std::unordered_map<int64_t, std::shared_ptr<Request>> all;
     std::mutex mu;
@@ -207,30 +240,46 @@ struct sw_server {
 };
 
 // Pops the requests of the next launch from the queue (the oldest request
-// and later ones with the same scoring, within the caps and the arena's
-// largest free block).  Caller holds the mutex.
-static std::vector<std::shared_ptr<Request>> take_batch(sw_server *S) {
+// and later ones from the same source - the same resident pool, or staged
+// sequences with the same scoring - within the caps and the arena's
+// largest free block) and returns the block size the launch needs.
+// Caller holds the mutex.
+static std::vector<std::shared_ptr<Request>> take_batch(sw_server *S, bool gpu_busy,
+                                                        size_t *bytes_out) {
     std::vector<std::shared_ptr<Request>> out;
     const size_t room = S->arena->largest_free();
-    size_t bytes = kLaunchFixed;
-    int64_t pairs = 0;
+    size_t bytes = 0, qb = 0, rb = 0;
+    int64_t pairs = 0, lmax = 0;
     double cells = 0;
     for (auto it = S->queue.begin(); it != S->queue.end();) {
         const auto &r = *it;
-        if (!out.empty() && !same_scoring(*out.front(), *r)) {
+        if (!out.empty() && !same_source(*out.front(), *r)) {
             ++it;
             continue;
         }
-        if (bytes + r->dev_bound > room) break;
         if (!out.empty() && (pairs + r->n_pairs > kLaunchMaxPairs ||
                              cells + r->cells > kLaunchMaxCells))
             break;
-        bytes += r->dev_bound;
+        DevicePlanShape shape;
+        std::string msg;
+        const Request &head = out.empty() ? *r : *out.front();
+        if (launch_shape(head, pairs + r->n_pairs, std::max(lmax, r->lmax), S->sms, gpu_busy,
+                         &shape, &msg) != SW_OK)
+            break;
+        const size_t b = layout_of(shape, pairs + r->n_pairs, qb + (size_t)r->q_bytes,
+                                   rb + (size_t)r->r_bytes, r->pool >= 0)
+                             .total;
+        if (b > room) break;
+        bytes = b;
+        lmax = std::max(lmax, r->lmax);
         pairs += r->n_pairs;
+        qb += (size_t)r->q_bytes;
+        rb += (size_t)r->r_bytes;
         cells += r->cells;
         out.push_back(r);
         it = S->queue.erase(it);
     }
+    *bytes_out = bytes;
     return out;
 }
 
@@ -242,60 +291,46 @@ static void fail_launch(sw_server *S, Launch &L, cudaError_t e, int slot) {
     cudaEventRecord(S->events[slot], S->streams[slot]);
 }
 
-// Plans and enqueues one launch on the slot's stream.  Called with the
-// mutex released: only the worker touches the slot and the launch.
+// Plans and enqueues one launch on the slot's stream: the merged offsets go
+// up through the slot's pinned buffer, staged sequences from the staging
+// pool (a pool launch reads its pool's resident sequences instead), then the
+// device planner and the alignment kernels run on the stream, and each
+// request's outputs come back with one strided copy.  Called with the mutex
+// released: only this thread touches the slot and the launch.
 static void start_launch(sw_server *S, Launch &L, int slot, bool gpu_busy) {
     cudaStream_t s = S->streams[slot];
     const Request &head = *L.reqs.front();
-    // merged CSR offsets: the requests' sequences one after another
-    int64_t n = 0;
-    for (auto &r : L.reqs) n += r->n_pairs;
-    std::vector<int64_t> qo((size_t)n + 1), ro((size_t)n + 1);
-    {
-        int64_t k = 0, qb = 0, rb = 0;
-        for (auto &r : L.reqs) {
-            for (int i = 0; i < r->n_pairs; ++i, ++k) {
-                qo[k] = qb + r->q_off[i];
-                ro[k] = rb + r->r_off[i];
-            }
-            qb += r->q_bytes;
-            rb += r->r_bytes;
-        }
-        qo[n] = qb;
-        ro[n] = rb;
-    }
-    HostPlan hp;
-    std::string msg;
+    const Pool *pool = head.pool >= 0 ? S->pools[(size_t)head.pool].get() : nullptr;
     const auto t_plan = std::chrono::steady_clock::now();
-    int rc = make_host_plan(qo.data(), ro.data(), (int32_t)n, head.mat, head.A, head.go, head.ge,
-                            SW_MODE_AUTO, S->sms, -1, 0.5, &hp, &msg,
-                            gpu_busy ? (32 >> kMinLog2G) : 1, kLaunchPlanSample);
-    const Layout Lay = layout_of(hp, n);
-    {
-        const double ms = std::chrono::duration<double, std::milli>(
-                              std::chrono::steady_clock::now() - t_plan).count();
-        std::lock_guard<std::mutex> g(S->mu);
-        S->plan_ms += ms;
-        S->pairs_launched += n;
+    int64_t n = 0, lmax = 0;
+    size_t qb_total = 0, rb_total = 0;
+    for (auto &r : L.reqs) {
+        n += r->n_pairs;
+        lmax = std::max(lmax, r->lmax);
+        qb_total += (size_t)r->q_bytes;
+        rb_total += (size_t)r->r_bytes;
     }
+    DevicePlanShape shape;
+    std::string msg;
+    int rc = launch_shape(head, n, lmax, S->sms, gpu_busy, &shape, &msg);
+    const Layout Lay = layout_of(shape, n, qb_total, rb_total, pool != nullptr);
     if (rc != SW_OK || Lay.total > L.dev_bytes) {
-        // cannot happen for checked requests within their bound; fail loudly
+        // cannot happen for a launch sized by take_batch; fail loudly
         S->worker_error = rc != SW_OK ? msg : "launch exceeds its arena block";
         for (auto &r : L.reqs) r->status = rc != SW_OK ? rc : SW_ENOMEM;
         cudaEventRecord(S->events[slot], s);
         return;
     }
-    unsigned char *d = S->d_arena + L.dev_off;
-    // tables through a pinned per-slot buffer (the slot is idle, so the
-    // buffer's previous contents are no longer being copied)
-    const size_t tb = Lay.tables_end - Lay.pairs;
+    // the offsets, built in the slot's pinned buffer (the slot is idle, so
+    // the buffer's previous contents are no longer being copied)
+    const size_t tb = Lay.offsets_bytes;
     if (S->h_tables_cap[slot] < tb) {
         cudaFreeHost(S->h_tables[slot]);
         S->h_tables[slot] = nullptr;
         S->h_tables_cap[slot] = 0;
         if (cudaMallocHost(&S->h_tables[slot], std::max(tb, (size_t)1 << 20)) != cudaSuccess) {
             cudaGetLastError();
-            S->worker_error = "cannot allocate pinned table buffer";
+            S->worker_error = "cannot allocate pinned offset buffer";
             for (auto &r : L.reqs) r->status = SW_ENOMEM;
             cudaEventRecord(S->events[slot], s);
             return;
@@ -303,15 +338,34 @@ static void start_launch(sw_server *S, Launch &L, int slot, bool gpu_busy) {
         S->h_tables_cap[slot] = std::max(tb, (size_t)1 << 20);
     }
     unsigned char *ht = S->h_tables[slot];
-    if (!hp.pairs.empty())
-        std::memcpy(ht + (Lay.pairs - Lay.pairs), hp.pairs.data(), hp.pairs.size() * sizeof(PairInfo));
-    if (!hp.classes.empty())
-        std::memcpy(ht + (Lay.classes - Lay.pairs), hp.classes.data(),
-                    hp.classes.size() * sizeof(ClassInfo));
-    if (!hp.plain.empty())
-        std::memcpy(ht + (Lay.plain - Lay.pairs), hp.plain.data(), hp.plain.size() * sizeof(PairInfo));
-    cudaError_t e = cudaSuccess;
+    int64_t *qo = reinterpret_cast<int64_t *>(ht);
+    int64_t *ro = reinterpret_cast<int64_t *>(ht + (Lay.ro - Lay.qo));
+    int64_t *qe = pool ? reinterpret_cast<int64_t *>(ht + (Lay.qe - Lay.qo)) : nullptr;
+    int64_t *re = pool ? reinterpret_cast<int64_t *>(ht + (Lay.re - Lay.qo)) : nullptr;
     {
+        int64_t k = 0, qb = 0, rb = 0;
+        for (auto &r : L.reqs) {
+            for (int i = 0; i < r->n_pairs; ++i, ++k) {
+                if (pool) {
+                    const int64_t p = r->first + i;
+                    qo[k] = pool->q_off[(size_t)p];
+                    qe[k] = pool->q_off[(size_t)p + 1];
+                    ro[k] = pool->r_off[(size_t)p];
+                    re[k] = pool->r_off[(size_t)p + 1];
+                } else {
+                    qo[k] = qb + r->q_off[i];
+                    ro[k] = rb + r->r_off[i];
+                }
+            }
+            qb += r->q_bytes;
+            rb += r->r_bytes;
+        }
+        qo[n] = pool ? 0 : qb;
+        ro[n] = pool ? 0 : rb;
+    }
+    unsigned char *d = S->d_arena + L.dev_off;
+    cudaError_t e = cudaSuccess;
+    if (!pool) {
         size_t qb = 0, rb = 0;
         for (auto &r : L.reqs) {
             const unsigned char *h = S->h_pool + r->stage_off;
@@ -325,19 +379,24 @@ static void start_launch(sw_server *S, Launch &L, int slot, bool gpu_busy) {
             rb += (size_t)r->r_bytes;
         }
     }
-    if (e == cudaSuccess && tb)
-        e = cudaMemcpyAsync(d + Lay.pairs, ht, tb, cudaMemcpyHostToDevice, s);
-    DeviceTables t;
-    t.pairs = reinterpret_cast<const PairInfo *>(d + Lay.pairs);
-    t.classes = reinterpret_cast<const ClassInfo *>(d + Lay.classes);
-    t.plain = reinterpret_cast<const PairInfo *>(d + Lay.plain);
-    t.counters = reinterpret_cast<int32_t *>(d + Lay.counters);
-    t.scratch = reinterpret_cast<uint32_t *>(d + Lay.scratch);
-    t.status = S->d_status;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + Lay.qo, ht, tb, cudaMemcpyHostToDevice, s);
+    const uint8_t *qbase = pool ? S->d_arena + pool->dev_off : d + Lay.q;
+    const uint8_t *rbase = pool ? S->d_arena + pool->dev_off + pool->r_at : d + Lay.r;
     int32_t *o = reinterpret_cast<int32_t *>(d + Lay.out);
     const Outputs outs{o, o + n, o + 2 * n, o + 3 * n, o + 4 * n};
     if (e == cudaSuccess)
-        e = enqueue_plan(hp, t, d + Lay.q, d + Lay.r, outs, head.mat, head.A, head.go, head.ge, s);
+        e = enqueue_device_plan(shape, d + Lay.ws, reinterpret_cast<const int64_t *>(d + Lay.qo),
+                                reinterpret_cast<const int64_t *>(d + Lay.ro), qbase, rbase, outs,
+                                S->d_status, s,
+                                pool ? reinterpret_cast<const int64_t *>(d + Lay.qe) : nullptr,
+                                pool ? reinterpret_cast<const int64_t *>(d + Lay.re) : nullptr);
+    {
+        const double ms = std::chrono::duration<double, std::milli>(
+                              std::chrono::steady_clock::now() - t_plan).count();
+        std::lock_guard<std::mutex> g(S->mu);
+        S->plan_ms += ms;
+        S->pairs_launched += n;
+    }
     {
         // each request's 5 output rows: one strided copy into its staging area
         int64_t first = 0;
@@ -397,10 +456,9 @@ static void worker_loop(sw_server *S) {
                     slot = (int)k;
             }
             if (slot < 0) break;
-            std::vector<std::shared_ptr<Request>> reqs = take_batch(S);
+            size_t bytes = 0;
+            std::vector<std::shared_ptr<Request>> reqs = take_batch(S, busy, &bytes);
             if (reqs.empty()) break;  // wait for memory to free up
-            size_t bytes = kLaunchFixed;
-            for (auto &r : reqs) bytes += r->dev_bound;
             size_t off = 0;
             if (!S->arena->alloc(bytes, &off)) {  // cannot fail: checked above
                 for (auto it = reqs.rbegin(); it != reqs.rend(); ++it) S->queue.push_front(*it);
@@ -451,6 +509,22 @@ static void planner_loop(sw_server *S) {
     }
 }
 
+// Whether a launch of this request alone fits the arena (less the pools).
+static bool fits_budget(sw_server *S, const Request &req) {
+    DevicePlanShape shape;
+    std::string msg;
+    if (launch_shape(req, req.n_pairs, req.lmax, S->sms, false, &shape, &msg) != SW_OK) return false;
+    const size_t need = layout_of(shape, req.n_pairs, (size_t)req.q_bytes, (size_t)req.r_bytes,
+                                  req.pool >= 0)
+                            .total;
+    size_t pooled = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto &p : S->pools) pooled += p->dev_bytes;
+    }
+    return need + pooled <= S->arena->size();
+}
+
 extern "C" {
 
 int sw_server_create(sw_ctx *ctx, int64_t budget_bytes, int32_t streams, int64_t staging_bytes,
@@ -477,7 +551,7 @@ int sw_server_create(sw_ctx *ctx, int64_t budget_bytes, int32_t streams, int64_t
     }
     cudaMemset(S->d_status, 0, sizeof(int32_t));
     S->arena.reset(new Arena((size_t)budget_bytes));
-    S->pool.reset(new Arena((size_t)staging_bytes));
+    S->staging.reset(new Arena((size_t)staging_bytes));
     S->streams.resize(streams);
     S->events.resize(streams);
     S->slots.resize(streams);
@@ -521,24 +595,26 @@ int sw_server_submit(sw_server *S, const uint8_t *q_seqs, const int64_t *q_offse
     }
     req->q_bytes -= q_offsets[0];
     req->r_bytes -= r_offsets[0];
-    for (int32_t i = 0; i < n_pairs; ++i)
-        req->cells += (double)(req->q_off[i + 1] - req->q_off[i]) *
-                      (double)(req->r_off[i + 1] - req->r_off[i]);
-    req->dev_bound = request_bound(req->q_bytes, req->r_bytes, n_pairs, scratch_words);
-    if (req->dev_bound + kLaunchFixed > S->arena->size())
+    for (int32_t i = 0; i < n_pairs; ++i) {
+        const int64_t a = req->q_off[i + 1] - req->q_off[i], b = req->r_off[i + 1] - req->r_off[i];
+        req->cells += (double)a * (double)b;
+        req->lmax = std::max(req->lmax, std::max(a, b));
+    }
+    (void)scratch_words;
+    if (!fits_budget(S, *req))
         return set_error(SW_EBUDGET, "sw_server_submit: request needs more device memory than the "
                                      "server's whole budget");
     req->st_q = 0;
     req->st_r = align_up((size_t)req->q_bytes);
     req->st_out = req->st_r + align_up((size_t)req->r_bytes);
     req->st_total = req->st_out + (size_t)5 * n_pairs * sizeof(int32_t);
-    if (req->st_total > S->pool->size())
+    if (req->st_total > S->staging->size())
         return set_error(SW_EBUDGET, "sw_server_submit: request larger than the staging pool");
     std::unique_lock<std::mutex> lk(S->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
-    while (!S->pool->alloc(req->st_total, &req->stage_off)) {
+    while (!S->staging->alloc(req->st_total, &req->stage_off)) {
         if (S->cv_space.wait_until(lk, deadline) == std::cv_status::timeout) {
-            if (!S->pool->alloc(req->st_total, &req->stage_off))
+            if (!S->staging->alloc(req->st_total, &req->stage_off))
                 return set_error(SW_ETIMEOUT,
                                  "sw_server_submit: staging pool full until the timeout");
             break;
@@ -549,6 +625,102 @@ int sw_server_submit(sw_server *S, const uint8_t *q_seqs, const int64_t *q_offse
     if (req->q_bytes) std::memcpy(h + req->st_q, q_seqs + q_offsets[0], (size_t)req->q_bytes);
     if (req->r_bytes) std::memcpy(h + req->st_r, r_seqs + r_offsets[0], (size_t)req->r_bytes);
     lk.lock();
+    req->id = S->next_id++;
+    *request_id = req->id;
+    S->all[req->id] = req;
+    S->queue.push_back(req);
+    S->cv_work.notify_one();
+    return SW_OK;
+}
+
+int sw_server_add_pool(sw_server *S, const uint8_t *q_seqs, const int64_t *q_offsets,
+                       const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                       const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                       int32_t gap_extend, int32_t *pool_id) {
+    if (!S || !pool_id || n_pairs < 1) return set_error(SW_EINVAL, "sw_server_add_pool: bad argument");
+    std::string msg;
+    int64_t qb = 0, rb = 0, scratch_words = 0;
+    int rc = check_batch(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
+                         gap_extend, &qb, &rb, &scratch_words, &msg);
+    if (rc != SW_OK) return set_error(rc, ("sw_server_add_pool: " + msg).c_str());
+    if ((qb > q_offsets[0] && !q_seqs) || (rb > r_offsets[0] && !r_seqs))
+        return set_error(SW_EINVAL, "sw_server_add_pool: NULL sequences");
+    auto P = std::make_unique<Pool>();
+    P->A = alphabet_size;
+    P->go = gap_open;
+    P->ge = gap_extend;
+    std::memcpy(P->mat, score_matrix, (size_t)alphabet_size * alphabet_size);
+    P->n_pairs = n_pairs;
+    P->q_off.resize((size_t)n_pairs + 1);
+    P->r_off.resize((size_t)n_pairs + 1);
+    for (int32_t i = 0; i <= n_pairs; ++i) {
+        P->q_off[i] = q_offsets[i] - q_offsets[0];
+        P->r_off[i] = r_offsets[i] - r_offsets[0];
+    }
+    const size_t qn = (size_t)(qb - q_offsets[0]), rn = (size_t)(rb - r_offsets[0]);
+    P->r_at = align_up(qn);
+    P->dev_bytes = P->r_at + align_up(rn);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (!S->arena->alloc(P->dev_bytes, &P->dev_off))
+            return set_error(SW_EBUDGET, "sw_server_add_pool: the pool does not fit the free budget");
+    }
+    unsigned char *d = S->d_arena + P->dev_off;
+    cudaError_t e = cudaSuccess;
+    if (qn) e = cudaMemcpy(d, q_seqs + q_offsets[0], qn, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && rn) e = cudaMemcpy(d + P->r_at, r_seqs + r_offsets[0], rn, cudaMemcpyHostToDevice);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (e != cudaSuccess) {
+        S->arena->release(P->dev_off, P->dev_bytes);
+        return set_error(SW_ECUDA, "sw_server_add_pool: copy to the device failed");
+    }
+    *pool_id = (int32_t)S->pools.size();
+    S->pools.push_back(std::move(P));
+    return SW_OK;
+}
+
+int sw_server_submit_pool(sw_server *S, int32_t pool_id, int64_t first_pair, int32_t n_pairs,
+                          int32_t timeout_ms, int64_t *request_id) {
+    if (!S || !request_id || n_pairs < 1) return set_error(SW_EINVAL, "sw_server_submit_pool: bad argument");
+    auto req = std::make_shared<Request>();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (pool_id < 0 || pool_id >= (int32_t)S->pools.size())
+            return set_error(SW_EINVAL, "sw_server_submit_pool: unknown pool");
+        const Pool &P = *S->pools[(size_t)pool_id];
+        if (first_pair < 0 || first_pair + n_pairs > P.n_pairs)
+            return set_error(SW_ERANGE, "sw_server_submit_pool: pair range outside the pool");
+        req->A = P.A;
+        req->go = P.go;
+        req->ge = P.ge;
+        std::memcpy(req->mat, P.mat, sizeof P.mat);
+        for (int64_t p = first_pair; p < first_pair + n_pairs; ++p) {
+            const int64_t a = P.q_off[(size_t)p + 1] - P.q_off[(size_t)p];
+            const int64_t b = P.r_off[(size_t)p + 1] - P.r_off[(size_t)p];
+            req->cells += (double)a * (double)b;
+            req->lmax = std::max(req->lmax, std::max(a, b));
+        }
+    }
+    req->pool = pool_id;
+    req->first = first_pair;
+    req->n_pairs = n_pairs;
+    req->st_q = req->st_r = req->st_out = 0;  // only the outputs are staged
+    req->st_total = (size_t)5 * n_pairs * sizeof(int32_t);
+    if (!fits_budget(S, *req))
+        return set_error(SW_EBUDGET, "sw_server_submit_pool: request needs more device memory "
+                                     "than the server's budget leaves");
+    if (req->st_total > S->staging->size())
+        return set_error(SW_EBUDGET, "sw_server_submit_pool: request larger than the staging pool");
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (!S->staging->alloc(req->st_total, &req->stage_off)) {
+        if (S->cv_space.wait_until(lk, deadline) == std::cv_status::timeout) {
+            if (!S->staging->alloc(req->st_total, &req->stage_off))
+                return set_error(SW_ETIMEOUT,
+                                 "sw_server_submit_pool: staging pool full until the timeout");
+            break;
+        }
+    }
     req->id = S->next_id++;
     *request_id = req->id;
     S->all[req->id] = req;
@@ -582,7 +754,7 @@ int sw_server_wait(sw_server *S, int64_t request_id, int32_t timeout_ms, int32_t
                     (size_t)5 * req->n_pairs * sizeof(int32_t));
         if (done_ns) *done_ns = req->done_ns;
     }
-    S->pool->release(req->stage_off, req->st_total);
+    S->staging->release(req->stage_off, req->st_total);
     S->all.erase(it);
     S->cv_space.notify_all();
     if (status != SW_OK)

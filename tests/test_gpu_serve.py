@@ -162,3 +162,86 @@ def test_queued_requests_merge_into_one_launch(gpu_lib, ctx):
         assert np.array_equal(o, oracle.align_workload(b))
     idx = np.arange(0, big.n_pairs, 211)
     assert np.array_equal(out_big[idx], oracle.align_workload(big, idx=idx))
+
+
+def test_resident_pools_equal_oracle(gpu_lib, ctx):
+    """Sequences uploaded once as resident pools; requests name pair ranges
+    (some overlapping, some at the pools' ends), mixed with staged requests,
+    from several client threads: every result equals the oracle's."""
+    swgb = gpu_lib
+    dna = wl.gen_config(1, n_pairs=6000)
+    prot = wl.gen_config(2, n_pairs=2000)
+    exp = {"dna": oracle.align_workload(dna), "protein": oracle.align_workload(prot)}
+    srv = swgb.sw_server_create(ctx, 2 << 30, streams=6, staging_bytes=1 << 28)
+    rng = np.random.default_rng(77)
+    jobs = []
+    for k in range(60):
+        kind = "dna" if k % 2 == 0 else "protein"
+        total = dna.n_pairs if kind == "dna" else prot.n_pairs
+        n = int(min(total, max(1, np.exp(rng.uniform(0, np.log(1500))))))
+        first = int(rng.integers(0, total - n + 1)) if k % 7 else total - n
+        jobs.append((kind, first, n))
+    staged = _requests(8, seed=88)
+    results, errors = {}, []
+    try:
+        pid = {"dna": swgb.sw_server_add_pool(srv, dna.q_seqs, dna.q_offsets, dna.r_seqs,
+                                              dna.r_offsets, dna.matrix, dna.gap_open,
+                                              dna.gap_extend),
+               "protein": swgb.sw_server_add_pool(srv, prot.q_seqs, prot.q_offsets, prot.r_seqs,
+                                                  prot.r_offsets, prot.matrix, prot.gap_open,
+                                                  prot.gap_extend)}
+
+        def client(c):
+            try:
+                mine = []
+                for k in range(c, len(jobs), 4):
+                    kind, first, n = jobs[k]
+                    mine.append((k, swgb.sw_server_submit_pool(srv, pid[kind], first, n), n))
+                for k in range(c, len(staged), 4):
+                    b = staged[k]
+                    mine.append((-1 - k, swgb.sw_server_submit(
+                        srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix,
+                        b.gap_open, b.gap_extend), b.n_pairs))
+                for k, rid, n in mine:
+                    results[k] = swgb.sw_server_wait(srv, rid, n)
+            except Exception as e:  # pragma: no cover - reported below
+                errors.append(e)
+
+        th = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        assert swgb.sw_ctx_status(ctx) == 0
+    finally:
+        swgb.sw_server_destroy(srv)
+    assert not errors, errors
+    for k, (kind, first, n) in enumerate(jobs):
+        assert np.array_equal(results[k], exp[kind][first:first + n]), (k, kind, first, n)
+    for k, b in enumerate(staged):
+        assert np.array_equal(results[-1 - k], oracle.align_workload(b))
+
+
+def test_pool_errors(gpu_lib, ctx):
+    swgb = gpu_lib
+    b = wl.gen_config(0, n_pairs=50)
+    srv = swgb.sw_server_create(ctx, 8 << 20, streams=2, staging_bytes=1 << 24)
+    try:
+        pid = swgb.sw_server_add_pool(srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix,
+                                      b.gap_open, b.gap_extend)
+        with pytest.raises(swgb.SwError) as e:
+            swgb.sw_server_submit_pool(srv, pid, 40, 20)
+        assert e.value.code == swgb.SW_ERANGE
+        with pytest.raises(swgb.SwError) as e:
+            swgb.sw_server_submit_pool(srv, pid + 5, 0, 1)
+        assert e.value.code == swgb.SW_EINVAL
+        big = wl.gen_config(1, n_pairs=20000)  # 16 MB of residues: above the budget
+        with pytest.raises(swgb.SwError) as e:
+            swgb.sw_server_add_pool(srv, big.q_seqs, big.q_offsets, big.r_seqs, big.r_offsets,
+                                    big.matrix, big.gap_open, big.gap_extend)
+        assert e.value.code == swgb.SW_EBUDGET
+        rid = swgb.sw_server_submit_pool(srv, pid, 10, 30)
+        out = swgb.sw_server_wait(srv, rid, 30)
+        assert np.array_equal(out, oracle.align_workload(b.slice(10, 40)))
+    finally:
+        swgb.sw_server_destroy(srv)
