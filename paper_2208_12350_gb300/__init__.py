@@ -483,7 +483,7 @@ def sw_traceback(ctx: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, g
                  gap_extend: int, results, cigar_offsets, out_ops, out_n_ops,
                  stream=None) -> None:
     """Sequences and outputs on the device; offsets, matrix, results (5, n)
-    and cigar_offsets on the host.  Synchronises the stream."""
+    and cigar_offsets on the host.  Asynchronous on the stream."""
     qo, ro = _host_i64(q_offsets), _host_i64(r_offsets)
     mat = _host_i8(score_matrix)
     res = np.ascontiguousarray(results, dtype=np.int32)

@@ -76,6 +76,12 @@ struct sw_ctx {
     // keeps freed memory for the next call instead of returning it)
     cudaMemPool_t pool = nullptr;
     bool guards = false;  // guard regions around one-shot workspace parts
+    // page-locked staging for host tables uploaded by asynchronous calls,
+    // reused once the event of its last upload has completed
+    void *pinned = nullptr;
+    size_t pinned_cap = 0;
+    cudaEvent_t pinned_ev = nullptr;
+    std::mutex pinned_mu;
 };
 
 namespace swgb {
@@ -224,6 +230,11 @@ int sw_ctx_destroy(sw_ctx *ctx) {
         cudaFree(ctx->d_status);
         // outstanding one-shot workspaces are released when their frees complete
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        if (ctx->pinned_ev) {
+            cudaEventSynchronize(ctx->pinned_ev);
+            cudaEventDestroy(ctx->pinned_ev);
+        }
+        cudaFreeHost(ctx->pinned);
     }
     delete ctx;
     return SW_OK;
@@ -603,3 +614,53 @@ int sw_check_residues(const uint8_t *seqs, int64_t n, int32_t alphabet_size, int
 }
 
 }  // extern "C"
+
+namespace swgb {
+// Stream-ordered device memory from the context's workspace pool (released
+// with cudaFreeAsync on the same stream).
+int ctx_alloc_async(sw_ctx *ctx, size_t bytes, cudaStream_t s, void **out) {
+    *out = nullptr;
+    cudaMemPool_t pool = nullptr;
+    const int rc = ctx_pool(ctx, &pool);
+    if (rc != SW_OK) return rc;
+    if (cudaMallocFromPoolAsync(out, std::max<size_t>(bytes, 256), pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return set_error(SW_ENOMEM, "workspace allocation from the context's pool failed");
+    }
+    return SW_OK;
+}
+
+// Copies `bytes` of host data to device memory `dst` on stream s through the
+// context's page-locked staging buffer (asynchronous DMA; the buffer is
+// reused only after its previous upload has completed).
+int ctx_upload_async(sw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return SW_OK;
+    std::lock_guard<std::mutex> lk(ctx->pinned_mu);
+    if (ctx->pinned_ev) {
+        if (cudaEventSynchronize(ctx->pinned_ev) != cudaSuccess)
+            return set_error(SW_ECUDA, "staging event wait failed");
+    } else if (cudaEventCreateWithFlags(&ctx->pinned_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SW_ECUDA, "staging event creation failed");
+    }
+    if (ctx->pinned_cap < bytes) {
+        cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+        ctx->pinned_cap = 0;
+        const size_t cap = std::max(bytes, (size_t)1 << 20);
+        if (cudaMallocHost(&ctx->pinned, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(SW_ENOMEM, "page-locked staging allocation failed");
+        }
+        ctx->pinned_cap = cap;
+    }
+    std::memcpy(ctx->pinned, src, bytes);
+    if (cudaMemcpyAsync(dst, ctx->pinned, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(ctx->pinned_ev, s) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(SW_ECUDA, "staged upload failed");
+    }
+    return SW_OK;
+}
+}  // namespace swgb

@@ -248,6 +248,12 @@ int set_error(int code, const char *msg);  // message for sw_last_error()
 cudaError_t enqueue_unpack_2bit(const uint8_t *packed, int64_t n_res, uint8_t *out, int sms,
                                 cudaStream_t s);
 int ctx_device(const ::sw_ctx *ctx);          // the CUDA device a context works on
+// Stream-ordered device memory from the context's workspace pool (release
+// with cudaFreeAsync on the same stream).  Returns an sw_status.
+int ctx_alloc_async(::sw_ctx *ctx, size_t bytes, cudaStream_t s, void **out);
+// Host-to-device upload on s through the context's page-locked staging
+// buffer (the host data may be reused when the call returns).
+int ctx_upload_async(::sw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s);
 
 // Checks the arguments and plans a batch (no device allocation; queries the
 // group kernel's occupancy on the current device).  Returns an sw_status;

@@ -70,11 +70,12 @@ def test_gap_settings(gpu_lib, ctx, go, ge):
 
 
 def test_long_spans_many_strips(gpu_lib, ctx):
-    """Planted copies thousands of residues long: spans of many 128-row
-    strips, indels inside."""
+    """Planted copies up to thousands of residues long, indels inside: spans
+    on both sides of the one-strip path's 512-row limit (longer ones take
+    the general kernel's 128-row strips)."""
     rng = np.random.default_rng(41)
     qs, rs = [], []
-    for L in (129, 255, 256, 1000, 3000):
+    for L in (129, 255, 256, 511, 512, 513, 520, 1000, 3000):
         q = rng.integers(0, 4, L).astype(np.uint8)
         mut = q.copy()
         for pos in rng.choice(L, size=max(1, L // 50), replace=False):
