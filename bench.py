@@ -530,7 +530,7 @@ def measure_config(swgb, torch, ctx, k, dev, stream, flush, steps, tune_cache, s
     mb_rate, _ = swgb.sw_microbench_int("viaddmax_s16x2" if packed16 else "viaddmax_s32",
                                         dev.index, 2048)
     entry = {"workload": batch.name, "pairs": batch.n_pairs, "forward_cells": cells,
-             "reverse_cells": rcells, "arith": info["arith"], "tuning": tune,
+             "reverse_cells": rcells, "arith": info["arith"], "rows": info["rows"], "tuning": tune,
              "batched_gcups": v, "ms_per_step": t * 1e3, "steps": len(times),
              "plain_gcups": pv, "plain_identical_outputs": plain_same,
              "batched_over_plain": v / pv,
@@ -797,7 +797,7 @@ def run_ours(args, rank, world, local):
                            else "one byte per residue",
                            "shards": (f"{world} LPT shards of {world} x the per-GPU pairs"
                                       if world > 1 else None),
-                           "tuning": tune, "arith": info["arith"],
+                           "tuning": tune, "arith": info["arith"], "rows_per_lane": info["rows"],
                            "group_pairs": info["group_pairs"]},
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,

@@ -115,6 +115,11 @@ typedef enum {
  * context's status word (sw_ctx_status) if any guard word changed.  Results
  * are unchanged; nothing traps. */
 #define SW_PLAN_GUARDS 32u
+/* Where the packed 16-bit form with 32-bit profile words applies (small
+ * alphabets), run its kernel with 32 query rows per lane (16 packed words,
+ * two blocks per SM) instead of 16 (8 words, three blocks per SM): fewer
+ * steps per cell, more padded rows per strip.  Same results. */
+#define SW_PLAN_ROWS32 64u
 
 typedef struct sw_ctx sw_ctx;
 typedef struct sw_plan sw_plan;
@@ -165,6 +170,17 @@ int sw_default_ctx(int32_t device, sw_ctx **out);
  * a group go to wider groups (cap_fraction > 0; a huge value keeps one
  * width for all pairs). */
 int sw_ctx_set_tuning(sw_ctx *ctx, int32_t narrow_log2g, double cap_fraction);
+
+/* Batched kernel form for plans created afterwards (a plan's flags still
+ * override): arith = -1 (default: the packed 16-bit form wherever its bound
+ * holds), 0 (scaled int32 always), 1 (packed where legal); rows = 16 or 32
+ * rows per lane for the packed form with 32-bit profile words (32 as
+ * SW_PLAN_ROWS32).  sw_autotune sets both. */
+int sw_ctx_set_form(sw_ctx *ctx, int32_t arith, int32_t rows);
+
+/* The context's current tuning (any pointer may be NULL). */
+int sw_ctx_get_tuning(const sw_ctx *ctx, int32_t *narrow_log2g, double *cap_fraction,
+                      int32_t *arith, int32_t *rows);
 
 /*
  * Plan a batch.  q_offsets and r_offsets are HOST arrays of n_pairs + 1
@@ -230,6 +246,8 @@ int sw_plan_info(const sw_plan *plan, int32_t *n_group_pairs, int32_t *n_plain,
 #define SW_ARITH_S32 0
 #define SW_ARITH_S16X2 1
 int sw_plan_arith(const sw_plan *plan, int32_t *arith);
+/* Query rows per lane of a plan's batched kernel (16 or 32). */
+int sw_plan_rows(const sw_plan *plan, int32_t *rows);
 
 /* Test aid for plans made with SW_PLAN_GUARDS: overwrite one word in the
  * middle of guard region `region` (0 .. 2 x the plan's guarded buffers - 1)
@@ -268,9 +286,12 @@ int sw_plan_preview(const int64_t *q_offsets, const int64_t *r_offsets, int32_t 
  * q_seqs/r_seqs on the DEVICE, `out` a DEVICE scratch array of 5 x n_pairs
  * int32 that receives the results - once per candidate tuning (bulk
  * lane-group width 2, 4 or 8 with long-pair caps 0.25, 0.5, 1 or none, and
- * the planner's own choice), keeps the fastest and sets it on ctx with
- * sw_ctx_set_tuning.  With a non-NULL cache_path the choice is looked up
- * first and stored after measuring in that JSON file, keyed by GPU name, SM
+ * the planner's own choice; for a batch that takes the packed form with
+ * 32-bit profile words, each of those also with 32 rows per lane and in the
+ * scaled int32 form), keeps the fastest and sets it on ctx with
+ * sw_ctx_set_tuning and sw_ctx_set_form (sw_ctx_get_tuning reads it back).
+ * With a non-NULL cache_path the choice is looked up first and stored after
+ * measuring in that JSON file, keyed by GPU name, SM
  * count and a signature of the batch (pair count, length sums, maxima and
  * histograms, scoring); a hit skips the measurement.  Outputs (may be
  * NULL): the chosen narrow_log2g and cap_fraction and its time in ms.

@@ -28,6 +28,7 @@ SW_PLAN_PACKED_2BIT = 4
 SW_PLAN_NO_S16X2 = 8
 SW_PLAN_PAIR_SCRATCH = 16
 SW_PLAN_GUARDS = 32
+SW_PLAN_ROWS32 = 64
 SW_ARITH_S32, SW_ARITH_S16X2 = 0, 1
 SW_MAX_LEN = 65535
 
@@ -45,6 +46,10 @@ SIGNATURES = {
     "sw_ctx_set_guards": ([_P, _I32], ctypes.c_int),
     "sw_ctx_host_in_place": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
+    "sw_ctx_set_form": ([_P, _I32, _I32], ctypes.c_int),
+    "sw_ctx_get_tuning": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_plan_rows": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
     "sw_plan_execute": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "sw_plan_execute_host": ([_P, _P, _P, _P, _P], ctypes.c_int),
@@ -196,6 +201,19 @@ def sw_ctx_set_tuning(ctx: int, narrow_log2g: int = -1, cap_fraction: float = 0.
     _check(load().sw_ctx_set_tuning(ctx, narrow_log2g, cap_fraction), "sw_ctx_set_tuning")
 
 
+def sw_ctx_set_form(ctx: int, arith: int = -1, rows: int = 16) -> None:
+    """Batched kernel form: arith -1 auto / 0 int32 / 1 packed; rows 16 or 32."""
+    _check(load().sw_ctx_set_form(ctx, arith, rows), "sw_ctx_set_form")
+
+
+def sw_ctx_get_tuning(ctx: int) -> dict:
+    lg, fr, ar, rw = _I32(), ctypes.c_double(), _I32(), _I32()
+    _check(load().sw_ctx_get_tuning(ctx, ctypes.byref(lg), ctypes.byref(fr), ctypes.byref(ar),
+                                    ctypes.byref(rw)), "sw_ctx_get_tuning")
+    return {"narrow_log2g": lg.value, "cap_fraction": fr.value, "arith": ar.value,
+            "rows": rw.value}
+
+
 # -------------------------------------------------------------------- plan
 
 def sw_plan_create(ctx: int, q_offsets, r_offsets, score_matrix, gap_open: int, gap_extend: int,
@@ -240,13 +258,16 @@ def sw_plan_info(plan: int) -> dict:
     sb = _I64()
     _check(load().sw_plan_info(plan, ctypes.byref(t), ctypes.byref(p), ctypes.byref(l),
                                ctypes.byref(sb)), "sw_plan_info")
-    ar = _I32()
+    ar, rw = _I32(), _I32()
     _check(load().sw_plan_arith(plan, ctypes.byref(ar)), "sw_plan_arith")
+    _check(load().sw_plan_rows(plan, ctypes.byref(rw)), "sw_plan_rows")
     return {"group_pairs": t.value, "plain_pairs": p.value, "launches": l.value,
-            "scratch_bytes": sb.value, "arith": "s16x2" if ar.value == SW_ARITH_S16X2 else "s32"}
+            "scratch_bytes": sb.value, "arith": "s16x2" if ar.value == SW_ARITH_S16X2 else "s32",
+            "rows": rw.value}
 
 
-PLAN_KINDS = {0: "int32", 1: "int32-int8-profile", 2: "s16x2", 3: "s16x2-byte-profile"}
+PLAN_KINDS = {0: "int32", 1: "int32-int8-profile", 2: "s16x2", 3: "s16x2-byte-profile",
+              4: "s16x2-32-rows"}
 
 
 def sw_plan_preview(q_offsets, r_offsets, score_matrix, gap_open: int, gap_extend: int,
@@ -291,7 +312,9 @@ def sw_autotune(ctx: int, q_offsets, r_offsets, score_matrix, gap_open: int, gap
                                  cache_path.encode() if cache_path else None, _stream(stream),
                                  ctypes.byref(lg), ctypes.byref(frac), ctypes.byref(ms)),
            "sw_autotune_ex")
-    return {"narrow_log2g": lg.value, "cap_fraction": frac.value, "ms": ms.value}
+    t = sw_ctx_get_tuning(ctx)
+    return {"narrow_log2g": lg.value, "cap_fraction": frac.value, "ms": ms.value,
+            "arith": {-1: "auto", 0: "s32", 1: "s16x2"}[t["arith"]], "rows": t["rows"]}
 
 
 # ---------------------------------------------------------------- one-shot

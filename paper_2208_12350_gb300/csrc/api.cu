@@ -67,6 +67,8 @@ struct sw_ctx {
     int32_t *d_status = nullptr;
     int narrow_log2g = -1;      // planner override: bulk lane-group width (log2), -1 = auto
     double cap_fraction = 0.5;  // planner override: long-pair cap (used with narrow_log2g)
+    int form_arith = -1;        // batched kernel form: -1 auto, 0 scaled int32, 1 packed 16-bit
+    int form_rows = 16;         // packed form with 32-bit profile words: 16 or 32 rows per lane
     // the device reads host memory through the host's page tables over a
     // coherent link (NVLink-C2C on Grace): pinned host inputs are read in place
     bool host_in_place = false;
@@ -255,6 +257,24 @@ int sw_ctx_status(sw_ctx *ctx, int32_t *status) {
     return SW_OK;
 }
 
+int sw_ctx_set_form(sw_ctx *ctx, int32_t arith, int32_t rows) {
+    if (!ctx || arith < -1 || arith > 1 || (rows != 16 && rows != 32))
+        return fail(SW_EINVAL, "sw_ctx_set_form: bad argument");
+    ctx->form_arith = arith;
+    ctx->form_rows = rows;
+    return SW_OK;
+}
+
+int sw_ctx_get_tuning(const sw_ctx *ctx, int32_t *narrow_log2g, double *cap_fraction,
+                      int32_t *arith, int32_t *rows) {
+    if (!ctx) return fail(SW_EINVAL, "sw_ctx_get_tuning: ctx is NULL");
+    if (narrow_log2g) *narrow_log2g = ctx->narrow_log2g;
+    if (cap_fraction) *cap_fraction = ctx->cap_fraction;
+    if (arith) *arith = ctx->form_arith;
+    if (rows) *rows = ctx->form_rows;
+    return SW_OK;
+}
+
 int sw_ctx_set_guards(sw_ctx *ctx, int32_t on) {
     if (!ctx || (on != 0 && on != 1)) return fail(SW_EINVAL, "sw_ctx_set_guards: bad argument");
     ctx->guards = on != 0;
@@ -285,8 +305,10 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
     std::string msg;
     int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
                             gap_extend, mode, ctx->sm_count, ctx->narrow_log2g, ctx->cap_fraction,
-                            &p->hp, &msg, 1, 8192, (flags & SW_PLAN_NO_S16X2) == 0,
-                            group_blocks_per_sm, (flags & SW_PLAN_PAIR_SCRATCH) == 0);
+                            &p->hp, &msg, 1, 8192,
+                            (flags & SW_PLAN_NO_S16X2) == 0 && ctx->form_arith != 0,
+                            group_blocks_per_sm, (flags & SW_PLAN_PAIR_SCRATCH) == 0,
+                            (flags & SW_PLAN_ROWS32) != 0 || ctx->form_rows == 32);
     if (rc != SW_OK) {
         delete p;
         return fail(rc, "sw_plan_create: %s", msg.c_str());
@@ -475,6 +497,12 @@ int sw_plan_info(const sw_plan *p, int32_t *n_group_pairs, int32_t *n_plain, int
 int sw_plan_arith(const sw_plan *p, int32_t *arith) {
     if (!p || !arith) return fail(SW_EINVAL, "sw_plan_arith: NULL argument");
     *arith = (!p->hp.pairs.empty() && is_packed(p->hp.kind)) ? SW_ARITH_S16X2 : SW_ARITH_S32;
+    return SW_OK;
+}
+
+int sw_plan_rows(const sw_plan *p, int32_t *rows) {
+    if (!p || !rows) return fail(SW_EINVAL, "sw_plan_rows: NULL argument");
+    *rows = rows_of(p->hp.kind);
     return SW_OK;
 }
 

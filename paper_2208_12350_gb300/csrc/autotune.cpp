@@ -2,12 +2,16 @@
 //
 // The planner (plan.cpp) picks lane-group widths from a cost model.  The
 // autotuner measures instead: it runs the batch under each candidate tuning
-// (bulk lane-group width G in {2, 4, 8} x long-pair cap in {0.25, 0.5, 1,
-// none}, plus the planner's own choice), keeps the fastest, sets it on the
-// context and records it in a JSON cache keyed by the GPU (name, SM count)
-// and a signature of the batch (pair count, length sums, maxima and length
+// - bulk lane-group width G in {2, 4, 8} x long-pair cap in {0.25, 0.5, 1,
+// none}, plus the planner's own choice, for each kernel form the batch
+// allows (the packed 16-bit form with 16 or with 32 rows per lane, and the
+// scaled int32 form) - keeps the fastest, sets it on the context and
+// records it in a JSON cache keyed by the GPU (name, SM count) and a
+// signature of the batch (pair count, length sums, maxima and length
 // histograms, scoring), so the next run of the same kind of batch skips the
-// measurement.
+// measurement.  Every form is a kernel instantiation built into the library
+// (no rebuild); steps per staging block and blocks per SM are fixed per form
+// (8 steps and 3 blocks for 16 rows, 8 and 2 for 32 rows).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,7 +40,7 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
 
 // Part of every cache key: a tuning measured on another kernel build is not
 // reused.  Changed whenever the batched kernel's code changes.
-constexpr char kKernelRevision[] = "group-kernel-r12 H+go / transposed reverse / linear / score tables / warp-built profiles / packed 16-bit / half-width tails / paired end-key chain / strip-start cost in the planner";
+constexpr char kKernelRevision[] = "group-kernel-r13 H+go / transposed reverse / linear / score tables / warp-built profiles / packed 16-bit / half-width tails / paired end-key chain / strip-start cost 18 / branch-free staging / group slots / forms";
 
 std::string batch_key(const char *gpu, int sms, const int64_t *qo, const int64_t *ro, int n_pairs,
                       const int8_t *mat, int A, int go, int ge) {
@@ -78,6 +82,7 @@ struct Entry {
     std::string key;
     int log2g = -1;
     double frac = 0.5, ms = 0;
+    int arith = -1, rows = 16;  // kernel form (sw_ctx_set_form)
 };
 
 // The cache file is a JSON object {"entries": [ {...}, ... ]} with one
@@ -97,11 +102,15 @@ std::vector<Entry> read_cache(const char *path) {
             const size_t p = line.find(name);
             if (p != std::string::npos) v = std::atof(line.c_str() + p + std::strlen(name));
         };
-        double lg = -1;
+        double lg = -1, ar = -1, rw = 16;
         num("\"narrow_log2g\": ", lg);
         num("\"cap_fraction\": ", e.frac);
         num("\"ms\": ", e.ms);
+        num("\"arith\": ", ar);
+        num("\"rows\": ", rw);
         e.log2g = (int)lg;
+        e.arith = (int)ar;
+        e.rows = (int)rw;
         out.push_back(e);
     }
     return out;
@@ -115,9 +124,10 @@ bool write_cache(const char *path, const std::vector<Entry> &entries, const char
     for (size_t i = 0; i < entries.size(); ++i) {
         char buf[256];
         snprintf(buf, sizeof buf,
-                 "  {\"key\": \"%s\", \"narrow_log2g\": %d, \"cap_fraction\": %.17g, \"ms\": %.17g}%s\n",
-                 entries[i].key.c_str(), entries[i].log2g, entries[i].frac, entries[i].ms,
-                 i + 1 < entries.size() ? "," : "");
+                 "  {\"key\": \"%s\", \"narrow_log2g\": %d, \"cap_fraction\": %.17g, "
+                 "\"arith\": %d, \"rows\": %d, \"ms\": %.17g}%s\n",
+                 entries[i].key.c_str(), entries[i].log2g, entries[i].frac, entries[i].arith,
+                 entries[i].rows, entries[i].ms, i + 1 < entries.size() ? "," : "");
         f << buf;
     }
     f << "]}\n";
@@ -161,7 +171,8 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
         cache = read_cache(cache_path);
         for (const Entry &e : cache)
             if (e.key == key) {
-                const int rc = sw_ctx_set_tuning(ctx, e.log2g, e.frac);
+                int rc = sw_ctx_set_tuning(ctx, e.log2g, e.frac);
+                if (rc == SW_OK) rc = sw_ctx_set_form(ctx, e.arith, e.rows);
                 if (rc != SW_OK) return rc;
                 if (chosen_log2g) *chosen_log2g = e.log2g;
                 if (chosen_frac) *chosen_frac = e.frac;
@@ -172,20 +183,51 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
     struct Cand {
         int lg;
         double frac;
+        int arith, rows;
     };
-    std::vector<Cand> cands = {{-1, 0.5}};
-    for (int lg = kMinLog2G; lg <= 3; ++lg)
-        for (double f : {0.25, 0.5, 1.0, 1e9}) cands.push_back({lg, f});
+    // the kernel forms this batch allows, from host-only plans: the default
+    // plan's; where that is a packed form, also the scaled int32 form; where
+    // it is the packed form with 32-bit profile words and two blocks of the
+    // 32-rows kernel fit an SM, also 32 rows per lane
+    std::vector<std::pair<int, int>> forms = {{-1, 16}};
+    {
+        auto kind_of = [&](bool rows32, ProfileKind *k) -> int {
+            HostPlan hp;
+            std::string msg;
+            const int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix,
+                                          alphabet_size, gap_open, gap_extend, SW_MODE_BATCHED,
+                                          sms, -1, 0.5, &hp, &msg, 1, 8192,
+                                          (flags & SW_PLAN_NO_S16X2) == 0, group_blocks_per_sm,
+                                          (flags & SW_PLAN_PAIR_SCRATCH) == 0, rows32);
+            if (rc != SW_OK) return set_error(rc, ("sw_autotune: " + msg).c_str());
+            *k = hp.kind;
+            return SW_OK;
+        };
+        ProfileKind k16 = ProfileKind::kInt32, k32 = ProfileKind::kInt32;
+        int rc0 = kind_of(false, &k16);
+        if (rc0 == SW_OK) rc0 = kind_of(true, &k32);
+        if (rc0 != SW_OK) return rc0;
+        if (k32 == ProfileKind::kPacked16R32) forms.push_back({1, 32});
+        if (k16 == ProfileKind::kPacked16 || k16 == ProfileKind::kPacked16Bytes)
+            forms.push_back({0, 16});
+    }
+    std::vector<Cand> cands;
+    for (const auto &f : forms) {
+        cands.push_back({-1, 0.5, f.first, f.second});
+        for (int lg = kMinLog2G; lg <= 3; ++lg)
+            for (double fr : {0.25, 0.5, 1.0, 1e9}) cands.push_back({lg, fr, f.first, f.second});
+    }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(SW_ECUDA, "sw_autotune: event creation failed");
     const int64_t n = n_pairs;
-    Cand best{-1, 0.5};
+    Cand best{-1, 0.5, -1, 16};
     double best_ms = 1e30;
     int rc = SW_OK;
     for (const Cand &c : cands) {
         if ((rc = sw_ctx_set_tuning(ctx, c.lg, c.frac)) != SW_OK) break;
+        if ((rc = sw_ctx_set_form(ctx, c.arith, c.rows)) != SW_OK) break;
         sw_plan *plan = nullptr;
         rc = sw_plan_create(ctx, q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size,
                             gap_open, gap_extend, SW_MODE_BATCHED, flags, &plan);
@@ -213,11 +255,12 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
     cudaEventDestroy(e1);
     if (rc != SW_OK) return rc;
     if ((rc = sw_ctx_set_tuning(ctx, best.lg, best.frac)) != SW_OK) return rc;
+    if ((rc = sw_ctx_set_form(ctx, best.arith, best.rows)) != SW_OK) return rc;
     if (chosen_log2g) *chosen_log2g = best.lg;
     if (chosen_frac) *chosen_frac = best.frac;
     if (chosen_ms) *chosen_ms = best_ms;
     if (cache_path && *cache_path) {
-        cache.push_back({key, best.lg, best.frac, best_ms});
+        cache.push_back({key, best.lg, best.frac, best_ms, best.arith, best.rows});
         if (!write_cache(cache_path, cache, gpu, sms))
             return set_error(SW_EINVAL, "sw_autotune: cannot write the cache file");
     }

@@ -80,7 +80,8 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp, int sample_cap,
-                   bool allow_packed, BlocksPerSmFn blocks_per_sm, bool group_slots) {
+                   bool allow_packed, BlocksPerSmFn blocks_per_sm, bool group_slots,
+                   bool rows32) {
     *out = HostPlan();
     int rc = check_batch(q_offsets, r_offsets, n_pairs, mat, A, go, ge, nullptr, nullptr,
                          nullptr, msg);
@@ -124,7 +125,12 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
         if (b < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
         ok = b >= 2;
     }
-    if (packed8)
+    if (packed8 && rows32) {
+        // the 32-rows-per-lane kernel, where two of its blocks fit an SM
+        const int b = blocks_per_sm(ProfileKind::kPacked16R32, go == ge, A, nullptr);
+        if (b < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
+        out->kind = b >= 2 ? ProfileKind::kPacked16R32 : ProfileKind::kPacked16;
+    } else if (packed8)
         out->kind = ProfileKind::kPacked16;
     else if (packed4)
         out->kind = ProfileKind::kPacked16Bytes;
@@ -171,7 +177,8 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
     }
     const std::vector<PlannedClass> planned =
         plan_classes(gp, out->n_warps, narrow_log2g, cap_fraction, sample_cap,
-                     out->kind == ProfileKind::kPacked16, rows_of(out->kind),
+                     out->kind == ProfileKind::kPacked16 || out->kind == ProfileKind::kPacked16R32,
+                     rows_of(out->kind),
                      strip_overhead_steps(A));
     out->pairs.reserve(gp.size());
     int warp_begin = 0;
@@ -269,7 +276,7 @@ static int estimate_blocks_per_sm(ProfileKind kind, bool, int alphabet, int *sme
     constexpr size_t kSmemPerSm = 233472, kReservedPerBlock = 1024, kMaxPerBlock = 232448;
     if (bytes > kMaxPerBlock) return 0;
     const int by_smem = (int)(kSmemPerSm / (bytes + kReservedPerBlock));
-    const int by_regs = (kind == ProfileKind::kPacked16 && kRowsPacked > 16) ? 2 : kGroupMinBlocks;
+    const int by_regs = kind == ProfileKind::kPacked16R32 ? 2 : kGroupMinBlocks;
     return std::min(by_smem, by_regs);
 }
 
@@ -290,7 +297,8 @@ extern "C" int sw_plan_preview(const int64_t *q_offsets, const int64_t *r_offset
     const int rc = make_host_plan(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size,
                                   gap_open, gap_extend, mode, sm_count, narrow_log2g,
                                   cap_fraction, &hp, &msg, 1, 8192,
-                                  (flags & SW_PLAN_NO_S16X2) == 0, estimate_blocks_per_sm);
+                                  (flags & SW_PLAN_NO_S16X2) == 0, estimate_blocks_per_sm, false,
+                                  (flags & SW_PLAN_ROWS32) != 0);
     if (rc != SW_OK) return set_error(rc, ("sw_plan_preview: " + msg).c_str());
     *out_kind = (int32_t)hp.kind;
     for (int32_t i = 0; i < n_pairs; ++i) pair_log2g[i] = pair_rank[i] = -1;

@@ -189,6 +189,18 @@ __device__ __forceinline__ void lds16_if(uint4 &v, const uint32_t *ssrc, bool p)
         : "r"((int)p), "r"(sa)
         : "memory");
 }
+// L2 eviction priorities: strip-boundary words stored and read back with
+// evict-last, so that they stay in L2 between strips (1; on 100k DNA pairs
+// 190 -> 131 MB of DRAM writes per launch, same time), or the default
+// policy (0).
+#ifndef SWGB_L2_HINTS
+#define SWGB_L2_HINTS 1
+#endif
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 // cp_async16 issued only where p holds: a predicated instruction, no branch
 // (an address formed for a lane with p false is never accessed)
 __device__ __forceinline__ void cp_async16_if(void *smem_dst, const void *gsrc, bool p) {
@@ -200,14 +212,40 @@ __device__ __forceinline__ void cp_async16_if(void *smem_dst, const void *gsrc, 
         : "memory");
 }
 // 16 bytes from shared to global memory where p holds (predicated, no branch)
-__device__ __forceinline__ void copy16_s2g_if(uint32_t *gdst, const uint32_t *ssrc, bool p) {
+__device__ __forceinline__ void copy16_s2g_if(uint32_t *gdst, const uint32_t *ssrc, bool p,
+                                              uint64_t pol) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(ssrc);
+#if SWGB_L2_HINTS
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t.reg .b32 a, b, c, d;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+        "@q ld.shared.v4.b32 {a, b, c, d}, [%1];\n\t"
+        "@q st.global.L2::cache_hint.v4.b32 [%0], {a, b, c, d}, %3;\n\t}" ::"l"(gdst),
+        "r"(sa), "r"((int)p), "l"(pol)
+        : "memory");
+#else
+    (void)pol;
     asm volatile(
         "{\n\t.reg .pred q;\n\t.reg .b32 a, b, c, d;\n\tsetp.ne.b32 q, %2, 0;\n\t"
         "@q ld.shared.v4.b32 {a, b, c, d}, [%1];\n\t"
         "@q st.global.v4.b32 [%0], {a, b, c, d};\n\t}" ::"l"(gdst),
         "r"(sa), "r"((int)p)
         : "memory");
+#endif
+}
+// cp_async16_if for boundary words, with the evict-last policy when enabled
+__device__ __forceinline__ void cp_async16_bnd_if(void *smem_dst, const void *gsrc, bool p,
+                                                  uint64_t pol) {
+#if SWGB_L2_HINTS
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+        "@q cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %3;\n\t}" ::"r"(d),
+        "l"(gsrc), "r"((int)p), "l"(pol)
+        : "memory");
+#else
+    (void)pol;
+    cp_async16_if(smem_dst, gsrc, p);
+#endif
 }
 
 
@@ -432,6 +470,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
     [[maybe_unused]] const uint32_t one_opaque = blockDim.x / NT;
     const int t = threadIdx.x;
     const int warp = t >> 5, lane = t & 31;
+    const uint64_t l2pol = SWGB_L2_HINTS ? l2_evict_last_policy() : 0ull;
     const size_t prof_bytes = P8 ? (size_t)(A + 1) * 32 * R : (size_t)(A + 1) * (R / 4) * 32 * 16;
     // shared memory: rings (16-byte aligned) | score tables | cold state | profiles
     char *rings = smem_group + (size_t)warp * 3 * kMaxGroups * kRingBytes;
@@ -568,7 +607,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
 #pragma unroll
             for (int k = 0; k < kU / 4; ++k) {
                 const bool b_due = bi_next <= bi_want;
-                cp_async16_if(bin_ring + (bi_next & 7) * 4, bin + bi_next * 4, b_due && gl == 0);
+                cp_async16_bnd_if(bin_ring + (bi_next & 7) * 4, bin + bi_next * 4,
+                                  b_due && gl == 0, l2pol);
                 bi_next += b_due ? 1 : 0;
             }
         };
@@ -576,7 +616,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
 #pragma unroll
             for (int k = 0; k < kU / 4; ++k) {
                 const bool due = bo_done < upto;
-                copy16_s2g_if(bout + bo_done, bout_ring + (bo_done & 31), due && gl == G - 1);
+                copy16_s2g_if(bout + bo_done, bout_ring + (bo_done & 31), due && gl == G - 1,
+                              l2pol);
                 bo_done += due ? 4 : 0;
             }
         };
@@ -1124,7 +1165,7 @@ size_t group_smem_bytes(ProfileKind kind, int alphabet) {
 // under a launch that needs more.  Occupancy per (profile, alphabet) is
 // cached per device.
 namespace {
-// the eight instantiations, indexed by (profile kind, linear gaps)
+// the ten instantiations, indexed by (profile kind, linear gaps)
 using GroupKernel = void (*)(GroupParams);
 GroupKernel group_kernel_of(ProfileKind kind, bool lin) {
     switch (kind) {
@@ -1137,6 +1178,9 @@ GroupKernel group_kernel_of(ProfileKind kind, bool lin) {
         case ProfileKind::kPacked16Bytes:
             return lin ? sw_group_kernel<kRows, true, true, true>
                        : sw_group_kernel<kRows, true, false, true>;
+        case ProfileKind::kPacked16R32:
+            return lin ? sw_group_kernel<32, false, true, true>
+                       : sw_group_kernel<32, false, false, true>;
         default:
             return lin ? sw_group_kernel<kRows, false, true, false>
                        : sw_group_kernel<kRows, false, false, false>;
@@ -1150,8 +1194,8 @@ int group_blocks_per_sm(ProfileKind kind, bool linear, int alphabet, int *smem_b
     if (alphabet < 1 || alphabet > kMaxAlphabet) return -1;
     constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static int cache[kMaxDevices][8][kMaxAlphabet + 1];
-    static bool raised[kMaxDevices][8];
+    static int cache[kMaxDevices][2 * kNumProfileKinds][kMaxAlphabet + 1];
+    static bool raised[kMaxDevices][2 * kNumProfileKinds];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
     const int ki = 2 * (int)kind + (linear ? 1 : 0);

@@ -179,17 +179,27 @@ int64_t sweep_steps(int n, int m, int G, int rows = kRows);
 // with an int32 or int8 profile, or two 16-bit cells per 32-bit word.
 // The packed form comes with a profile of 32-bit words (scores scaled by 8)
 // or, for larger alphabets, of bytes (scaled by 4).
-enum class ProfileKind : int { kInt32 = 0, kInt8 = 1, kPacked16 = 2, kPacked16Bytes = 3 };
+// kPacked16R32: the packed form with 32-bit profile words and 32 rows per
+// lane (16 words, two end-key chains), two blocks per SM.
+enum class ProfileKind : int {
+    kInt32 = 0,
+    kInt8 = 1,
+    kPacked16 = 2,
+    kPacked16Bytes = 3,
+    kPacked16R32 = 4
+};
+constexpr int kNumProfileKinds = 5;
 inline bool is_packed(ProfileKind k) {
-    return k == ProfileKind::kPacked16 || k == ProfileKind::kPacked16Bytes;
+    return k == ProfileKind::kPacked16 || k == ProfileKind::kPacked16Bytes ||
+           k == ProfileKind::kPacked16R32;
 }
 
-// Rows per lane of the packed form (16: 8 words, 32: 16 words).
-#ifndef SWGB_PACKED_ROWS
-#define SWGB_PACKED_ROWS 16
-#endif
-constexpr int kRowsPacked = SWGB_PACKED_ROWS;
-inline int rows_of(ProfileKind k) { return k == ProfileKind::kPacked16 ? kRowsPacked : kRows; }
+// Rows per lane of the packed forms with 32-bit profile words (16: 8 words;
+// the R32 kind: 32, 16 words).
+constexpr int kRowsPacked = 16;
+inline int rows_of(ProfileKind k) {
+    return k == ProfileKind::kPacked16 ? kRowsPacked : k == ProfileKind::kPacked16R32 ? 32 : kRows;
+}
 
 // Whether a pair fits the packed 16-bit form with scores scaled by `scale`
 // (8 or 4): every value scale x (score terms) stays in a signed 16-bit
@@ -277,12 +287,14 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
 using BlocksPerSmFn = int (*)(ProfileKind, bool, int, int *);
 // group_slots: strip-boundary words in one slot per lane group, sized for
 // the batch's largest need (HostPlan::slot_words), instead of per pair.
+// rows32: where the packed form with 32-bit profile words applies, take its
+// 32-rows-per-lane kernel.
 int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pairs,
                    const int8_t *mat, int32_t A, int32_t go, int32_t ge, int32_t mode,
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192,
                    bool allow_packed = true, BlocksPerSmFn blocks_per_sm = group_blocks_per_sm,
-                   bool group_slots = false);
+                   bool group_slots = false, bool rows32 = false);
 // Enqueues the kernels of a planned batch on s (queue-head reset included).
 cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
                          const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,

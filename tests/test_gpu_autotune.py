@@ -101,3 +101,58 @@ def test_autotune_with_plan_flags(gpu_lib, tmp_path):
         assert len({e["key"] for e in doc["entries"]}) == 3
     finally:
         swgb.sw_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("arith,rows", [(0, 16), (1, 16), (1, 32), (-1, 32)])
+def test_kernel_forms_exact(gpu_lib, arith, rows):
+    """Each kernel form the autotuner chooses between - the packed 16-bit
+    form with 16 or 32 rows per lane, and the scaled int32 form - gives the
+    oracle's results on a batch that spans one-strip, multi-strip and
+    long-cap pairs."""
+    import torch
+    swgb = gpu_lib
+    b = wl.gen_config(1, n_pairs=1500)
+    ctx = swgb.sw_ctx_create(0)
+    try:
+        swgb.sw_ctx_set_form(ctx, arith, rows)
+        assert swgb.sw_ctx_get_tuning(ctx)["rows"] == rows
+        a = swgb.Aligner(b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix, b.gap_open,
+                         b.gap_extend, mode=swgb.SW_MODE_BATCHED, ctx=ctx)
+        info = swgb.sw_plan_info(a.plan)
+        assert info["arith"] == ("s32" if arith == 0 else "s16x2")
+        assert info["rows"] == (16 if arith == 0 else rows)
+        a.run()
+        res = a.results()
+        a.close()
+        idx = np.arange(0, b.n_pairs, 7)
+        assert np.array_equal(res[idx], oracle.align_workload(b, idx=idx))
+    finally:
+        swgb.sw_ctx_destroy(ctx)
+
+
+def test_autotune_records_form(gpu_lib, tmp_path):
+    """The autotuner's choice includes the kernel form; a cache hit restores it."""
+    import torch
+    swgb = gpu_lib
+    b = wl.gen_config(1, n_pairs=2000)
+    dev = torch.device("cuda:0")
+    q = torch.from_numpy(b.q_seqs).to(dev)
+    r = torch.from_numpy(b.r_seqs).to(dev)
+    out = torch.empty((5, b.n_pairs), dtype=torch.int32, device=dev)
+    cache = tmp_path / "tune.json"
+    ctx = swgb.sw_ctx_create(0)
+    ctx2 = swgb.sw_ctx_create(0)
+    try:
+        first = swgb.sw_autotune(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
+                                 b.gap_extend, q, r, out, cache_path=str(cache))
+        assert first["arith"] in ("auto", "s32", "s16x2") and first["rows"] in (16, 32)
+        e = json.loads(cache.read_text())["entries"][0]
+        assert {e["arith"], e["rows"]} <= {-1, 0, 1, 16, 32}
+        swgb.sw_ctx_set_form(ctx2, 0, 16)
+        second = swgb.sw_autotune(ctx2, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
+                                  b.gap_extend, q, r, out, cache_path=str(cache))
+        assert second == first
+        assert swgb.sw_ctx_get_tuning(ctx2) == swgb.sw_ctx_get_tuning(ctx)
+    finally:
+        swgb.sw_ctx_destroy(ctx)
+        swgb.sw_ctx_destroy(ctx2)
