@@ -150,6 +150,23 @@ __host__ __device__ constexpr int unroll_of() {
 #ifndef SWGB_BOUT_ANY_COLUMN
 #define SWGB_BOUT_ANY_COLUMN 1
 #endif
+// Packed form with gaps and 32-bit profile words, the row above word 0:
+// 0 = two shuffles (the lane above's last word of H and of F) and two
+// selects for lane 0; 1 = one shuffle of a word holding both (the boundary
+// word's format, which lane 0 takes instead with one select).  Measured
+// with the same tuning: +1.1 % on 100k DNA pairs (the byte-profile form
+// keeps 0: -0.2 % on 20k protein pairs).
+#ifndef SWGB_ONE_SHUFFLE
+#define SWGB_ONE_SHUFFLE 1
+#endif
+// Packed form with 32-bit profile words, the diagonal sum H_diag + s'
+// (three terms): 0 = plain adds; 1 = two multiply-adds by a one the
+// compiler cannot see, issued on the FMA pipe instead of the ALU pipe.
+// Measured: +1.3 % on 100k DNA pairs, +1.5 % together with one shuffle
+// (the byte-profile form, one add per word, keeps 0: -0.7 % on protein).
+#ifndef SWGB_DADD_FMA
+#define SWGB_DADD_FMA 1
+#endif
 // A lane's R rows as two halves a column apart (2: two independent row
 // chains per step) or one block of R rows (1).  Measured on 100k and 200k
 // DNA pairs, the split form was 0.2 % and 1.1 % slower, so it is off; it
@@ -231,6 +248,20 @@ __device__ __forceinline__ void copy16_s2g_if(uint32_t *gdst, const uint32_t *ss
         "r"(sa), "r"((int)p)
         : "memory");
 #endif
+}
+// Strip-boundary words are read once, by the next strip: once a whole L2
+// line of them has landed in shared memory, it is dropped from L2 without a
+// write-back (1; the line holds only this buffer's consumed words, 128-byte
+// aligned), or left to be written back when evicted (0).  Measured on 100k
+// DNA pairs: DRAM traffic per launch 243 -> 105 MB, time unchanged; the
+// byte-profile form keeps 0 (3.4 % slower with it on 20k protein pairs).
+#ifndef SWGB_DISCARD
+#define SWGB_DISCARD 1
+#endif
+__device__ __forceinline__ void discard_l2_if(const void *line, bool p) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+        "@q discard.global.L2 [%0], 128;\n\t}" ::"l"(line), "r"((int)p));
 }
 // cp_async16_if for boundary words, with the evict-last policy when enabled
 __device__ __forceinline__ void cp_async16_bnd_if(void *smem_dst, const void *gsrc, bool p,
@@ -545,7 +576,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
         // end tracking (threshold, its "keep the score" mask, one record per
         // half: column << 16 | 8 score + row code)
         uint32_t Hw[W], Ew[W];
-        uint32_t outHw = 0u, outFw = 0u, diag0w = 0u;
+        uint32_t outHw = 0u, outFw = 0u, diag0w = 0u, outX = 0u;
         uint32_t Tw[NC], rec_lo[NC], rec_hi[NC], tmask = (CL - 1) * 0x10001u;
 #pragma unroll
         for (int c = 0; c < NC; ++c) Tw[c] = (CL - 1) * 0x10001u, rec_lo[c] = rec_hi[c] = 0u;
@@ -557,6 +588,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
         int bo_done = 0;                // boundary-out words written so far
         const uint32_t *bin = p.scratch;
         uint32_t *bout = p.scratch;
+        // next 128-byte line of boundary-in words to drop from L2
+        [[maybe_unused]] const uint32_t *bdisc = p.scratch;
         bool has_in = false, has_out = false;
         bool live = false, rev = false, drained = false;
         bool need_prof = false;  // this lane's group started a strip without its profile
@@ -652,7 +685,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
             if constexpr (PK) {
 #pragma unroll
                 for (int k = 0; k < W; ++k) Hw[k] = Ew[k] = 0u;
-                outHw = outFw = diag0w = 0u;
+                outHw = outFw = diag0w = outX = 0u;
                 // forward: best score 0 with the largest row code; reverse:
                 // just below the score S with any row code
                 const uint32_t t0 = rev ? (uint32_t)(SC * cold.target[t] - 1) : (uint32_t)(CL - 1);
@@ -670,6 +703,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
             uint32_t *bnd = cold.bnd[t];
             bin = bnd + ((ps + 1) & 1) * m4;
             bout = bnd + (ps & 1) * m4;
+            bdisc = reinterpret_cast<const uint32_t *>(((uintptr_t)bin + 127) & ~(uintptr_t)127);
             has_in = ps > 0;
             has_out = ps + 1 < cold.passes[t];
             rc_next = 0;
@@ -766,6 +800,14 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
             cp_async_commit();
             cp_async_wait<kAhead>();
             __syncwarp();
+#if SWGB_DISCARD
+            if constexpr (!P8) {
+                // the boundary-in words of columns below s + kU are in the ring
+                const bool dd = gl == 0 && live && has_in && bdisc + 32 <= bin + min(s + kU, stop);
+                discard_l2_if(bdisc, dd);
+                bdisc += dd ? 32 : 0;
+            }
+#endif
 
             // column residues of the upper rows (the lower half takes each one
             // step later, so its residue is the upper half's of the step before)
@@ -810,28 +852,39 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                     const int j0 = s + u - 2 * gl;
                     const int j1 = j0 - 1;
                     const bool in1 = (unsigned)j1 < (unsigned)mcols;
-                    uint32_t inH = __shfl_up_sync(kFull, outHw, 1, G);
-                    uint32_t inF = LIN ? 0u : __shfl_up_sync(kFull, outFw, 1, G);
-                    if (gl == 0) {
-                        // previous strip's last row (H low, F - go high), or (0, 0)
-                        inH = bws[u];
-                        inF = bws[u];
+                    uint32_t upH, upF;
+                    if constexpr (SWGB_ONE_SHUFFLE && !LIN && !P8) {
+                        // the lane above's last row as one word (H low, F - go
+                        // high); lane 0: the previous strip's boundary word
+                        uint32_t inX = __shfl_up_sync(kFull, outX, 1, G);
+                        if (gl == 0) inX = bws[u];
+                        upH = __byte_perm(inX, outHw, 0x5410);
+                        upF = __byte_perm(inX, outFw, 0x5432);
+                    } else {
+                        uint32_t inH = __shfl_up_sync(kFull, outHw, 1, G);
+                        uint32_t inF = LIN ? 0u : __shfl_up_sync(kFull, outFw, 1, G);
+                        if (gl == 0) {
+                            // previous strip's last row (H low, F - go high), or (0, 0)
+                            inH = bws[u];
+                            inF = bws[u];
+                        }
+                        // word 0's row above: the lane above's last row (high half of
+                        // its last word; lane 0: the boundary word's halves) and this
+                        // lane's row R/2 - 1 of the step before
+                        upH = __byte_perm(inH, outHw, selH);
+                        upF = LIN ? 0u : __byte_perm(inF, outFw, 0x5432);
                     }
-                    // word 0's row above: the lane above's last row (high half of
-                    // its last word; lane 0: the boundary word's halves) and this
-                    // lane's row R/2 - 1 of the step before
-                    const uint32_t upH = __byte_perm(inH, outHw, selH);
-                    const uint32_t upF = LIN ? 0u : __byte_perm(inF, outFw, 0x5432);
                     int c0 = cres[u];
                     int c1 = u == 0 ? ccarry : cres[u - 1];
 #if SWGB_STEP_ORDER_FENCE
-                    asm volatile("" : "+r"(c0), "+r"(c1) : "r"(inH));
+                    asm volatile("" : "+r"(c0), "+r"(c1) : "r"(upH));
 #endif
                     // s' of word k: 32-bit profile, the sum of a low-half word
                     // (row k, column j0) and a high-half word (row R/2 + k,
                     // column j1); byte profile, the two rows' bytes moved to
                     // the halves (zero-extended: every byte is below 128)
                     uint32_t scw[W];
+                    [[maybe_unused]] uint32_t sch[W];
                     if constexpr (P8) {
                         const uint2 b0 = *reinterpret_cast<const uint2 *>(
                             prof + ((size_t)c0 * 32 + lane) * 16);
@@ -846,7 +899,14 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                         int sc[R];
                         load_scores_halves<R, false, 2>(prof, c0, c1, lane, sc);
 #pragma unroll
-                        for (int k = 0; k < W; ++k) scw[k] = (uint32_t)sc[k] + (uint32_t)sc[W + k];
+                        for (int k = 0; k < W; ++k) {
+                            if constexpr (SWGB_DADD_FMA != 0) {
+                                scw[k] = (uint32_t)sc[k];
+                                sch[k] = (uint32_t)sc[W + k];
+                            } else {
+                                scw[k] = (uint32_t)sc[k] + (uint32_t)sc[W + k];
+                            }
+                        }
                     }
                     uint32_t diag = diag0w;
                     uint32_t F = LIN ? 0u : __viaddmax_s16x2(upF, geP, upH);
@@ -858,7 +918,19 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         // carry-free: both halves of every term are non-negative
-                        const uint32_t D = diag + scw[k];
+                        uint32_t D;
+                        if constexpr (SWGB_DADD_FMA && !P8) {
+                            asm("mad.lo.u32 %0, %1, %2, %3;"
+                                : "=r"(D) : "r"(scw[k]), "r"(one_opaque), "r"(diag));
+                            {
+                                uint32_t D2;
+                                asm("mad.lo.u32 %0, %1, %2, %3;"
+                                    : "=r"(D2) : "r"(sch[k]), "r"(one_opaque), "r"(D));
+                                D = D2;
+                            }
+                        } else {
+                            D = diag + scw[k];
+                        }
                         uint32_t V;
                         if constexpr (LIN) {
                             // go == ge: E - go = H_left and F - go = H_up exactly
@@ -892,8 +964,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
                     }
                     outHw = hprev;
                     outFw = F;
+                    outX = __byte_perm(outHw, outFw, 0x7632);
                     if (gl == G - 1 && has_out && (SWGB_BOUT_ANY_COLUMN || in1))
-                        bout_ring[j1 & 31] = __byte_perm(outHw, outFw, 0x7632);
+                        bout_ring[j1 & 31] = outX;
                     diag0w = upH;
                     // a half whose best score grew records (step, acc half); the
                     // step gives the column: j0 = step - 2 gl, j1 = j0 - 1
