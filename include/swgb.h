@@ -175,12 +175,14 @@ int sw_ctx_set_tuning(sw_ctx *ctx, int32_t narrow_log2g, double cap_fraction);
  * override): arith = -1 (default: the packed 16-bit form wherever its bound
  * holds), 0 (scaled int32 always), 1 (packed where legal); rows = 16 or 32
  * rows per lane for the packed form with 32-bit profile words (32 as
- * SW_PLAN_ROWS32).  sw_autotune sets both. */
-int sw_ctx_set_form(sw_ctx *ctx, int32_t arith, int32_t rows);
+ * SW_PLAN_ROWS32); blocks_per_sm = resident blocks per SM of the persistent
+ * kernel (0, the default: as many as its registers and shared memory allow;
+ * a larger value than fits means the same).  sw_autotune sets all three. */
+int sw_ctx_set_form(sw_ctx *ctx, int32_t arith, int32_t rows, int32_t blocks_per_sm);
 
 /* The context's current tuning (any pointer may be NULL). */
 int sw_ctx_get_tuning(const sw_ctx *ctx, int32_t *narrow_log2g, double *cap_fraction,
-                      int32_t *arith, int32_t *rows);
+                      int32_t *arith, int32_t *rows, int32_t *blocks_per_sm);
 
 /*
  * Plan a batch.  q_offsets and r_offsets are HOST arrays of n_pairs + 1
@@ -288,7 +290,8 @@ int sw_plan_preview(const int64_t *q_offsets, const int64_t *r_offsets, int32_t 
  * lane-group width 2, 4 or 8 with long-pair caps 0.25, 0.5, 1 or none, and
  * the planner's own choice; for a batch that takes the packed form with
  * 32-bit profile words, each of those also with 32 rows per lane and in the
- * scaled int32 form), keeps the fastest and sets it on ctx with
+ * scaled int32 form), then the fastest with two resident blocks per SM
+ * instead of three, keeps the fastest and sets it on ctx with
  * sw_ctx_set_tuning and sw_ctx_set_form (sw_ctx_get_tuning reads it back).
  * With a non-NULL cache_path the choice is looked up first and stored after
  * measuring in that JSON file, keyed by GPU name, SM

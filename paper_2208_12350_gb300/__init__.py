@@ -46,9 +46,10 @@ SIGNATURES = {
     "sw_ctx_set_guards": ([_P, _I32], ctypes.c_int),
     "sw_ctx_host_in_place": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
-    "sw_ctx_set_form": ([_P, _I32, _I32], ctypes.c_int),
+    "sw_ctx_set_form": ([_P, _I32, _I32, _I32], ctypes.c_int),
     "sw_ctx_get_tuning": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
-                           ctypes.POINTER(_I32), ctypes.POINTER(_I32)], ctypes.c_int),
+                           ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
+                          ctypes.c_int),
     "sw_plan_rows": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
     "sw_plan_create": ([_P, _P, _P, _I32, _P, _I32, _I32, _I32, _I32, _U32, _PP], ctypes.c_int),
     "sw_plan_execute": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -201,17 +202,18 @@ def sw_ctx_set_tuning(ctx: int, narrow_log2g: int = -1, cap_fraction: float = 0.
     _check(load().sw_ctx_set_tuning(ctx, narrow_log2g, cap_fraction), "sw_ctx_set_tuning")
 
 
-def sw_ctx_set_form(ctx: int, arith: int = -1, rows: int = 16) -> None:
-    """Batched kernel form: arith -1 auto / 0 int32 / 1 packed; rows 16 or 32."""
-    _check(load().sw_ctx_set_form(ctx, arith, rows), "sw_ctx_set_form")
+def sw_ctx_set_form(ctx: int, arith: int = -1, rows: int = 16, blocks_per_sm: int = 0) -> None:
+    """Batched kernel form: arith -1 auto / 0 int32 / 1 packed; rows 16 or 32;
+    resident blocks per SM (0: as many as fit)."""
+    _check(load().sw_ctx_set_form(ctx, arith, rows, blocks_per_sm), "sw_ctx_set_form")
 
 
 def sw_ctx_get_tuning(ctx: int) -> dict:
-    lg, fr, ar, rw = _I32(), ctypes.c_double(), _I32(), _I32()
+    lg, fr, ar, rw, bl = _I32(), ctypes.c_double(), _I32(), _I32(), _I32()
     _check(load().sw_ctx_get_tuning(ctx, ctypes.byref(lg), ctypes.byref(fr), ctypes.byref(ar),
-                                    ctypes.byref(rw)), "sw_ctx_get_tuning")
+                                    ctypes.byref(rw), ctypes.byref(bl)), "sw_ctx_get_tuning")
     return {"narrow_log2g": lg.value, "cap_fraction": fr.value, "arith": ar.value,
-            "rows": rw.value}
+            "rows": rw.value, "blocks_per_sm": bl.value}
 
 
 # -------------------------------------------------------------------- plan
@@ -314,7 +316,8 @@ def sw_autotune(ctx: int, q_offsets, r_offsets, score_matrix, gap_open: int, gap
            "sw_autotune_ex")
     t = sw_ctx_get_tuning(ctx)
     return {"narrow_log2g": lg.value, "cap_fraction": frac.value, "ms": ms.value,
-            "arith": {-1: "auto", 0: "s32", 1: "s16x2"}[t["arith"]], "rows": t["rows"]}
+            "arith": {-1: "auto", 0: "s32", 1: "s16x2"}[t["arith"]], "rows": t["rows"],
+            "blocks_per_sm": t["blocks_per_sm"]}
 
 
 # ---------------------------------------------------------------- one-shot

@@ -69,6 +69,7 @@ struct sw_ctx {
     double cap_fraction = 0.5;  // planner override: long-pair cap (used with narrow_log2g)
     int form_arith = -1;        // batched kernel form: -1 auto, 0 scaled int32, 1 packed 16-bit
     int form_rows = 16;         // packed form with 32-bit profile words: 16 or 32 rows per lane
+    int form_blocks = 0;        // resident blocks per SM of the batched kernel (0: as many as fit)
     // the device reads host memory through the host's page tables over a
     // coherent link (NVLink-C2C on Grace): pinned host inputs are read in place
     bool host_in_place = false;
@@ -257,21 +258,24 @@ int sw_ctx_status(sw_ctx *ctx, int32_t *status) {
     return SW_OK;
 }
 
-int sw_ctx_set_form(sw_ctx *ctx, int32_t arith, int32_t rows) {
-    if (!ctx || arith < -1 || arith > 1 || (rows != 16 && rows != 32))
+int sw_ctx_set_form(sw_ctx *ctx, int32_t arith, int32_t rows, int32_t blocks_per_sm) {
+    if (!ctx || arith < -1 || arith > 1 || (rows != 16 && rows != 32) || blocks_per_sm < 0 ||
+        blocks_per_sm > 32)
         return fail(SW_EINVAL, "sw_ctx_set_form: bad argument");
     ctx->form_arith = arith;
     ctx->form_rows = rows;
+    ctx->form_blocks = blocks_per_sm;
     return SW_OK;
 }
 
 int sw_ctx_get_tuning(const sw_ctx *ctx, int32_t *narrow_log2g, double *cap_fraction,
-                      int32_t *arith, int32_t *rows) {
+                      int32_t *arith, int32_t *rows, int32_t *blocks_per_sm) {
     if (!ctx) return fail(SW_EINVAL, "sw_ctx_get_tuning: ctx is NULL");
     if (narrow_log2g) *narrow_log2g = ctx->narrow_log2g;
     if (cap_fraction) *cap_fraction = ctx->cap_fraction;
     if (arith) *arith = ctx->form_arith;
     if (rows) *rows = ctx->form_rows;
+    if (blocks_per_sm) *blocks_per_sm = ctx->form_blocks;
     return SW_OK;
 }
 
@@ -308,7 +312,8 @@ int sw_plan_create(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
                             &p->hp, &msg, 1, 8192,
                             (flags & SW_PLAN_NO_S16X2) == 0 && ctx->form_arith != 0,
                             group_blocks_per_sm, (flags & SW_PLAN_PAIR_SCRATCH) == 0,
-                            (flags & SW_PLAN_ROWS32) != 0 || ctx->form_rows == 32);
+                            (flags & SW_PLAN_ROWS32) != 0 || ctx->form_rows == 32,
+                            ctx->form_blocks);
     if (rc != SW_OK) {
         delete p;
         return fail(rc, "sw_plan_create: %s", msg.c_str());

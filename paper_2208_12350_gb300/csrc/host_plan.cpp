@@ -81,7 +81,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp, int sample_cap,
                    bool allow_packed, BlocksPerSmFn blocks_per_sm, bool group_slots,
-                   bool rows32) {
+                   bool rows32, int blocks_cap) {
     *out = HostPlan();
     int rc = check_batch(q_offsets, r_offsets, n_pairs, mat, A, go, ge, nullptr, nullptr,
                          nullptr, msg);
@@ -155,6 +155,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
             bps = blocks_per_sm(out->kind, go == ge, A, &smem);
             if (bps < 0) return plan_err(msg, SW_ECUDA, "occupancy query failed");
             group_fits = bps > 0;
+            if (blocks_cap > 0) bps = std::min(bps, blocks_cap);
         }
     }
     std::vector<PlanPair> gp;  // group-path pairs, id = index into gid

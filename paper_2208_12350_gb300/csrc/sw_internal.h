@@ -294,7 +294,7 @@ int make_host_plan(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n
                    int sm_count, int narrow_log2g, double cap_fraction, HostPlan *out,
                    std::string *msg, int min_pairs_per_warp = 1, int sample_cap = 8192,
                    bool allow_packed = true, BlocksPerSmFn blocks_per_sm = group_blocks_per_sm,
-                   bool group_slots = false, bool rows32 = false);
+                   bool group_slots = false, bool rows32 = false, int blocks_cap = 0);
 // Enqueues the kernels of a planned batch on s (queue-head reset included).
 cudaError_t enqueue_plan(const HostPlan &hp, const DeviceTables &t, const uint8_t *q,
                          const uint8_t *r, const Outputs &o, const int8_t *mat, int A, int go,

@@ -103,19 +103,21 @@ def test_autotune_with_plan_flags(gpu_lib, tmp_path):
         swgb.sw_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("arith,rows", [(0, 16), (1, 16), (1, 32), (-1, 32)])
-def test_kernel_forms_exact(gpu_lib, arith, rows):
+@pytest.mark.parametrize("arith,rows,blocks", [(0, 16, 0), (1, 16, 0), (1, 32, 0), (-1, 32, 0),
+                                               (-1, 16, 2), (0, 16, 1)])
+def test_kernel_forms_exact(gpu_lib, arith, rows, blocks):
     """Each kernel form the autotuner chooses between - the packed 16-bit
-    form with 16 or 32 rows per lane, and the scaled int32 form - gives the
-    oracle's results on a batch that spans one-strip, multi-strip and
-    long-cap pairs."""
+    form with 16 or 32 rows per lane, and the scaled int32 form, with as many
+    resident blocks per SM as fit or fewer - gives the oracle's results on a
+    batch that spans one-strip, multi-strip and long-cap pairs."""
     import torch
     swgb = gpu_lib
     b = wl.gen_config(1, n_pairs=1500)
     ctx = swgb.sw_ctx_create(0)
     try:
-        swgb.sw_ctx_set_form(ctx, arith, rows)
-        assert swgb.sw_ctx_get_tuning(ctx)["rows"] == rows
+        swgb.sw_ctx_set_form(ctx, arith, rows, blocks)
+        t = swgb.sw_ctx_get_tuning(ctx)
+        assert t["rows"] == rows and t["blocks_per_sm"] == blocks
         a = swgb.Aligner(b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix, b.gap_open,
                          b.gap_extend, mode=swgb.SW_MODE_BATCHED, ctx=ctx)
         info = swgb.sw_plan_info(a.plan)
@@ -147,7 +149,7 @@ def test_autotune_records_form(gpu_lib, tmp_path):
                                  b.gap_extend, q, r, out, cache_path=str(cache))
         assert first["arith"] in ("auto", "s32", "s16x2") and first["rows"] in (16, 32)
         e = json.loads(cache.read_text())["entries"][0]
-        assert {e["arith"], e["rows"]} <= {-1, 0, 1, 16, 32}
+        assert {e["arith"], e["rows"]} <= {-1, 0, 1, 16, 32} and e["blocks_per_sm"] in (0, 2)
         swgb.sw_ctx_set_form(ctx2, 0, 16)
         second = swgb.sw_autotune(ctx2, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
                                   b.gap_extend, q, r, out, cache_path=str(cache))
