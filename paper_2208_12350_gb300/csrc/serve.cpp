@@ -203,8 +203,8 @@ struct Launch {
     bool enqueued = false;  // its work and completion event are on the stream
 };
 
-// Planner threads: a launch's host planning takes milliseconds for tens of
-// thousands of pairs, so several launches are planned and enqueued at once
+// Helper threads: a launch's host work (staging copies, table uploads and
+// the enqueue of its kernels) runs on these, several launches at once,
 // while the worker keeps admitting and retiring.
 constexpr int kPlanners = 8;
 
