@@ -667,14 +667,16 @@ int ctx_alloc_async(sw_ctx *ctx, size_t bytes, cudaStream_t s, void **out) {
 // Copies `bytes` of host data to device memory `dst` on stream s through the
 // context's page-locked staging buffer (asynchronous DMA; the buffer is
 // reused only after its previous upload has completed).
-int ctx_upload_async(sw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {
-    if (bytes == 0) return SW_OK;
-    std::lock_guard<std::mutex> lk(ctx->pinned_mu);
+int ctx_pinned_acquire(sw_ctx *ctx, size_t bytes, void **host) {
+    ctx->pinned_mu.lock();
     if (ctx->pinned_ev) {
-        if (cudaEventSynchronize(ctx->pinned_ev) != cudaSuccess)
+        if (cudaEventSynchronize(ctx->pinned_ev) != cudaSuccess) {
+            ctx->pinned_mu.unlock();
             return set_error(SW_ECUDA, "staging event wait failed");
+        }
     } else if (cudaEventCreateWithFlags(&ctx->pinned_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        ctx->pinned_mu.unlock();
         return set_error(SW_ECUDA, "staging event creation failed");
     }
     if (ctx->pinned_cap < bytes) {
@@ -684,16 +686,35 @@ int ctx_upload_async(sw_ctx *ctx, void *dst, const void *src, size_t bytes, cuda
         const size_t cap = std::max(bytes, (size_t)1 << 20);
         if (cudaMallocHost(&ctx->pinned, cap) != cudaSuccess) {
             cudaGetLastError();
+            ctx->pinned_mu.unlock();
             return set_error(SW_ENOMEM, "page-locked staging allocation failed");
         }
         ctx->pinned_cap = cap;
     }
-    std::memcpy(ctx->pinned, src, bytes);
-    if (cudaMemcpyAsync(dst, ctx->pinned, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaEventRecord(ctx->pinned_ev, s) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(SW_ECUDA, "staged upload failed");
-    }
+    *host = ctx->pinned;
     return SW_OK;
+}
+
+int ctx_pinned_commit(sw_ctx *ctx, void *dst, size_t bytes, cudaStream_t s) {
+    int rc = SW_OK;
+    if (bytes > 0 &&
+        (cudaMemcpyAsync(dst, ctx->pinned, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaEventRecord(ctx->pinned_ev, s) != cudaSuccess)) {
+        cudaGetLastError();
+        rc = set_error(SW_ECUDA, "staged upload failed");
+    }
+    ctx->pinned_mu.unlock();
+    return rc;
+}
+
+void ctx_pinned_release(sw_ctx *ctx) { ctx->pinned_mu.unlock(); }
+
+int ctx_upload_async(sw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return SW_OK;
+    void *host = nullptr;
+    const int rc = ctx_pinned_acquire(ctx, bytes, &host);
+    if (rc != SW_OK) return rc;
+    std::memcpy(host, src, bytes);
+    return ctx_pinned_commit(ctx, dst, bytes, s);
 }
 }  // namespace swgb

@@ -188,21 +188,32 @@ __global__ void __launch_bounds__(kThreads) cigar_kernel(const __grid_constant__
 
 // ---- fast path
 
-constexpr int kTbRows = 16;        // rows per lane
-constexpr int kTbMaxRows = 512;    // 32 lanes x 16 rows: one strip per span
+constexpr int kTbMaxRows = 512;  // 32 lanes x 16 rows: one strip per span
+constexpr int kTbRowOpts = 4;    // rows per lane: 10, 12, 14 or 16
 constexpr int32_t kTbNegInf = -(1 << 29);
+__host__ __device__ constexpr int tb_rows(int ri) { return 10 + 2 * ri; }
 
 struct TbPair {
     int64_t q, r;   // offsets of the spans' first residues
     int64_t ch;     // offset (64-bit words) of its choice words: G x M of them
     int64_t out;    // offset of its ops in the output
-    int32_t N, M, id, log2g;
+    int32_t N, M, id, cls;  // cls = log2(G) * kTbRowOpts + rows option
+};
+
+constexpr int kTbClasses = 6 * kTbRowOpts;
+
+// A launch's blocks by class: blocks [block0, next class's block0) take the
+// class's pairs [first, first + count), 128 / G of them per block.
+struct TbClassRange {
+    int32_t cls, first, count, block0;
 };
 
 struct TbParams {
     const uint8_t *q, *r;
-    const TbPair *pairs;  // this launch's pairs (one width), longest first
+    const TbPair *pairs;  // by class (widest first), longest first within a class
     int32_t n_pairs;
+    int32_t n_ranges;
+    TbClassRange ranges[kTbClasses];
     uint64_t *choice;
     uint32_t *ops;
     int32_t *n_ops;
@@ -210,39 +221,179 @@ struct TbParams {
     int8_t mat[kMaxAlphabet * kMaxAlphabet];
 };
 
-__device__ void tb_walk(const TbParams &p, const TbPair &tp);
-
-template <int LOG2G>
-__global__ void __launch_bounds__(128) tb_fill_kernel(const __grid_constant__ TbParams p) {
+// The walk back of one pair from (N, M), by its whole lane group.  The walk
+// is a sequence of runs - diagonal moves in state H, moves left in state E
+// (D ops), moves up in state F (I ops) - and each round looks ahead along the
+// current run: lane t of the group reads the choice nibbles of the next L
+// cells t L .. t L + L - 1 of the run (G L >= 16 cells in all), a ballot
+// finds the first cell that ends the run, and the whole run up to it is
+// taken at once.  All lanes keep the same walk state; lane 0 writes the ops.
+template <int LOG2G, int R>
+__device__ __forceinline__ void tb_walk_group(const TbParams &p, const TbPair &tp, int gl) {
     constexpr int G = 1 << LOG2G;
-    __shared__ int smat[kMaxAlphabet * kMaxAlphabet];  // s - go
+    constexpr int L = G >= 16 ? 1 : 16 / G;  // cells per lane and round
+    constexpr int T = G * L;                 // cells per round
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int gshift = lane & ~(G - 1);
+    const uint64_t *ch = p.choice + tp.ch;
+    uint32_t *out = p.ops + tp.out;
+    const int M = tp.M;
+    const bool lin = p.go == p.ge;
+    auto cell = [&](int ii, int jj) -> uint32_t {  // 1 <= ii <= N, 1 <= jj <= M
+        const int l = (ii - 1) / R, r = ii - 1 - l * R;
+        return (uint32_t)(ch[(int64_t)l * M + (jj - 1)] >> (4 * r)) & 15u;
+    };
+    int nr = 0, run_op = -1, run_len = 0;
+    auto push = [&](int op, int len) {
+        if (op == run_op) {
+            run_len += len;
+            return;
+        }
+        if (run_len > 0) {
+            if (gl == 0) out[nr] = ((uint32_t)run_len << 4) | (uint32_t)run_op;
+            ++nr;
+        }
+        run_op = op;
+        run_len = len;
+    };
+    int i = tp.N, j = M, state = 0;  // 0 = H, 1 = E, 2 = F
+    while (i > 0 || j > 0) {
+        // this lane's first cell of the round that ends the run (T: none), and
+        // what that cell says (16: the run reached the matrix edge)
+        int stop = T;
+        uint32_t cs = 0;
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+            const int t = gl * L + u;
+            if (stop < T) break;
+            if (state == 0) {
+                const int ii = i - t, jj = j - t;
+                if (ii < 1 || jj < 1) {
+                    stop = t;
+                    cs = 16;
+                } else {
+                    const uint32_t c = cell(ii, jj);
+                    if (!(c & 1u)) {
+                        stop = t;
+                        cs = c;
+                    }
+                }
+            } else if (state == 1) {
+                // a D at (i, j - t), then the gap opened there?
+                const int jj = j - t;
+                if (jj < 1) {
+                    stop = t;  // (not reached: a gap opens at column 1 at the latest)
+                    cs = 16;
+                } else if (i > 0 ? (cell(i, jj) & 4u) != 0 : (jj == 1 || lin)) {
+                    stop = t;
+                }
+            } else {
+                const int ii = i - t;
+                if (ii < 1) {
+                    stop = t;
+                    cs = 16;
+                } else if (j > 0 ? (cell(ii, j) & 8u) != 0 : (ii == 1 || lin)) {
+                    stop = t;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(gmask, stop < T) >> gshift;
+        const int src = m ? __ffs(m) - 1 : 0;
+        const int first = __shfl_sync(gmask, stop, src + gshift);
+        const uint32_t c0 = __shfl_sync(gmask, cs, src + gshift);
+        if (state == 0) {
+            if (!m) {
+                push(0, T);
+                i -= T;
+                j -= T;
+            } else {
+                if (first > 0) push(0, first);
+                i -= first;
+                j -= first;
+                if (c0 == 16)
+                    state = i == 0 ? 1 : 2;  // the boundary row is all D, the column all I
+                else
+                    state = (c0 & 2u) ? 1 : 2;
+                if (i == 0 && j == 0) break;
+            }
+        } else if (state == 1) {
+            const int len = m ? first + 1 : T;
+            push(2, len);
+            j -= len;
+            if (m) state = 0;
+        } else {
+            const int len = m ? first + 1 : T;
+            push(1, len);
+            i -= len;
+            if (m) state = 0;
+        }
+    }
+    if (run_len > 0) {
+        if (gl == 0) out[nr] = ((uint32_t)run_len << 4) | (uint32_t)run_op;
+        ++nr;
+    }
+    // the ops were produced last first: reverse them, the group together
+    __syncwarp(gmask);
+    for (int a = gl; a < nr / 2; a += G) {
+        const uint32_t x = out[a], y = out[nr - 1 - a];
+        out[a] = y;
+        out[nr - 1 - a] = x;
+    }
+    if (gl == 0) p.n_ops[tp.id] = nr;
+}
+
+// One lane group of G lanes per pair; lane t owns rows R t .. R t + R - 1 of
+// the span.  Each lane's scores s - go for its rows come from a profile it
+// builds in shared memory (R bytes per residue code, one 16-byte load per
+// step), so a step reads no per-cell table entry.
+template <int LOG2G, int R>
+__device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &cr,
+                                        const int *smat, uint4 *tb_prof) {
+    constexpr int G = 1 << LOG2G;
+    static_assert(R <= 16, "a lane's decisions fill at most one 64-bit word per column");
     const int A = p.A, go = p.go, ge = p.ge;
-    for (int i = threadIdx.x; i < A * A; i += blockDim.x) smat[i] = (int)p.mat[i] - go;
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
-    const int pidx = ((int)blockIdx.x * 4 + (int)(threadIdx.x >> 5)) * (32 / G) + (lane >> LOG2G);
-    const bool has = pidx < p.n_pairs;
+    const int grp = (int)threadIdx.x >> LOG2G;
+    const int pidx = ((int)blockIdx.x - cr.block0) * (128 / G) + grp;
+    const bool has = pidx < cr.count;
     TbPair tp{};
-    if (has) tp = p.pairs[pidx];
+    if (has) tp = p.pairs[cr.first + pidx];
     const int N = has ? tp.N : 0, M = has ? tp.M : 0;
     const uint8_t *qa = p.q + tp.q, *rb = p.r + tp.r;
-    // this lane's rows i = 16 gl + r + 1 (1-based): matrix row offsets and
-    // the column-0 boundary (H = go + (i - 1) ge, kept as H + go; E = -inf)
-    int xr[kTbRows], X[kTbRows], E[kTbRows];
+    {
+        // this lane's profile: byte r of entry y is s(q[R gl + r], y) - go (the
+        // host checks that it fits a signed byte); rows past the span take 0
+        int xr[R];
 #pragma unroll
-    for (int r = 0; r < kTbRows; ++r) {
-        const int i0 = gl * kTbRows + r;  // 0-based row
-        xr[r] = i0 < N ? min((int)qa[i0], A - 1) * A : 0;
+        for (int r = 0; r < R; ++r) {
+            const int i0 = gl * R + r;
+            xr[r] = i0 < N ? min((int)qa[i0], A - 1) * A : -1;
+        }
+        for (int y = 0; y < A; ++y) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (xr[r] >= 0) w[r >> 2] |= ((uint32_t)smat[xr[r] + y] & 0xFFu) << (8 * (r & 3));
+            tb_prof[y * 128 + threadIdx.x] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    // this lane's rows i = R gl + r + 1 (1-based): the column-0 boundary
+    // (H = go + (i - 1) ge, kept as H + go; E = -inf)
+    int X[R], E[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i0 = gl * R + r;  // 0-based row
         X[r] = go + i0 * ge + go;
         E[r] = kTbNegInf;
     }
     // The first row's diagonal: the row above at the previous column.  Lane 0
     // starts from H[0][0] + go; every lane passes down, until its first
-    // column, its last row's column-0 boundary (H[16 gl + 16][0] + go), which
+    // column, its last row's column-0 boundary (H[R gl + R][0] + go), which
     // the lane below takes as the diagonal of its first column.
     int diag0 = go;
-    int outX = X[kTbRows - 1], outF = kTbNegInf;
+    int outX = X[R - 1], outF = kTbNegInf;
     uint64_t *ch = p.choice + tp.ch + (int64_t)gl * M;
     // the warp runs until its longest pair is done (pairs sorted longest first)
     int steps = has ? M + G - 1 : 0;
@@ -265,15 +416,24 @@ __global__ void __launch_bounds__(128) tb_fill_kernel(const __grid_constant__ Tb
         // next column's residue, fetched a step ahead
         y_next = (j + 1 >= 1 && j + 1 <= M) ? min((int)rb[j], A - 1) : 0;
         if (in) {
+            const uint4 pw = tb_prof[y * 128 + threadIdx.x];
+            const uint32_t pws[4] = {pw.x, pw.y, pw.z, pw.w};
             int diag = diag_first;
             uint32_t lo = 0, hi = 0;
 #pragma unroll
-            for (int r = 0; r < kTbRows; ++r) {
+            for (int r = 0; r < R; ++r) {
+                // byte r & 3 of word r >> 2 with its sign replicated into the
+                // upper bytes (PTX prmt: a selector nibble with its top bit set
+                // replicates the sign of the byte it names)
+                constexpr unsigned kSx[4] = {0x8880u, 0x9991u, 0xAAA2u, 0xBBB3u};
+                uint32_t sx;
+                asm("prmt.b32 %0, %1, 0, %2;" : "=r"(sx) : "r"(pws[r >> 2]), "r"(kSx[r & 3]));
+                const int sc = (int)sx;
                 bool eo, fo, ef, dm;
                 const int e = __vibmax_s32(X[r], E[r] + ge, &eo);  // E = max(H_left + go, E + ge)
                 const int f = __vibmax_s32(upX, upF + ge, &fo);    // F = max(H_up + go, F_up + ge)
                 const int m1 = __vibmax_s32(e, f, &ef);
-                const int h = __vibmax_s32(diag + smat[xr[r] + y], m1, &dm);
+                const int h = __vibmax_s32(diag + sc, m1, &dm);
                 const uint32_t nib = (uint32_t)dm | ((uint32_t)ef << 1) | ((uint32_t)eo << 2) |
                                      ((uint32_t)fo << 3);
                 if (r < 8)
@@ -291,73 +451,71 @@ __global__ void __launch_bounds__(128) tb_fill_kernel(const __grid_constant__ Tb
             outF = upF;
         }
     }
-    // the group's first lane walks back while its choice words are in L2 (the
-    // warp barrier orders the other lanes' stores before its loads)
+    // the group walks back while its choice words are in L2 (the barrier
+    // orders every lane's stores before the loads)
     __syncwarp();
-    if (has && gl == 0) tb_walk(p, tp);
+    if (has) tb_walk_group<LOG2G, R>(p, tp, gl);
 }
 
-// The walk back of one fast-path pair from (N, M), reading its choice words.
-__device__ void tb_walk(const TbParams &p, const TbPair &tp) {
-    const uint64_t *ch = p.choice + tp.ch;
-    uint32_t *out = p.ops + tp.out;
-    const bool lin = p.go == p.ge;
-    int nr = 0;
-    auto push = [&](int op) {
-        if (nr > 0 && (int)(out[nr - 1] & 15u) == op)
-            out[nr - 1] += 16u;
-        else
-            out[nr++] = (1u << 4) | (uint32_t)op;
+// Every fast-path pair of a call in one launch: each block finds its class
+// (lane-group width and rows per lane) in the range table and runs that
+// instantiation, so the classes share one grid and one tail.
+__global__ void __launch_bounds__(128) tb_fill_kernel(const __grid_constant__ TbParams p) {
+    extern __shared__ uint4 tb_prof[];                 // [code][thread]: R bytes of s - go
+    __shared__ int smat[kMaxAlphabet * kMaxAlphabet];  // s - go
+    const int A = p.A;
+    for (int i = threadIdx.x; i < A * A; i += blockDim.x) smat[i] = (int)p.mat[i] - p.go;
+    __syncthreads();
+    int c = 0;
+    for (int k = 1; k < p.n_ranges; ++k)
+        if ((int)blockIdx.x >= p.ranges[k].block0) c = k;
+    const TbClassRange cr = p.ranges[c];
+#define SWGB_TB_CASE(LG, RI)                                               \
+    case (LG) * kTbRowOpts + (RI):                                         \
+        tb_fill<LG, tb_rows(RI)>(p, cr, smat, tb_prof);                    \
+        break;
+#define SWGB_TB_ROWS(LG) \
+    SWGB_TB_CASE(LG, 0) SWGB_TB_CASE(LG, 1) SWGB_TB_CASE(LG, 2) SWGB_TB_CASE(LG, 3)
+    switch (cr.cls) {
+        SWGB_TB_ROWS(0)
+        SWGB_TB_ROWS(1)
+        SWGB_TB_ROWS(2)
+        SWGB_TB_ROWS(3)
+        SWGB_TB_ROWS(4)
+        SWGB_TB_ROWS(5)
+        default: break;
+    }
+#undef SWGB_TB_ROWS
+#undef SWGB_TB_CASE
+}
+
+// The width and rows per lane of a span of N rows: the smallest G R >= N over
+// R in {10, 12, 14, 16} and G a power of two up to 32 (ties: more rows per
+// lane, so fewer lanes and less skew).
+int tb_class_of(int32_t N) {
+    int best = -1, best_rows = INT32_MAX;
+    for (int ri = kTbRowOpts - 1; ri >= 0; --ri) {
+        int lg = 0;
+        while ((tb_rows(ri) << lg) < N && lg < 5) ++lg;
+        const int rows = tb_rows(ri) << lg;
+        if (rows >= N && rows < best_rows) {
+            best_rows = rows;
+            best = lg * kTbRowOpts + ri;
+        }
+    }
+    return best;
+}
+
+// tb_class_of for N in [1, kTbMaxRows], from a table built once
+int tb_class(int32_t N) {
+    struct Table {
+        int8_t cls[kTbMaxRows + 1];
+        Table() {
+            for (int k = 0; k <= kTbMaxRows; ++k) cls[k] = (int8_t)tb_class_of(k);
+        }
     };
-    int i = tp.N, j = tp.M, state = 0;  // 0 = H, 1 = E, 2 = F
-    while (i > 0 || j > 0) {
-        uint32_t c = 0;
-        if (i > 0 && j > 0) {
-            const uint64_t w = ch[(int64_t)((i - 1) / kTbRows) * tp.M + (j - 1)];
-            c = (uint32_t)(w >> (4 * ((i - 1) % kTbRows))) & 15u;
-        }
-        if (state == 0) {
-            if (i > 0 && j > 0) {
-                if (c & 1u) {
-                    push(0);
-                    --i;
-                    --j;
-                } else {
-                    state = (c & 2u) ? 1 : 2;
-                }
-            } else {
-                state = i == 0 ? 1 : 2;  // the boundary row is all D, the column all I
-            }
-        } else if (state == 1) {
-            push(2);
-            const bool open = (i > 0 && j > 0) ? (c & 4u) != 0 : (j == 1 || lin);
-            --j;
-            if (open) state = 0;
-        } else {
-            push(1);
-            const bool open = (i > 0 && j > 0) ? (c & 8u) != 0 : (i == 1 || lin);
-            --i;
-            if (open) state = 0;
-        }
-    }
-    for (int a = 0, b = nr - 1; a < b; ++a, --b) {
-        const uint32_t tmp = out[a];
-        out[a] = out[b];
-        out[b] = tmp;
-    }
-    p.n_ops[tp.id] = nr;
-}
-
-using TbFill = void (*)(TbParams);
-TbFill tb_fill_of(int log2g) {
-    switch (log2g) {
-        case 0: return tb_fill_kernel<0>;
-        case 1: return tb_fill_kernel<1>;
-        case 2: return tb_fill_kernel<2>;
-        case 3: return tb_fill_kernel<3>;
-        case 4: return tb_fill_kernel<4>;
-        default: return tb_fill_kernel<5>;
-    }
+    static const Table t;
+    return t.cls[N];
 }
 
 }  // namespace
@@ -398,13 +556,25 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
     int smax = 0;
     for (int k = 0; k < alphabet_size * alphabet_size; ++k)
         smax = std::max(smax, std::abs((int)score_matrix[k]));
-    // per-cell magnitude bound of the fast path's int32 values
+    // per-cell magnitude bound of the fast path's int32 values, and its
+    // profile of s - go as signed bytes
     const int64_t unit = (int64_t)-gap_open - gap_extend + smax;
+    bool bytes_ok = true;
+    for (int k = 0; k < alphabet_size * alphabet_size; ++k) {
+        const int v = (int)score_matrix[k] - gap_open;
+        bytes_ok = bytes_ok && v >= -128 && v <= 127;
+    }
     char buf[160];
     std::vector<CigarPair> pairs;  // general path
-    std::vector<TbPair> fast;
-    fast.reserve((size_t)n);
+    // fast-path pairs: a key per pair (class and span length; kNoKey for the
+    // others), kept per thread across calls so that its pages stay mapped
+    constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+    thread_local std::vector<uint32_t> keyv;
+    keyv.resize((size_t)n);
+    int64_t n_fast = 0;
+    int32_t mlo = INT32_MAX, mhi = 0;
     for (int64_t p = 0; p < n; ++p) {
+        keyv[p] = kNoKey;
         const int32_t S = results[p], qe = results[n + p], re = results[2 * n + p],
                       qs = results[3 * n + p], rs = results[4 * n + p];
         if (S <= 0) continue;
@@ -420,18 +590,12 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
                      (long long)p, (long long)N + M);
             return set_error(SW_ERANGE, buf);
         }
-        if (N <= kTbMaxRows && ((int64_t)N + M + 2) * unit <= ((int64_t)1 << 28)) {
-            TbPair tp{};
-            tp.q = q_offsets[p] + qs;
-            tp.r = r_offsets[p] + rs;
-            tp.N = N;
-            tp.M = M;
-            tp.id = (int32_t)p;
-            tp.out = cigar_offsets[p];
-            int lg = 0;
-            while ((kTbRows << lg) < N) ++lg;
-            tp.log2g = lg;
-            fast.push_back(tp);
+        if (bytes_ok && N <= kTbMaxRows &&
+            ((int64_t)kTbMaxRows + M + 2) * unit <= ((int64_t)1 << 28)) {
+            keyv[p] = ((uint32_t)tb_class(N) << 16) | (uint32_t)M;  // M < 2^16
+            ++n_fast;
+            mlo = std::min(mlo, M);
+            mhi = std::max(mhi, M);
             continue;
         }
         CigarPair cp{};
@@ -443,7 +607,7 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
         cp.out = cigar_offsets[p];
         pairs.push_back(cp);
     }
-    if ((!pairs.empty() || !fast.empty()) && (!q_seqs || !r_seqs || !out_ops))
+    if ((!pairs.empty() || n_fast > 0) && (!q_seqs || !r_seqs || !out_ops))
         return set_error(SW_EINVAL, "sw_traceback: NULL device pointer");
     int dev_prev = -1;
     cudaGetDevice(&dev_prev);
@@ -460,38 +624,63 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
     cudaError_t e = cudaMemsetAsync(out_n_ops, 0, (size_t)n * sizeof(int32_t), s);
     if (e != cudaSuccess) return set_error(SW_ECUDA, "sw_traceback: memset failed");
 
-    // ---- fast path: widths longest first within each, choice words per pair
-    if (!fast.empty()) {
-        {
-            // by width, then longest first: a counting sort on (width, Mmax - M)
-            // over the batch's range of span lengths
-            int32_t mlo = INT32_MAX, mhi = 0;
-            for (const TbPair &t : fast) {
-                mlo = std::min(mlo, t.M);
-                mhi = std::max(mhi, t.M);
-            }
-            const size_t span = (size_t)(mhi - mlo) + 1;
-            std::vector<int32_t> count(6 * span + 1, 0);
-            auto key = [&](const TbPair &t) { return (size_t)t.log2g * span + (size_t)(mhi - t.M); };
-            for (const TbPair &t : fast) ++count[key(t) + 1];
-            for (size_t k = 1; k < count.size(); ++k) count[k] += count[k - 1];
-            std::vector<TbPair> sorted(fast.size());
-            for (const TbPair &t : fast) sorted[(size_t)count[key(t)]++] = t;
-            fast.swap(sorted);
+    // ---- fast path: classes widest first, longest first within each (a
+    // counting sort on (class, Mmax - M)), the records written in that order
+    // straight into the page-locked staging buffer
+    if (n_fast > 0) {
+        const size_t span = (size_t)(mhi - mlo) + 1;
+        std::vector<int32_t> count((size_t)kTbClasses * span + 1, 0);
+        auto slot = [&](uint32_t k) {
+            return (size_t)(kTbClasses - 1 - (int)(k >> 16)) * span + (size_t)(mhi - (int32_t)(k & 0xFFFFu));
+        };
+        for (int64_t p = 0; p < n; ++p)
+            if (keyv[p] != kNoKey) ++count[slot(keyv[p]) + 1];
+        for (size_t k = 1; k < count.size(); ++k) count[k] += count[k - 1];
+        const size_t rec_bytes = (size_t)n_fast * sizeof(TbPair);
+        void *host = nullptr;
+        if ((rc = ctx_pinned_acquire(ctx, rec_bytes, &host)) != SW_OK) return rc;
+        TbPair *fast = static_cast<TbPair *>(host);
+        for (int64_t p = 0; p < n; ++p) {
+            const uint32_t k = keyv[p];
+            if (k == kNoKey) continue;
+            TbPair &tp = fast[count[slot(k)]++];
+            const int32_t qe = results[n + p], re = results[2 * n + p], qs = results[3 * n + p],
+                          rs = results[4 * n + p];
+            tp.q = q_offsets[p] + qs;
+            tp.r = r_offsets[p] + rs;
+            tp.out = cigar_offsets[p];
+            tp.N = qe - qs + 1;
+            tp.M = re - rs + 1;
+            tp.id = (int32_t)p;
+            tp.cls = (int32_t)(k >> 16);
         }
         int64_t words = 0;
-        for (TbPair &tp : fast) {
-            tp.ch = words;
-            words += ((int64_t)1 << tp.log2g) * tp.M;
+        for (int64_t a = 0; a < n_fast; ++a) {
+            fast[a].ch = words;
+            words += ((int64_t)1 << (fast[a].cls / kTbRowOpts)) * fast[a].M;
         }
         void *ws = nullptr;
-        const size_t pair_bytes = (fast.size() * sizeof(TbPair) + 255) & ~(size_t)255;
-        if ((rc = ctx_alloc_async(ctx, pair_bytes + (size_t)words * 8, s, &ws)) != SW_OK)
+        const size_t pair_bytes = (rec_bytes + 255) & ~(size_t)255;
+        if ((rc = ctx_alloc_async(ctx, pair_bytes + (size_t)words * 8, s, &ws)) != SW_OK) {
+            ctx_pinned_release(ctx);
             return rc;
+        }
         TbPair *d_fast = static_cast<TbPair *>(ws);
         uint64_t *d_choice = reinterpret_cast<uint64_t *>(static_cast<unsigned char *>(ws) + pair_bytes);
-        if ((rc = ctx_upload_async(ctx, d_fast, fast.data(), fast.size() * sizeof(TbPair), s)) !=
-            SW_OK) {
+        // the ranges of the classes, read from the records before they are released
+        TbClassRange ranges[kTbClasses];
+        int n_ranges = 0;
+        int64_t blocks = 0;
+        for (int64_t a = 0; a < n_fast;) {
+            int64_t b = a;
+            while (b < n_fast && fast[b].cls == fast[a].cls) ++b;
+            const int cls = fast[a].cls;
+            const int64_t per_block = 128 >> (cls / kTbRowOpts);
+            ranges[n_ranges++] = {cls, (int32_t)a, (int32_t)(b - a), (int32_t)blocks};
+            blocks += (b - a + per_block - 1) / per_block;
+            a = b;
+        }
+        if ((rc = ctx_pinned_commit(ctx, d_fast, rec_bytes, s)) != SW_OK) {
             cudaFreeAsync(ws, s);
             return rc;
         }
@@ -506,17 +695,19 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
         tp.go = gap_open;
         tp.ge = gap_extend;
         std::memcpy(tp.mat, score_matrix, (size_t)alphabet_size * alphabet_size);
-        for (size_t a = 0; e == cudaSuccess && a < fast.size();) {
-            size_t b = a;
-            while (b < fast.size() && fast[b].log2g == fast[a].log2g) ++b;
-            const int lg = fast[a].log2g;
-            const int64_t per_block = 4 * (32 >> lg);
-            tp.pairs = d_fast + a;
-            tp.n_pairs = (int32_t)(b - a);
-            const int64_t blocks = ((int64_t)(b - a) + per_block - 1) / per_block;
-            tb_fill_of(lg)<<<(unsigned)blocks, 128, 0, s>>>(tp);
+        // each thread's profile: one 16-byte entry per residue code
+        const size_t prof_bytes = (size_t)alphabet_size * 128 * 16;
+        tp.pairs = d_fast;
+        tp.n_pairs = (int32_t)n_fast;
+        tp.n_ranges = n_ranges;
+        std::memcpy(tp.ranges, ranges, sizeof ranges);
+        // with the kernel's static shared memory (the score table) the block
+        // can pass the default 48 KB
+        e = cudaFuncSetAttribute(tb_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)prof_bytes);
+        if (e == cudaSuccess) {
+            tb_fill_kernel<<<(unsigned)blocks, 128, prof_bytes, s>>>(tp);
             e = cudaGetLastError();
-            a = b;
         }
         cudaFreeAsync(ws, s);  // stream-ordered: after the kernels that use it
         if (e != cudaSuccess)

@@ -67,7 +67,8 @@ int check_batch(const int64_t *q_offsets, const int64_t *r_offsets, int32_t n_pa
         if (a > SW_MAX_LEN || b > SW_MAX_LEN)
             return plan_err(msg, SW_ERANGE, "pair %lld has lengths (%lld, %lld) above SW_MAX_LEN", i,
                             a, b);
-        if (a > 0 && b > 0 && group_path_eligible((int)a, (int)b, smax, go, ge))
+        if (max_scratch_words && a > 0 && b > 0 &&
+            group_path_eligible((int)a, (int)b, smax, go, ge))
             words += pair_scratch_words((int)a, (int)b, 1 << kMinLog2G, kRows);
     }
     if (q_bytes) *q_bytes = n_pairs > 0 ? q_offsets[n_pairs] : 0;

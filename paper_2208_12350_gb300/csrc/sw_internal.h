@@ -264,6 +264,14 @@ int ctx_alloc_async(::sw_ctx *ctx, size_t bytes, cudaStream_t s, void **out);
 // Host-to-device upload on s through the context's page-locked staging
 // buffer (the host data may be reused when the call returns).
 int ctx_upload_async(::sw_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s);
+// The same staging buffer for a caller that writes the upload in place:
+// ctx_pinned_acquire waits for the previous upload through it, grows it to
+// `bytes` and returns it held; ctx_pinned_commit enqueues the copy of its
+// first `bytes` to dst on s and releases it; ctx_pinned_release releases it
+// without a copy.  Every acquire is followed by exactly one of the two.
+int ctx_pinned_acquire(::sw_ctx *ctx, size_t bytes, void **host);
+int ctx_pinned_commit(::sw_ctx *ctx, void *dst, size_t bytes, cudaStream_t s);
+void ctx_pinned_release(::sw_ctx *ctx);
 
 // Checks the arguments and plans a batch (no device allocation; queries the
 // group kernel's occupancy on the current device).  Returns an sw_status;

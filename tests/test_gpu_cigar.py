@@ -114,3 +114,54 @@ def test_errors(gpu_lib, ctx):
         gpu_lib.sw_traceback(ctx, q, b.q_offsets, r, b.r_offsets, b.matrix, b.gap_open,
                              b.gap_extend, bad, gpu_lib.sw_cigar_capacity(bad), ops, n_ops)
     assert e.value.code == gpu_lib.SW_ERANGE
+
+
+def _planted(rng, lengths, A):
+    """A planted copy of each query with substitutions and one indel away
+    from its ends, so that the located span is (about) the whole query."""
+    qs, rs = [], []
+    for L in lengths:
+        q = rng.integers(0, A, L).astype(np.uint8)
+        mut = q.copy()
+        if L > 24:
+            mid = np.arange(8, L - 8)
+            for pos in rng.choice(mid, size=max(1, L // 25), replace=False):
+                mut[pos] = (mut[pos] + 1) % A
+            mut = np.delete(mut, int(rng.integers(8, L - 8)))
+        r = np.concatenate([rng.integers(0, A, 13).astype(np.uint8), mut,
+                            rng.integers(0, A, 7).astype(np.uint8)])
+        qs.append(q)
+        rs.append(r)
+    return qs, rs
+
+
+def test_every_width_and_row_count(gpu_lib, ctx):
+    """Spans at and just past every fast-path size R x G (R = 10, 12, 14, 16
+    rows per lane, G = 1..32 lanes), so every (width, rows) class runs."""
+    sizes = sorted({R << lg for R in (10, 12, 14, 16) for lg in range(6)})
+    lengths = [L for s in sizes for L in (s - 1, s, s + 1) if 1 <= L <= 520]
+    qs, rs = _planted(np.random.default_rng(7), lengths, 4)
+    b = wl.make_batch("classes", qs, rs, wl.dna_matrix(), -6, -1)
+    res, got = gpu_cigars(gpu_lib, ctx, b)
+    assert np.array_equal(res, oracle.align_workload(b))
+    assert_same_cigars(b, res, got)
+
+
+@pytest.mark.parametrize("A", [20, 32])
+def test_large_alphabets(gpu_lib, ctx, A):
+    """BLOSUM62 (a 40 KB profile per block) and a 32-letter alphabet (64 KB:
+    the kernel's shared-memory limit raised for the launch)."""
+    rng = np.random.default_rng(100 + A)
+    if A == 20:
+        mat = np.asarray(wl.load_blosum62()[0], dtype=np.int8)
+        go, ge = -11, -1
+    else:
+        mat = rng.integers(-9, 10, size=(A, A)).astype(np.int8)
+        np.fill_diagonal(mat, 12)
+        go, ge = -10, -2
+    lengths = [int(x) for x in rng.integers(5, 400, size=120)]
+    qs, rs = _planted(rng, lengths, A)
+    b = wl.make_batch(f"alpha{A}", qs, rs, mat, go, ge)
+    res, got = gpu_cigars(gpu_lib, ctx, b)
+    assert np.array_equal(res, oracle.align_workload(b))
+    assert_same_cigars(b, res, got)
