@@ -60,6 +60,22 @@ def test_workloads(gpu_lib, ctx, k, n):
     assert_same_cigars(b, res, got)
 
 
+def test_large_batch_sampled(gpu_lib, ctx):
+    """A batch large enough that the host splits its preparation over worker
+    threads; every 23rd pair checked against the oracle op for op."""
+    b = wl.gen_config(1, n_pairs=40000)
+    res, got = gpu_cigars(gpu_lib, ctx, b)
+    ops, off, n_ops = got
+    idx = np.arange(0, b.n_pairs, 23)
+    assert np.array_equal(res[idx], oracle.align_workload(b, idx=idx))
+    eops, eoff, en = oracle.cigar_workload(b.subset(idx), res[idx])
+    for k, p in enumerate(idx):
+        assert n_ops[p] == en[k], f"pair {p}"
+        a = ops[off[p]:off[p] + n_ops[p]]
+        e = eops[eoff[k]:eoff[k] + en[k]]
+        assert np.array_equal(a, e), f"pair {p}"
+
+
 @pytest.mark.parametrize("go,ge", [(-1, -1), (0, 0), (-20, -3), (-16383, -1)])
 def test_gap_settings(gpu_lib, ctx, go, ge):
     base = wl.gen_config(1, n_pairs=300)
