@@ -15,19 +15,21 @@
 // state it emits D (E) or I (F) and returns to state H where the run
 // opened.  The same rule, on the same values, as the CPU oracle.
 //
-// Fast path (spans of at most 512 rows whose values fit int32 with room):
-// one lane group per pair, as in the batched kernel - lane t of a group of
-// G lanes owns rows 16 t .. 16 t + 15 of the whole span (one strip) in
-// registers and walks the columns on the anti-diagonal wavefront (lane t on
-// column k - t + 1 at step k), taking the row above from lane t - 1 by a
-// register shuffle.  Scores are int32 (the host checks the bound) and each
-// cell's four decisions come from DPX max-with-predicate instructions
-// (__vibmax_s32): E opened here, F opened here, E at least F, the diagonal
-// at least both gaps.  They are packed as a nibble per row, one 64-bit word
-// per lane and column, stored lane-major so that a group's stores of a step
-// are G words.  Then the group's first lane walks back, reading one word
-// per step while they are still in L2.  Pairs of a launch share a width G (the smallest power of
-// two with 16 G >= N), 32 / G pairs per warp, longest first.
+// Fast path (spans of at most 512 rows whose values fit int32 with room and
+// whose scores s - go fit a signed byte): one lane group per pair, as in the
+// batched kernel - lane t of a group of G lanes owns rows R t .. R t + R - 1
+// of the whole span (one strip) in registers, R = 10, 12, 14 or 16 chosen
+// per span with G (the smallest G R >= N), and walks the columns on the
+// anti-diagonal wavefront (lane t on column k - t + 1 at step k), taking the
+// row above from lane t - 1 by a register shuffle and its scores from a
+// per-lane profile in shared memory (one 16-byte load per step).  Scores are
+// int32 and each cell's four decisions come from DPX max-with-predicate
+// instructions (__vibmax_s32): E opened here, F opened here, E at least F,
+// the diagonal at least both gaps.  They are packed as a nibble per row, one
+// 64-bit word per lane and column, stored lane-major.  Then the whole group
+// walks back while the words are in L2, taking each run of the walk (up to
+// 16 cells per round) with one ballot.  All classes of (G, R) share one
+// launch, widest first, longest first within a class.
 //
 // General path (longer spans, or values beyond int32): one CTA of kThreads
 // threads per pair; thread t owns row s*kThreads + t of row strip s and
@@ -44,6 +46,9 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -186,6 +191,62 @@ __global__ void __launch_bounds__(kThreads) cigar_kernel(const __grid_constant__
     }
     p.n_ops[cp.id] = nr;
 }
+
+// Worker threads for the host preparation of large batches, started on
+// first use and kept (waking a parked thread costs far less than starting
+// one).  run(k, fn) calls fn(0) .. fn(k - 1), fn(0) on the calling thread,
+// and returns when all are done; one run at a time.
+class HostPool {
+  public:
+    static constexpr int kMax = 8;
+    static HostPool &get() {
+        static HostPool *pool = new HostPool();  // never destroyed: parked threads end with the process
+        return *pool;
+    }
+    void run(int k, const std::function<void(int)> &fn) {
+        std::lock_guard<std::mutex> one(run_mu_);
+        k = std::min(k, kMax);
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            while ((int)th_.size() < k - 1) {
+                const int id = (int)th_.size() + 1;
+                th_.emplace_back([this, id] { loop(id); });
+                th_.back().detach();
+            }
+            job_ = &fn;
+            want_ = k;
+            left_ = k - 1;
+            ++gen_;
+        }
+        cv_.notify_all();
+        fn(0);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [this] { return left_ == 0; });
+        job_ = nullptr;
+    }
+
+  private:
+    void loop(int id) {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_.wait(lk, [&] { return gen_ != seen; });
+            seen = gen_;
+            if (id >= want_) continue;
+            const std::function<void(int)> *fn = job_;
+            lk.unlock();
+            (*fn)(id);
+            lk.lock();
+            if (--left_ == 0) done_.notify_one();
+        }
+    }
+    std::mutex run_mu_, mu_;
+    std::condition_variable cv_, done_;
+    std::vector<std::thread> th_;
+    const std::function<void(int)> *job_ = nullptr;
+    uint64_t gen_ = 0;
+    int want_ = 0, left_ = 0;
+};
 
 // ---- fast path
 
@@ -610,11 +671,7 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
             fn(sh[0]);
             return;
         }
-        std::vector<std::thread> th;
-        th.reserve((size_t)n_thr - 1);
-        for (int t = 1; t < n_thr; ++t) th.emplace_back([&, t] { fn(sh[t]); });
-        fn(sh[0]);
-        for (std::thread &x : th) x.join();
+        HostPool::get().run(n_thr, [&](int t) { fn(sh[t]); });
     };
     run_shares([&](Share &w) {
         for (int64_t p = w.begin; p < w.end; ++p) {
