@@ -761,15 +761,38 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
             for (int64_t p = w.begin; p < w.end; ++p)
                 if (keyv[p] != kNoKey) ++w.hist[slot(keyv[p])];
         });
-        // stable counting sort: slot-major, then share, then pair order
+        // stable counting sort: slot-major, then share, then pair order.  A
+        // slot fixes the class and M, so its pairs' choice words (G M each)
+        // follow from its first position; the classes' ranges from the slots
+        std::vector<int64_t> slot_first(n_slots), slot_words(n_slots);
+        TbClassRange ranges[kTbClasses];
+        int n_ranges = 0;
+        int64_t blocks = 0, words = 0;
         {
             int64_t at = 0;
-            for (size_t k = 0; k < n_slots; ++k)
+            for (size_t k = 0; k < n_slots; ++k) {
+                const int cls = kTbClasses - 1 - (int)(k / span);
+                const int64_t wpp = ((int64_t)1 << (cls / kTbRowOpts)) * (mhi - (int64_t)(k % span));
+                slot_first[k] = at;
+                slot_words[k] = words;
+                const int64_t at0 = at;
                 for (Share &w : sh) {
                     const int32_t c = w.hist[k];
                     w.hist[k] = (int32_t)at;
                     at += c;
                 }
+                words += (at - at0) * wpp;
+                if (at > at0) {
+                    if (n_ranges == 0 || ranges[n_ranges - 1].cls != cls)
+                        ranges[n_ranges++] = {cls, (int32_t)at0, 0, 0};
+                    ranges[n_ranges - 1].count += (int32_t)(at - at0);
+                }
+            }
+            for (int c = 0; c < n_ranges; ++c) {
+                const int64_t per_block = 128 >> (ranges[c].cls / kTbRowOpts);
+                ranges[c].block0 = (int32_t)blocks;
+                blocks += (ranges[c].count + per_block - 1) / per_block;
+            }
         }
         const size_t rec_bytes = (size_t)n_fast * sizeof(TbPair);
         void *host = nullptr;
@@ -779,7 +802,9 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
             for (int64_t p = w.begin; p < w.end; ++p) {
                 const uint32_t k = keyv[p];
                 if (k == kNoKey) continue;
-                TbPair &tp = fast[w.hist[slot(k)]++];
+                const size_t sl = slot(k);
+                const int64_t pos = w.hist[sl]++;
+                TbPair &tp = fast[pos];
                 const int32_t qe = results[n + p], re = results[2 * n + p],
                               qs = results[3 * n + p], rs = results[4 * n + p];
                 tp.q = q_offsets[p] + qs;
@@ -789,13 +814,9 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
                 tp.M = re - rs + 1;
                 tp.id = (int32_t)p;
                 tp.cls = (int32_t)(k >> 16);
+                tp.ch = slot_words[sl] + (pos - slot_first[sl]) * ((int64_t)1 << (tp.cls / kTbRowOpts)) * tp.M;
             }
         });
-        int64_t words = 0;
-        for (int64_t a = 0; a < n_fast; ++a) {
-            fast[a].ch = words;
-            words += ((int64_t)1 << (fast[a].cls / kTbRowOpts)) * fast[a].M;
-        }
         void *ws = nullptr;
         const size_t pair_bytes = (rec_bytes + 255) & ~(size_t)255;
         if ((rc = ctx_alloc_async(ctx, pair_bytes + (size_t)words * 8, s, &ws)) != SW_OK) {
@@ -804,19 +825,6 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
         }
         TbPair *d_fast = static_cast<TbPair *>(ws);
         uint64_t *d_choice = reinterpret_cast<uint64_t *>(static_cast<unsigned char *>(ws) + pair_bytes);
-        // the ranges of the classes, read from the records before they are released
-        TbClassRange ranges[kTbClasses];
-        int n_ranges = 0;
-        int64_t blocks = 0;
-        for (int64_t a = 0; a < n_fast;) {
-            int64_t b = a;
-            while (b < n_fast && fast[b].cls == fast[a].cls) ++b;
-            const int cls = fast[a].cls;
-            const int64_t per_block = 128 >> (cls / kTbRowOpts);
-            ranges[n_ranges++] = {cls, (int32_t)a, (int32_t)(b - a), (int32_t)blocks};
-            blocks += (b - a + per_block - 1) / per_block;
-            a = b;
-        }
         if ((rc = ctx_pinned_commit(ctx, d_fast, rec_bytes, s)) != SW_OK) {
             cudaFreeAsync(ws, s);
             return rc;
