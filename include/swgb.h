@@ -519,14 +519,18 @@ int sw_unpack_2bit(const uint8_t *packed, int64_t n_res, uint8_t *codes, void *s
  * matrix, results and cigar_offsets on the HOST (read during the call).
  * Pair p's ops go to out_ops[cigar_offsets[p] ..], their count to
  * out_n_ops[p] (0 when the score is 0).  Asynchronous: the work is enqueued
- * on `stream` and the call returns.  Spans of at most 512 query residues
- * whose scores fit int32 with room take the fast path (a lane group per
- * span, four choice bits per cell, then a walk back per span); longer spans
- * the general one.  Scratch (half a byte per cell of the fast path's spans,
- * rounded to 16 rows; at most about 1 GiB per launch of the general path's
- * choice bytes) comes from the context's workspace pool, stream-ordered.
- * Errors: SW_EINVAL (bad arguments), SW_ERANGE (coordinates outside a pair,
- * or room below the pair's need), SW_ENOMEM, SW_ECUDA.
+ * on `stream` and the call returns (its host preparation, split over up to
+ * 8 worker threads for large batches, is done by then).  Spans of at most
+ * 512 query residues whose scores fit int32 with room and whose s - go fit a
+ * signed byte take the fast path (a lane group per span, 10 to 16 rows per
+ * lane, four choice bits per cell, then the group walks the span back);
+ * longer spans the general one.  Scratch (half a byte per cell of the fast
+ * path's spans, rounded up to its rows; at most about 1 GiB per launch of
+ * the general path's choice bytes) comes from the context's workspace pool,
+ * stream-ordered.
+ * Errors: SW_EINVAL (bad arguments), SW_ERANGE (offsets negative or
+ * decreasing, a length above SW_MAX_LEN, coordinates outside a pair, or room
+ * below the pair's need), SW_ENOMEM, SW_ECUDA.
  */
 int sw_cigar_capacity(const int32_t *results, int32_t n_pairs, int64_t *offsets);
 int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,

@@ -253,6 +253,16 @@ class HostPool {
 constexpr int kTbMaxRows = 512;  // 32 lanes x 16 rows: one strip per span
 constexpr int kTbRowOpts = 4;    // rows per lane: 10, 12, 14 or 16
 constexpr int32_t kTbNegInf = -(1 << 29);
+// Fast path, the adds of a cell: 0 = plain adds; 1 = E + ge, F + ge and
+// H_diag + s as multiply-adds by a one the compiler cannot see (FMA pipe);
+// 2 = also H + go.
+#ifndef SWGB_TB_FMA
+#define SWGB_TB_FMA 0
+#endif
+// Fast path, resident blocks per SM the fill kernel's registers are sized for.
+#ifndef SWGB_TB_MIN_BLOCKS
+#define SWGB_TB_MIN_BLOCKS 1
+#endif
 // Fast path, the choice nibbles: 1 = each decision ORs its bit in under its
 // predicate; 0 = a nibble assembled from the four flags, then shifted in
 // (measured on 100k DNA spans: 1 is 7 % faster end to end).
@@ -430,6 +440,7 @@ __device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &c
     if (has) tp = p.pairs[cr.first + pidx];
     const int N = has ? tp.N : 0, M = has ? tp.M : 0;
     const uint8_t *qa = p.q + tp.q, *rb = p.r + tp.r;
+    [[maybe_unused]] const int one = (int)(blockDim.x >> 7);  // 1: blocks have 128 threads
     {
         // this lane's profile: byte r of entry y is s(q[R gl + r], y) - go (the
         // host checks that it fits a signed byte); rows past the span take 0
@@ -498,10 +509,22 @@ __device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &c
                 asm("prmt.b32 %0, %1, 0, %2;" : "=r"(sx) : "r"(pws[r >> 2]), "r"(kSx[r & 3]));
                 const int sc = (int)sx;
                 bool eo, fo, ef, dm;
-                const int e = __vibmax_s32(X[r], E[r] + ge, &eo);  // E = max(H_left + go, E + ge)
-                const int f = __vibmax_s32(upX, upF + ge, &fo);    // F = max(H_up + go, F_up + ge)
+                int e_in, f_in, d_in;
+                if constexpr (SWGB_TB_FMA >= 1) {
+                    // the adds as multiply-adds by a one the compiler cannot
+                    // see, so that they issue on the FMA pipe
+                    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(e_in) : "r"(E[r]), "r"(one), "r"(ge));
+                    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(f_in) : "r"(upF), "r"(one), "r"(ge));
+                    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(d_in) : "r"(diag), "r"(one), "r"(sc));
+                } else {
+                    e_in = E[r] + ge;
+                    f_in = upF + ge;
+                    d_in = diag + sc;
+                }
+                const int e = __vibmax_s32(X[r], e_in, &eo);  // E = max(H_left + go, E + ge)
+                const int f = __vibmax_s32(upX, f_in, &fo);   // F = max(H_up + go, F_up + ge)
                 const int m1 = __vibmax_s32(e, f, &ef);
-                const int h = __vibmax_s32(diag + sc, m1, &dm);
+                const int h = __vibmax_s32(d_in, m1, &dm);
 #if SWGB_TB_PACK
                 // each decision sets its bit by a predicated or
                 uint32_t &wd = r < 8 ? lo : hi;
@@ -519,7 +542,10 @@ __device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &c
                     hi |= nib << (4 * (r - 8));
 #endif
                 diag = X[r];
-                X[r] = h + go;
+                if constexpr (SWGB_TB_FMA >= 2)
+                    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(X[r]) : "r"(h), "r"(one), "r"(go));
+                else
+                    X[r] = h + go;
                 E[r] = e;
                 upX = X[r];
                 upF = f;
@@ -538,7 +564,7 @@ __device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &c
 // Every fast-path pair of a call in one launch: each block finds its class
 // (lane-group width and rows per lane) in the range table and runs that
 // instantiation, so the classes share one grid and one tail.
-__global__ void __launch_bounds__(128) tb_fill_kernel(const __grid_constant__ TbParams p) {
+__global__ void __launch_bounds__(128, SWGB_TB_MIN_BLOCKS) tb_fill_kernel(const __grid_constant__ TbParams p) {
     extern __shared__ uint4 tb_prof[];                 // [code][thread]: R bytes of s - go
     __shared__ int smat[kMaxAlphabet * kMaxAlphabet];  // s - go
     const int A = p.A;
@@ -627,7 +653,8 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
         return set_error(SW_EINVAL, "sw_traceback: bad argument");
     if (n_pairs == 0) return SW_OK;
     std::string msg;
-    int rc = check_batch(q_offsets, r_offsets, n_pairs, score_matrix, alphabet_size, gap_open,
+    // scoring checks here; the offsets are checked pair by pair below
+    int rc = check_batch(q_offsets, r_offsets, 0, score_matrix, alphabet_size, gap_open,
                          gap_extend, nullptr, nullptr, nullptr, &msg);
     if (rc != SW_OK) return set_error(rc, ("sw_traceback: " + msg).c_str());
     const int64_t n = n_pairs;
@@ -653,10 +680,12 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
     keyv_store.resize((size_t)n);
     uint32_t *const keyv = keyv_store.data();  // (the worker threads have stores of their own)
     const int n_thr = (int)std::max<int64_t>(
-        1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(), n / 16384}));
+        1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(), n / 4096}));
     struct Share {
         int64_t begin = 0, end = 0, n_fast = 0, bad = -1;
-        int bad_kind = 0;  // 1: coordinates outside the pair, 2: too little op room
+        // 1: coordinates outside the pair, 2: too little op room, 3: offsets
+        // negative or decreasing, 4: a length above SW_MAX_LEN
+        int bad_kind = 0;
         int32_t mlo = INT32_MAX, mhi = 0;
         std::vector<CigarPair> general;
         std::vector<int32_t> hist;  // per key slot (second pass)
@@ -676,10 +705,19 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
     run_shares([&](Share &w) {
         for (int64_t p = w.begin; p < w.end; ++p) {
             keyv[p] = kNoKey;
+            const int64_t qn = q_offsets[p + 1] - q_offsets[p], rm = r_offsets[p + 1] - r_offsets[p];
+            if (q_offsets[p] < 0 || r_offsets[p] < 0 || qn < 0 || rm < 0 || qn > SW_MAX_LEN ||
+                rm > SW_MAX_LEN) {
+                w.bad = p;
+                w.bad_kind = (qn > SW_MAX_LEN || rm > SW_MAX_LEN) && qn >= 0 && rm >= 0 &&
+                                     q_offsets[p] >= 0 && r_offsets[p] >= 0
+                                 ? 4
+                                 : 3;
+                return;
+            }
             const int32_t S = results[p], qe = results[n + p], re = results[2 * n + p],
                           qs = results[3 * n + p], rs = results[4 * n + p];
             if (S <= 0) continue;
-            const int64_t qn = q_offsets[p + 1] - q_offsets[p], rm = r_offsets[p + 1] - r_offsets[p];
             if (qs < 0 || qs > qe || qe >= qn || rs < 0 || rs > re || re >= rm) {
                 w.bad = p;
                 w.bad_kind = 1;
@@ -715,7 +753,13 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
     for (const Share &w : sh) {
         if (w.bad >= 0) {
             const int64_t p = w.bad;
-            if (w.bad_kind == 1)
+            if (w.bad_kind == 3)
+                snprintf(buf, sizeof buf,
+                         "sw_traceback: offsets of pair %lld negative or decreasing", (long long)p);
+            else if (w.bad_kind == 4)
+                snprintf(buf, sizeof buf, "sw_traceback: pair %lld has a length above SW_MAX_LEN",
+                         (long long)p);
+            else if (w.bad_kind == 1)
                 snprintf(buf, sizeof buf, "sw_traceback: pair %lld has coordinates outside it",
                          (long long)p);
             else
