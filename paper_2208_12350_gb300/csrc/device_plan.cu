@@ -214,17 +214,24 @@ __global__ void __launch_bounds__(kThreads) dp_classify(const DevicePlanShape S,
     if (threadIdx.x < 2 && tot[threadIdx.x]) atomicAdd(&hdr->total[threadIdx.x], tot[threadIdx.x]);
 }
 
+// The long-pair cap of a route, in pair-cost units: cap_fraction times the
+// mean load of a bulk-width group (a cost above it takes wider groups).
+__device__ __forceinline__ uint64_t route_cap(const DevicePlanShape &S, const Header *hdr,
+                                              int route) {
+    const double groups = (double)S.n_warps[route] * (double)(32 >> S.bulk_log2g);
+    const double cap = S.cap_fraction * (double)hdr->total[route] / (groups > 1.0 ? groups : 1.0);
+    return cap >= 1.8e19 ? ~0ull : (uint64_t)cap;  // cost > cap <=> cost > floor(cap)
+}
+
 // The width class of a group-route pair (log2 of its lane count), or -1
 // when no group slot holds it (it then takes the plain kernel).
-__device__ __forceinline__ int choose_lg(const DevicePlanShape &S, const Header *hdr, int n, int m,
+__device__ __forceinline__ int choose_lg(const DevicePlanShape &S, uint64_t cap, int n, int m,
                                          int route) {
     const int rows = S.rows[route], gn = S.bulk_log2g;
-    const double groups = (double)S.n_warps[route] * (double)(32 >> gn);
-    const double cap = S.cap_fraction * (double)hdr->total[route] / (groups > 1.0 ? groups : 1.0);
     int lg = gn;
-    if ((double)pair_cost(n, m, gn, rows, S.strip_ov) > cap) {
+    if ((uint64_t)pair_cost(n, m, gn, rows, S.strip_ov) > cap) {
         for (lg = gn + 1; lg < 5; ++lg)
-            if ((double)pair_cost(n, m, lg, rows, S.strip_ov) <= cap) break;
+            if ((uint64_t)pair_cost(n, m, lg, rows, S.strip_ov) <= cap) break;
     }
     if (S.half_tails[route] && lg == gn && gn > kMinLog2G) {
         const int h = rows << gn;
@@ -263,23 +270,33 @@ __global__ void __launch_bounds__(kThreads) dp_keys(const DevicePlanShape S, con
     __shared__ uint32_t hist[kWarps][kDigits];
     __shared__ unsigned long long bwork[kNumBuckets];
     __shared__ int32_t bcount[kNumBuckets];
+    __shared__ uint64_t cap[2];  // the routes' long-pair caps, computed once per block
     if (threadIdx.x < kNumBuckets) {
         bwork[threadIdx.x] = 0;
         bcount[threadIdx.x] = 0;
     }
+    if (threadIdx.x < 2) cap[threadIdx.x] = route_cap(S, hdr, threadIdx.x);
     __syncthreads();
     const int lo = blockIdx.x * kTile, hi = min(S.n_pairs, lo + kTile);
+    // per-thread bucket counts and work in registers (a select per bucket,
+    // no shared-memory atomics per pair), reduced per warp after the loop
+    uint32_t my_count[kNumBuckets];
+    unsigned long long my_work[kNumBuckets];
+#pragma unroll
+    for (int b = 0; b < kNumBuckets; ++b) my_count[b] = 0, my_work[b] = 0;
     for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
         bool bad = false;
         const PairView v = view_pair(S, off, i, &bad);
         int bucket = kBucketNone;
         uint32_t cost = 0;
         if (v.route < 2) {
-            const int lg = choose_lg(S, hdr, v.n, v.m, v.route);
+            const int lg = choose_lg(S, cap[v.route], v.n, v.m, v.route);
             if (lg >= 0) {
                 bucket = bucket_of(v.route, lg);
                 cost = pair_cost(v.n, v.m, lg, S.rows[v.route], S.strip_ov);
-                atomicAdd(&bwork[bucket], (unsigned long long)cost << lg);
+                const unsigned long long w = (unsigned long long)cost << lg;
+#pragma unroll
+                for (int b = 0; b < kNumBuckets; ++b) my_work[b] += b == bucket ? w : 0ull;
             } else {
                 bucket = v.n <= kPlainShortMaxN ? kBucketPlainShort : kBucketPlainLong;
             }
@@ -290,8 +307,22 @@ __global__ void __launch_bounds__(kThreads) dp_keys(const DevicePlanShape S, con
             const uint64_t c = (uint64_t)v.n * (uint64_t)v.m;
             cost = c > 0xffffffffull ? 0xffffffffu : (uint32_t)c;
         }
-        atomicAdd(&bcount[bucket], 1);
+#pragma unroll
+        for (int b = 0; b < kNumBuckets; ++b) my_count[b] += b == bucket ? 1u : 0u;
         keys0[i] = (uint16_t)((bucket << 12) | (4095u - log_level(cost)));
+    }
+#pragma unroll
+    for (int b = 0; b < kNumBuckets; ++b) {
+        uint32_t c = my_count[b];
+        unsigned long long w = my_work[b];
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (c) atomicAdd(&bcount[b], (int32_t)c);
+            if (w) atomicAdd(&bwork[b], w);
+        }
     }
     __syncthreads();
     if (threadIdx.x < kNumBuckets) {

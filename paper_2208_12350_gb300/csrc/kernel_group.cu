@@ -525,6 +525,13 @@ __global__ void __launch_bounds__(kGroupWarps * 32, (PK && R > 16) ? 2 : kGroupM
     cold.rend = cw + 8 * NT;
     cold.best_row = cw + 9 * NT;
     cold.best_key = reinterpret_cast<uint32_t *>(cw + 10 * NT);
+    {
+        // a launch whose queues are all empty (a route of a device-planned
+        // batch with no pairs on it) ends before any setup
+        int queued = 0;
+        for (int c = 0; c < p.n_classes; ++c) queued += p.classes[c].count;
+        if (queued == 0) return;
+    }
     for (int i = t; i < A * (A + 1); i += blockDim.x) {
         const int x = i / (A + 1), c = i - x * (A + 1);
         if (c == A) {
