@@ -239,11 +239,13 @@ def run_reference(args, rank):
 
 # ------------------------------------------------------------ ncu traffic
 
-def profiled_traffic(batch, tune, arith="s16x2", flags=0, sms=152) -> int | None:
-    """DRAM bytes per launch of the group kernel from the committed ncu
-    summary, if that capture was of this workload, this arithmetic, this
-    kernel source and a plan with the same lane-group widths per pair (else
-    None: the counters are stale)."""
+def profiled_traffic(batch, tune, arith="s16x2", flags=0, sms=152) -> tuple[int | None, bool]:
+    """(DRAM bytes per launch of the group kernel from the committed ncu
+    summary, whether the captured plan put the same number of pairs on each
+    lane-group width as this run's tuning).  The bytes are None unless that
+    capture was of this workload, this arithmetic and this kernel source (the
+    counters are stale otherwise); a plan with other widths (the autotuner's
+    choice can differ between boxes) keeps the figure and says so."""
     import hashlib
     import re
     form = "" if arith == "s16x2" else "s32_"
@@ -251,26 +253,26 @@ def profiled_traffic(batch, tune, arith="s16x2", flags=0, sms=152) -> int | None
     src = os.path.join(ROOT, "paper_2208_12350_gb300", "csrc", "kernel_group.cu")
     import paper_2208_12350_gb300 as swgb
     # captures are of the default plan (starts and ends, one byte per residue)
-    if not os.path.exists(path) or tune is None or flags & ~swgb.SW_PLAN_NO_S16X2:
-        return None
+    if not os.path.exists(path) or flags & ~swgb.SW_PLAN_NO_S16X2:
+        return None, False
+    if tune is None:  # not autotuned: the planner's own choice
+        tune = {"narrow_log2g": -1, "cap_fraction": 0.5}
     text = open(path).read()
     sha = re.search(r"kernel_sha256: ([0-9a-f]{64})", text)
     wid = re.search(r"widths: ([0-9,]+)", text)
     byt = re.search(r"dram_bytes_per_launch: (\d+)", text)
     if not (sha and wid and byt):
-        return None
+        return None, False
     if sha.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
-        return None
+        return None, False
     ar = re.search(r"arith: (\w+)", text)
     if (ar.group(1) if ar else "s32") != arith:
-        return None
+        return None, False
     _, lg, _ = swgb.sw_plan_preview(batch.q_offsets, batch.r_offsets, batch.matrix,
                                     batch.gap_open, batch.gap_extend, swgb.SW_MODE_BATCHED, flags,
                                     sms, tune["narrow_log2g"], tune["cap_fraction"])
     hist = np.bincount(lg[lg >= 0], minlength=6)[:6].tolist() + [int(np.sum(lg < 0))]
-    if hist != [int(x) for x in wid.group(1).split(",")]:
-        return None
-    return int(byt.group(1))
+    return int(byt.group(1)), hist == [int(x) for x in wid.group(1).split(",")]
 
 
 # ------------------------------------------------------------------- serving
@@ -637,8 +639,8 @@ def run_ours(args, rank, world, local):
     sm_mhz = clk.get("sm_mhz")
     mb_rate, _ = swgb.sw_microbench_int(peak_op, local, 2048)
     peak_measured = mb_rate / 1e12
-    traffic = profiled_traffic(batch, tune, info["arith"], flags, sms) \
-        if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] else None
+    traffic, traffic_same_plan = profiled_traffic(batch, tune, info["arith"], flags, sms) \
+        if batch.n_pairs == wl.CONFIGS[args.config]["n_pairs"] else (None, False)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_measured, "unit": "Tops/s",
             "frac": achieved / peak_measured if peak_measured else None, "traffic": traffic,
             **roofline_fracs(ops_per_cell, 2 if packed16 else 4, cells + rcells, per_launch,
@@ -646,6 +648,7 @@ def run_ours(args, rank, world, local):
             "peak_kind": f"measured __{peak_op} issue rate, whole device, this run",
             "ops_per_cell": ops_per_cell, "cells_forward": cells, "cells_reverse": rcells,
             "traffic_unit": "DRAM bytes per launch (ncu, committed summary)",
+            "traffic_same_plan": traffic_same_plan,
             "algorithmic_bytes": int(batch.q_seqs.nbytes + batch.r_seqs.nbytes + 20 * batch.n_pairs)}
 
     # --- plain one-block-per-pair comparator
