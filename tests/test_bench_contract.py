@@ -94,9 +94,13 @@ def test_roofline_traffic_only_for_the_captured_kernel(bench_mod):
         assert bench_mod.profiled_traffic(b, None, "s16x2", 0, 152) == (want, True)
     else:
         assert got is None  # the kernel changed since the capture: stale counters
-    # another arithmetic, other plan flags: no traffic
-    assert bench_mod.profiled_traffic(b, {"narrow_log2g": -1, "cap_fraction": 0.5},
-                                      "s32", 0, 152)[0] is None
+    # another arithmetic reads its own capture (never the packed form's)
+    s32 = open(os.path.join(ROOT, "profiles", "sw_group_kernel_s32_dna-100k.md")).read()
+    s32_bytes = int(re.search(r"dram_bytes_per_launch: (\d+)", s32).group(1))
+    s32_sha = re.search(r"kernel_sha256: ([0-9a-f]{64})", s32).group(1)
+    assert bench_mod.profiled_traffic(b, {"narrow_log2g": -1, "cap_fraction": 0.5}, "s32", 0,
+                                      152)[0] == (s32_bytes if s32_sha == sha_now else None)
+    # other plan flags: no traffic
     assert bench_mod.profiled_traffic(b, {"narrow_log2g": -1, "cap_fraction": 0.5}, "s16x2",
                                       swgb.SW_PLAN_ENDS_ONLY, 152)[0] is None
 
