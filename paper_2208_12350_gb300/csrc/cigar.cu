@@ -26,7 +26,8 @@
 // int32 and each cell's four decisions come from DPX max-with-predicate
 // instructions (__vibmax_s32): E opened here, F opened here, E at least F,
 // the diagonal at least both gaps.  They are packed as a nibble per row, one
-// 64-bit word per lane and column, stored lane-major.  Then the whole group
+// 64-bit word per lane and column, stored by wavefront step (a group's
+// stores of a step are contiguous).  Then the whole group
 // walks back while the words are in L2, taking each run of the walk (up to
 // 16 cells per round) with one ballot.  All classes of (G, R) share one
 // launch, widest first, longest first within a class.
@@ -273,7 +274,7 @@ __host__ __device__ constexpr int tb_rows(int ri) { return 10 + 2 * ri; }
 
 struct TbPair {
     int64_t q, r;   // offsets of the spans' first residues
-    int64_t ch;     // offset (64-bit words) of its choice words: G x M of them
+    int64_t ch;     // offset (64-bit words) of its choice words: G x (M + G - 1) of them
     int64_t out;    // offset of its ops in the output
     int32_t N, M, id, cls;  // cls = log2(G) * kTbRowOpts + rows option
 };
@@ -320,7 +321,7 @@ __device__ __forceinline__ void tb_walk_group(const TbParams &p, const TbPair &t
     const bool lin = p.go == p.ge;
     auto cell = [&](int ii, int jj) -> uint32_t {  // 1 <= ii <= N, 1 <= jj <= M
         const int l = (ii - 1) / R, r = ii - 1 - l * R;
-        return (uint32_t)(ch[(int64_t)l * M + (jj - 1)] >> (4 * r)) & 15u;
+        return (uint32_t)(ch[(int64_t)(jj - 1 + l) * G + l] >> (4 * r)) & 15u;
     };
     int nr = 0, run_op = -1, run_len = 0;
     auto push = [&](int op, int len) {
@@ -473,7 +474,9 @@ __device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &c
     // the lane below takes as the diagonal of its first column.
     int diag0 = go;
     int outX = X[R - 1], outF = kTbNegInf;
-    uint64_t *ch = p.choice + tp.ch + (int64_t)gl * M;
+    // choice words by step: lane l's word for column j sits at step j - 1 + l,
+    // so the G words a group stores at a step are contiguous
+    uint64_t *ch = p.choice + tp.ch + gl;
     // the warp runs until its longest pair is done (pairs sorted longest first)
     int steps = has ? M + G - 1 : 0;
     for (int off = 16; off > 0; off >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, off));
@@ -550,7 +553,7 @@ __device__ __forceinline__ void tb_fill(const TbParams &p, const TbClassRange &c
                 upX = X[r];
                 upF = f;
             }
-            ch[j - 1] = ((uint64_t)hi << 32) | lo;
+            ch[(int64_t)k * G] = ((uint64_t)hi << 32) | lo;
             outX = upX;
             outF = upF;
         }
@@ -816,7 +819,8 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
             int64_t at = 0;
             for (size_t k = 0; k < n_slots; ++k) {
                 const int cls = kTbClasses - 1 - (int)(k / span);
-                const int64_t wpp = ((int64_t)1 << (cls / kTbRowOpts)) * (mhi - (int64_t)(k % span));
+                const int64_t G = (int64_t)1 << (cls / kTbRowOpts);
+                const int64_t wpp = G * (mhi - (int64_t)(k % span) + G - 1);
                 slot_first[k] = at;
                 slot_words[k] = words;
                 const int64_t at0 = at;
@@ -858,7 +862,8 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
                 tp.M = re - rs + 1;
                 tp.id = (int32_t)p;
                 tp.cls = (int32_t)(k >> 16);
-                tp.ch = slot_words[sl] + (pos - slot_first[sl]) * ((int64_t)1 << (tp.cls / kTbRowOpts)) * tp.M;
+                const int64_t G = (int64_t)1 << (tp.cls / kTbRowOpts);
+                tp.ch = slot_words[sl] + (pos - slot_first[sl]) * G * (tp.M + G - 1);
             }
         });
         void *ws = nullptr;
