@@ -197,9 +197,12 @@ __global__ void __launch_bounds__(kThreads) cigar_kernel(const __grid_constant__
 // first use and kept (waking a parked thread costs far less than starting
 // one).  run(k, fn) calls fn(0) .. fn(k - 1), fn(0) on the calling thread,
 // and returns when all are done; one run at a time.
+#ifndef SWGB_TB_HOST_THREADS
+#define SWGB_TB_HOST_THREADS 8
+#endif
 class HostPool {
   public:
-    static constexpr int kMax = 8;
+    static constexpr int kMax = SWGB_TB_HOST_THREADS;
     static HostPool &get() {
         static HostPool *pool = new HostPool();  // never destroyed: parked threads end with the process
         return *pool;
@@ -683,7 +686,8 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
     keyv_store.resize((size_t)n);
     uint32_t *const keyv = keyv_store.data();  // (the worker threads have stores of their own)
     const int n_thr = (int)std::max<int64_t>(
-        1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(), n / 4096}));
+        1, std::min<int64_t>({HostPool::kMax, (int64_t)std::thread::hardware_concurrency(),
+                              n / 4096}));
     struct Share {
         int64_t begin = 0, end = 0, n_fast = 0, bad = -1;
         // 1: coordinates outside the pair, 2: too little op room, 3: offsets
