@@ -313,9 +313,16 @@ def serve_sweep(swgb, ctx, pools, expect, args, resident: bool) -> dict:
         return swgb.sw_server_submit(srv, b.q_seqs, b.q_offsets, b.r_seqs, b.r_offsets, b.matrix,
                                      b.gap_open, b.gap_extend, timeout_ms=120000)
 
-    for rq in reqs[:16]:  # warm-up, one at a time
+    # warm-up: one at a time, then a burst that puts work on every stream slot
+    # (their first launches allocate staging and workspace)
+    for rq in reqs[:16]:
         out = swgb.sw_server_wait(srv, submit(rq), rq.batch.n_pairs, timeout_ms=120000)
         identical &= check(rq, out)
+    for _ in range(2):
+        burst = [(rq, submit(rq)) for rq in reqs[:64]]
+        for rq, rid in burst:
+            identical &= check(rq, swgb.sw_server_wait(srv, rid, rq.batch.n_pairs,
+                                                       timeout_ms=120000))
     points = []
     n_sub = max(1, args.serve_clients)
     rate = args.serve_rate0

@@ -263,6 +263,11 @@ constexpr int32_t kTbNegInf = -(1 << 29);
 #ifndef SWGB_TB_FMA
 #define SWGB_TB_FMA 0
 #endif
+// Fast path, cells of the current run the walk examines per round (at least;
+// G when the group is wider).
+#ifndef SWGB_TB_LOOKAHEAD
+#define SWGB_TB_LOOKAHEAD 16
+#endif
 // Fast path, resident blocks per SM the fill kernel's registers are sized for.
 #ifndef SWGB_TB_MIN_BLOCKS
 #define SWGB_TB_MIN_BLOCKS 1
@@ -313,7 +318,7 @@ struct TbParams {
 template <int LOG2G, int R>
 __device__ __forceinline__ void tb_walk_group(const TbParams &p, const TbPair &tp, int gl) {
     constexpr int G = 1 << LOG2G;
-    constexpr int L = G >= 16 ? 1 : 16 / G;  // cells per lane and round
+    constexpr int L = G >= SWGB_TB_LOOKAHEAD ? 1 : SWGB_TB_LOOKAHEAD / G;  // cells per lane and round
     constexpr int T = G * L;                 // cells per round
     const int lane = threadIdx.x & 31;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
