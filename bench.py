@@ -454,11 +454,13 @@ def roofline_fracs(ops_per_cell: int, max_ops_per_cell: int, cells_total: int, s
             "peak_nominal": nom, "max_ops_per_cell": max_ops_per_cell}
 
 
-def time_one_shot(swgb, torch, batch, dev, stream, steps, warmup):
+def time_one_shot(swgb, torch, batch, dev, stream, steps, warmup, in_place=False):
     """End to end through sw_align_batch: every step copies the sequences and
-    offsets from page-locked host buffers to the device, plans on the device
-    (no offset read-back, no host planning), runs both passes and copies the
-    five result rows back; host-timed, synchronised at the end of each step."""
+    offsets from page-locked host buffers to the device (in_place: passes the
+    page-locked buffers themselves, which the kernels read over the coherent
+    host link), plans on the device (no offset read-back, no host planning),
+    runs both passes and copies the five result rows back; host-timed,
+    synchronised at the end of each step."""
     qh = torch.from_numpy(batch.q_seqs).pin_memory()
     rh = torch.from_numpy(batch.r_seqs).pin_memory()
     qoh = torch.from_numpy(batch.q_offsets).pin_memory()
@@ -472,12 +474,16 @@ def time_one_shot(swgb, torch, batch, dev, stream, steps, warmup):
 
     def step():
         with torch.cuda.stream(stream):
-            q.copy_(qh, non_blocking=True)
-            r.copy_(rh, non_blocking=True)
-            qo.copy_(qoh, non_blocking=True)
-            ro.copy_(roh, non_blocking=True)
-            swgb.sw_align_batch(q, qo, r, ro, batch.matrix, batch.gap_open, batch.gap_extend,
-                                out, stream)
+            if in_place:
+                swgb.sw_align_batch(qh, qoh, rh, roh, batch.matrix, batch.gap_open,
+                                    batch.gap_extend, out, stream)
+            else:
+                q.copy_(qh, non_blocking=True)
+                r.copy_(rh, non_blocking=True)
+                qo.copy_(qoh, non_blocking=True)
+                ro.copy_(roh, non_blocking=True)
+                swgb.sw_align_batch(q, qo, r, ro, batch.matrix, batch.gap_open,
+                                    batch.gap_extend, out, stream)
             oh.copy_(out, non_blocking=True)
         stream.synchronize()
 
@@ -714,6 +720,17 @@ def run_ours(args, rank, world, local):
                        "identical_outputs": bool(np.array_equal(ores, res)),
                        "call": "sw_align_batch (device offsets; planned on the device)",
                        "inputs": "page-locked host buffers copied to the device each step"}
+        if swgb.sw_ctx_host_in_place(ctx):
+            it, ires, ih2d, id2h, istats = time_one_shot(swgb, torch, batch, dev, stream,
+                                                         args.steps, args.warmup, in_place=True)
+            e2e_oneshot["in_place"] = {
+                "value": job_cells * args.steps / it / 1e9, "unit": "GCUPS",
+                "ms_per_step": it / args.steps * 1e3, "step_ms": istats,
+                "h2d_bytes_per_step": ih2d, "d2h_bytes_per_step": id2h,
+                "identical_outputs": bool(np.array_equal(ires, res)),
+                "inputs": ("the page-locked host buffers themselves (sequences and "
+                           "offsets), read by the planner and the kernels over the "
+                           "coherent host link")}
 
     cigar = None
     if not args.no_cigar and not args.ends_only and world == 1:

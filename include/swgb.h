@@ -319,6 +319,10 @@ int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64_t *r_offse
  * One-shot alignment of a batch whose sequences AND offsets are on the
  * DEVICE (score_matrix on the HOST): the forward and reverse passes of
  * every pair, as ADEPT's batch call (Section III-B), planned on the device.
+ * Where the device reads host memory coherently (sw_ctx_host_in_place: a
+ * GB300's host link), the sequences and offsets may instead be page-locked
+ * host buffers (cudaMallocHost / cudaHostRegister), read in place by the
+ * kernels; the outputs stay device memory.
  *
  * Asynchronous: the call checks its arguments, enqueues everything on
  * `stream` and returns SW_OK without waiting for the device or reading

@@ -573,6 +573,17 @@ int sw_align_batch_ex(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offse
         return fail(SW_EINVAL, "sw_align_batch_ex: unknown mode %d", mode);
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(SW_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
+    if (ctx->host_in_place) {
+        // page-locked host inputs are read in place (their device view)
+        auto view = [&](const void *h) -> const void * {
+            const uint8_t *d = host_view(ctx, static_cast<const uint8_t *>(h));
+            return d ? static_cast<const void *>(d) : h;
+        };
+        q_seqs = static_cast<const uint8_t *>(view(q_seqs));
+        r_seqs = static_cast<const uint8_t *>(view(r_seqs));
+        q_offsets = static_cast<const int64_t *>(view(q_offsets));
+        r_offsets = static_cast<const int64_t *>(view(r_offsets));
+    }
     reap_retired(ctx, false);
     DevicePlanShape shape;
     std::string msg;

@@ -209,3 +209,28 @@ def test_overlapping_calls_on_two_streams(gpu_lib, ctx):
     assert_same(o1.T.cpu().numpy(), oracle.align_workload(b1), "stream 1")
     assert_same(o2.T.cpu().numpy(), oracle.align_workload(b2), "stream 2")
     assert gpu_lib.sw_ctx_status(ctx) == 0
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_page_locked_host_inputs_read_in_place(gpu_lib, ctx, k):
+    """Where the device reads host memory coherently, the call takes the
+    page-locked host buffers of the sequences and offsets themselves."""
+    import torch
+    swgb = gpu_lib
+    if not swgb.sw_ctx_host_in_place(ctx):
+        pytest.skip("this device does not read page-locked host memory in place")
+    b = wl.gen_config(k, n_pairs=20000)
+    swgb.sw_ctx_status(ctx)  # (read and cleared: earlier tests set bits on purpose)
+    qh = torch.from_numpy(b.q_seqs).pin_memory()
+    rh = torch.from_numpy(b.r_seqs).pin_memory()
+    qoh = torch.from_numpy(b.q_offsets).pin_memory()
+    roh = torch.from_numpy(b.r_offsets).pin_memory()
+    out = torch.full((5, b.n_pairs), -9, dtype=torch.int32, device="cuda")
+    swgb.sw_align_batch_ex(ctx, qh, qoh, rh, roh, b.matrix, b.gap_open, b.gap_extend,
+                           swgb.SW_MODE_AUTO, out)
+    torch.cuda.synchronize()
+    got = out.T.contiguous().cpu().numpy()
+    assert np.array_equal(got, one_shot(swgb, b, ctx=ctx))
+    idx = np.arange(0, b.n_pairs, 11)
+    assert np.array_equal(got[idx], oracle.align_workload(b, idx=idx))
+    assert swgb.sw_ctx_status(ctx) == 0
