@@ -326,6 +326,11 @@ def serve_sweep(swgb, ctx, pools, expect, args, resident: bool) -> dict:
     points = []
     n_sub = max(1, args.serve_clients)
     rate = args.serve_rate0
+    # the client side must not pause: collect once, then no cyclic GC during
+    # the sweep (the earlier legs leave a large heap behind)
+    import gc
+    gc.collect()
+    gc.disable()
     try:
         for _ in range(args.serve_points):
             n = min(len(reqs), max(200, int(rate * 20.0)))
@@ -384,6 +389,7 @@ def serve_sweep(swgb, ctx, pools, expect, args, resident: bool) -> dict:
             rate *= 1.5
         st = swgb.sw_server_stats(srv)
     finally:
+        gc.enable()
         swgb.sw_server_destroy(srv)
     kept = [p for p in points if p["served_rps"] >= 0.9 * p["offered_rps"]
             and p["p99_ms"] <= 1000.0]
