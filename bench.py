@@ -740,32 +740,60 @@ def run_ours(args, rank, world, local):
 
     cigar = None
     if not args.no_cigar and not args.ends_only and world == 1:
-        # traceback of every aligned pair: cells = the spans' global DP
+        # traceback of every aligned pair: cells = the spans' global DP.  The
+        # headline call takes the results where the alignment left them, on
+        # the device (sw_traceback_device: spans classified by kernels); the
+        # host-prepared call (sw_traceback, results on the host) beside it.
         res5 = np.ascontiguousarray(res.T)
         coff = swgb.sw_cigar_capacity(res5)
+        res5_d = torch.from_numpy(res5).to(dev)
+        qo_d = torch.from_numpy(np.ascontiguousarray(batch.q_offsets, dtype=np.int64)).to(dev)
+        ro_d = torch.from_numpy(np.ascontiguousarray(batch.r_offsets, dtype=np.int64)).to(dev)
+        coff_d = torch.empty(batch.n_pairs + 1, dtype=torch.int64, device=dev)
+        swgb.sw_cigar_capacity_device(res5_d, coff_d, stream)
+        stream.synchronize()
+        same_offsets = bool(np.array_equal(coff_d.cpu().numpy(), coff))
         ops = torch.zeros(max(1, int(coff[-1])), dtype=torch.int32, device=dev)
         nops = torch.zeros(batch.n_pairs, dtype=torch.int32, device=dev)
         ok = res[:, 0] > 0
         span_cells = int(np.sum((res[ok, 1] - res[ok, 3] + 1).astype(np.int64) *
                                 (res[ok, 2] - res[ok, 4] + 1)))
-        swgb.sw_traceback(ctx, q8, batch.q_offsets, r8, batch.r_offsets, batch.matrix,
-                          batch.gap_open, batch.gap_extend, res5, coff, ops, nops, stream)
-        torch.cuda.synchronize()
-        reps = 3
-        dev_ms, host_ms = [], []
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            th = time.perf_counter()
+
+        def tb_device():
+            swgb.sw_traceback_device(ctx, q8, qo_d, r8, ro_d, batch.matrix, batch.gap_open,
+                                     batch.gap_extend, res5_d, coff_d, ops, nops, stream)
+
+        def tb_host():
             swgb.sw_traceback(ctx, q8, batch.q_offsets, r8, batch.r_offsets, batch.matrix,
                               batch.gap_open, batch.gap_extend, res5, coff, ops, nops, stream)
-            host_ms.append((time.perf_counter() - th) * 1e3)
-            e1.record(stream)
-            stream.synchronize()
-            dev_ms.append(e0.elapsed_time(e1))
-        dt = (time.perf_counter() - t0) / reps
+
+        def time_calls(call, reps=3):
+            call()
+            torch.cuda.synchronize()
+            dev_ms, host_ms = [], []
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                th = time.perf_counter()
+                call()
+                host_ms.append((time.perf_counter() - th) * 1e3)
+                e1.record(stream)
+                stream.synchronize()
+                dev_ms.append(e0.elapsed_time(e1))
+            dt = (time.perf_counter() - t0) / reps
+            return {"value": span_cells / dt / 1e9, "unit": "GCUPS (span cells)",
+                    "ms": dt * 1e3, "device_ms": statistics.median(dev_ms),
+                    "call_host_ms": statistics.median(host_ms),
+                    "device_value": span_cells / (statistics.median(dev_ms) * 1e-3) / 1e9}
+
+        host_leg = time_calls(tb_host)
+        host_ops = ops.cpu().numpy().view(np.uint32).copy()
+        host_nops = nops.cpu().numpy().copy()
+        ops.zero_()
+        nops.zero_()
+        dev_leg = time_calls(tb_device)
         # the CIGARs of a sample of pairs against the CPU oracle's
         import oracle
         idx = np.flatnonzero(ok)[::97]
@@ -776,17 +804,21 @@ def run_ours(args, rank, world, local):
         same = all(int(got_n[p]) == int(en[k]) and np.array_equal(
             got_ops[coff[p]:coff[p] + got_n[p]], eops[eoff[k]:eoff[k] + en[k]])
             for k, p in enumerate(idx))
-        cigar = {"value": span_cells / dt / 1e9, "unit": "GCUPS (span cells)", "ms": dt * 1e3,
-                 "device_ms": statistics.median(dev_ms),
-                 "call_host_ms": statistics.median(host_ms),
-                 "device_value": span_cells / (statistics.median(dev_ms) * 1e-3) / 1e9,
-                 "span_cells": span_cells, "pairs": int(ok.sum()),
-                 "ops": int(nops.sum().item()), "oracle_identical_sample": bool(same),
-                 "sample": f"{len(idx)} aligned pairs (every 97th) against the CPU oracle",
-                 "note": "value: host-timed call + stream synchronisation (host preparation of "
-                         "the span list included); device_value: CUDA events around the call on "
-                         "its stream (the GPU idles while the call prepares: call_host_ms is the "
-                         "call's own host time); scratch from the context's pool"}
+        host_leg["identical_to_device_call"] = bool(
+            np.array_equal(host_nops, got_n) and np.array_equal(host_ops, got_ops))
+        host_leg["call"] = ("sw_traceback: results and offsets on the host, spans classified "
+                            "by host threads inside the call (the GPU idles meanwhile)")
+        cigar = dict(dev_leg)
+        cigar.update({
+            "span_cells": span_cells, "pairs": int(ok.sum()), "ops": int(nops.sum().item()),
+            "oracle_identical_sample": bool(same), "device_offsets_identical": same_offsets,
+            "sample": f"{len(idx)} aligned pairs (every 97th) against the CPU oracle",
+            "call": "sw_traceback_device: results, offsets and cigar offsets on the device",
+            "host_inputs": host_leg,
+            "note": "value: host-timed call + stream synchronisation, 3 calls after one "
+                    "untimed; the device call waits for its three classification kernels and "
+                    "reads back a summary before it enqueues the fill and walk; device_value: "
+                    "CUDA events around the call on its stream; scratch from the context's pool"})
 
     overridden = bool(args.gaps or args.dna_scores or args.ends_only or args.pairs or args.packed)
     configs = None

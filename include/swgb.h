@@ -544,6 +544,39 @@ int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
                  uint32_t *out_ops, int32_t *out_n_ops, void *stream);
 
 /*
+ * Traceback of a batch whose results are already on the device (Fig. 2(c),
+ * the same alignments, ops and rule as sw_traceback), with the span
+ * classification done by kernels instead of host threads.
+ *
+ * sw_cigar_capacity_device: results (5 x n_pairs int32 rows, as the
+ * alignment calls write them) and offsets[0..n_pairs] on the DEVICE; writes
+ * the same offsets as sw_cigar_capacity, offsets[n_pairs] the total.
+ * Asynchronous on `stream`.  Errors: SW_EINVAL, SW_ECUDA.
+ *
+ * sw_traceback_device: q_seqs, q_offsets, r_seqs, r_offsets, results,
+ * cigar_offsets, out_ops and out_n_ops on the DEVICE; score_matrix on the
+ * host.  Three kernels classify the spans (fast or general path, lane-group
+ * class, span length), sort the fast-path records by class and length and
+ * lay out their choice words; the call then waits for them (and so for the
+ * work queued on `stream` before it), reads back a summary of under 1 KB
+ * (and the general-path records, when there are any), and enqueues the
+ * fill and walk kernels, which run asynchronously.  Scratch as for
+ * sw_traceback, from the context's pool, stream-ordered.  Offsets and
+ * results are checked on the device: SW_ERANGE names the smallest bad pair
+ * (offsets negative or decreasing, a length above SW_MAX_LEN, coordinates
+ * outside the pair, or room below its need) and then nothing is enqueued
+ * beyond the cleared out_n_ops.  Other errors: SW_EINVAL, SW_ENOMEM,
+ * SW_ECUDA.
+ */
+int sw_cigar_capacity_device(const int32_t *results, int32_t n_pairs, int64_t *offsets,
+                             void *stream);
+int sw_traceback_device(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
+                        const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                        const int8_t *score_matrix, int32_t alphabet_size, int32_t gap_open,
+                        int32_t gap_extend, const int32_t *results, const int64_t *cigar_offsets,
+                        uint32_t *out_ops, int32_t *out_n_ops, void *stream);
+
+/*
  * Integer issue-rate microbenchmark on `device` (made current for the call;
  * synchronous).  op: 0 = 32-bit add, 1 = 32-bit max, 2 = __viaddmax_s32
  * (add then max), 3 = __vimax3_s32_relu, 4 = __viaddmax_s16x2,

@@ -93,6 +93,9 @@ SIGNATURES = {
     "sw_cigar_capacity": ([_P, _I32, _P], ctypes.c_int),
     "sw_traceback": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P],
                      ctypes.c_int),
+    "sw_cigar_capacity_device": ([_P, _I32, _P, _P], ctypes.c_int),
+    "sw_traceback_device": ([_P, _P, _P, _P, _P, _I32, _P, _I32, _I32, _I32, _P, _P, _P, _P, _P],
+                            ctypes.c_int),
     "sw_microbench_int": ([_I32, _I32, _I64, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 }
@@ -518,6 +521,48 @@ def sw_traceback(ctx: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix, g
                                len(qo) - 1, mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
                                res.ctypes.data, co.ctypes.data, _addr(out_ops), _addr(out_n_ops),
                                _stream(stream)), "sw_traceback")
+
+
+def _dev_tensor(x, dtype, name: str):
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == dtype and x.is_contiguous()):
+        raise TypeError(f"{name}: a contiguous {dtype} CUDA tensor is required")
+    return x
+
+
+def sw_cigar_capacity_device(results, offsets, stream=None) -> None:
+    """results (5, n) int32 and offsets (n + 1,) int64, both on the device;
+    offsets gets each aligned pair's op room, offsets[n] the total.
+    Asynchronous on the stream."""
+    import torch
+    res = _dev_tensor(results, torch.int32, "results")
+    off = _dev_tensor(offsets, torch.int64, "offsets")
+    n = int(res.shape[1]) if res.dim() == 2 else 0
+    if res.dim() != 2 or res.shape[0] != 5 or off.numel() != n + 1:
+        raise ValueError("results must be (5, n) and offsets (n + 1,)")
+    _check(load().sw_cigar_capacity_device(_addr(res), n, _addr(off), _stream(stream)),
+           "sw_cigar_capacity_device")
+
+
+def sw_traceback_device(ctx: int, q_seqs, q_offsets, r_seqs, r_offsets, score_matrix,
+                        gap_open: int, gap_extend: int, results, cigar_offsets, out_ops,
+                        out_n_ops, stream=None) -> None:
+    """Everything on the device but the score matrix: offsets (n + 1,) int64,
+    results (5, n) int32, cigar_offsets (n + 1,) int64.  Waits for the
+    classification kernels, then enqueues the fill and walk on the stream."""
+    import torch
+    qo = _dev_tensor(q_offsets, torch.int64, "q_offsets")
+    ro = _dev_tensor(r_offsets, torch.int64, "r_offsets")
+    res = _dev_tensor(results, torch.int32, "results")
+    co = _dev_tensor(cigar_offsets, torch.int64, "cigar_offsets")
+    n = int(qo.numel()) - 1
+    if ro.numel() != n + 1 or co.numel() != n + 1 or tuple(res.shape) != (5, n):
+        raise ValueError("offsets must be (n + 1,) and results (5, n)")
+    mat = _host_i8(score_matrix)
+    _check(load().sw_traceback_device(ctx, _addr(q_seqs), _addr(qo), _addr(r_seqs), _addr(ro), n,
+                                      mat.ctypes.data, mat.shape[0], gap_open, gap_extend,
+                                      _addr(res), _addr(co), _addr(out_ops), _addr(out_n_ops),
+                                      _stream(stream)), "sw_traceback_device")
 
 
 def cigar_strings(ops, offsets, n_ops) -> list[str]:

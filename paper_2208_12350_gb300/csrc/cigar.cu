@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(128, SWGB_TB_MIN_BLOCKS) tb_fill_kernel(const 
 // The width and rows per lane of a span of N rows: the smallest G R >= N over
 // R in {10, 12, 14, 16} and G a power of two up to 32 (ties: more rows per
 // lane, so fewer lanes and less skew).
-int tb_class_of(int32_t N) {
+__host__ __device__ int tb_class_of(int32_t N) {
     int best = -1, best_rows = INT32_MAX;
     for (int ri = kTbRowOpts - 1; ri >= 0; --ri) {
         int lg = 0;
@@ -631,6 +631,355 @@ int tb_class(int32_t N) {
     };
     static const Table t;
     return t.cls[N];
+}
+
+
+// The fast path's one launch over records already on the device, classes
+// widest first; d_choice holds the choice words the records' offsets name.
+cudaError_t launch_tb_fill(const TbPair *d_fast, int32_t n_fast, uint64_t *d_choice,
+                           const TbClassRange *ranges, int n_ranges, int64_t blocks,
+                           const uint8_t *q, const uint8_t *r, uint32_t *ops, int32_t *n_ops,
+                           const int8_t *mat, int A, int go, int ge, cudaStream_t s) {
+    TbParams tp;
+    std::memset(&tp, 0, sizeof tp);
+    tp.q = q;
+    tp.r = r;
+    tp.choice = d_choice;
+    tp.ops = ops;
+    tp.n_ops = n_ops;
+    tp.A = A;
+    tp.go = go;
+    tp.ge = ge;
+    std::memcpy(tp.mat, mat, (size_t)A * A);
+    tp.pairs = d_fast;
+    tp.n_pairs = n_fast;
+    tp.n_ranges = n_ranges;
+    std::memcpy(tp.ranges, ranges, sizeof(TbClassRange) * (size_t)n_ranges);
+    // each thread's profile: one 16-byte entry per residue code; with the
+    // kernel's static shared memory (the score table) the block can pass the
+    // default 48 KB
+    const size_t prof_bytes = (size_t)A * 128 * 16;
+    cudaError_t e = cudaFuncSetAttribute(tb_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)prof_bytes);
+    if (e != cudaSuccess) return e;
+    tb_fill_kernel<<<(unsigned)blocks, 128, prof_bytes, s>>>(tp);
+    return cudaGetLastError();
+}
+
+// The general path for `pairs` (their q, r, N, M, id and out set): one CTA
+// per pair, in chunks whose choice bytes fit the scratch budget.
+int run_general(sw_ctx *ctx, std::vector<CigarPair> &pairs, const uint8_t *q_seqs,
+                const uint8_t *r_seqs, uint32_t *out_ops, int32_t *out_n_ops,
+                const int8_t *score_matrix, int alphabet_size, int gap_open, int gap_extend,
+                cudaStream_t s, const char *who) {
+    int rc = SW_OK;
+    cudaError_t e = cudaSuccess;
+    if (pairs.empty()) return SW_OK;
+    CigarParams prm;
+    std::memset(&prm, 0, sizeof prm);
+    prm.q = q_seqs;
+    prm.r = r_seqs;
+    prm.ops = out_ops;
+    prm.n_ops = out_n_ops;
+    prm.A = alphabet_size;
+    prm.go = gap_open;
+    prm.ge = gap_extend;
+    std::memcpy(prm.mat, score_matrix, (size_t)alphabet_size * alphabet_size);
+    int64_t biggest = 0;
+    for (const CigarPair &cp : pairs) biggest = std::max(biggest, choice_bytes(cp.N, cp.M));
+    const size_t tb_cap = std::max<size_t>(kScratchBudget, (size_t)biggest);
+    size_t row_cap = 0;
+    for (const CigarPair &cp : pairs) row_cap += 2 * ((size_t)cp.M + 1);
+    // chunks: a chunk's pairs share the choice scratch, so the next chunk runs
+    // after it in stream order; every record is laid out before the upload
+    std::vector<std::pair<size_t, size_t>> chunks;
+    {
+        size_t first = 0;
+        int64_t row_at = 0;
+        while (first < pairs.size()) {
+            size_t last = first;
+            int64_t used = 0;
+            while (last < pairs.size()) {
+                const int64_t b = choice_bytes(pairs[last].N, pairs[last].M);
+                if (last > first && used + b > (int64_t)tb_cap) break;
+                pairs[last].tb = used;
+                pairs[last].row = row_at;
+                row_at += 2 * ((int64_t)pairs[last].M + 1);
+                used += b;
+                ++last;
+            }
+            chunks.emplace_back(first, last);
+            first = last;
+        }
+    }
+    const size_t pair_bytes = (pairs.size() * sizeof(CigarPair) + 255) & ~(size_t)255;
+    const size_t row_bytes = (row_cap * sizeof(int64_t) + 255) & ~(size_t)255;
+    void *ws = nullptr;
+    if ((rc = ctx_alloc_async(ctx, pair_bytes + row_bytes + tb_cap, s, &ws)) != SW_OK) return rc;
+    unsigned char *wb = static_cast<unsigned char *>(ws);
+    CigarPair *d_pairs = reinterpret_cast<CigarPair *>(wb);
+    prm.row = reinterpret_cast<int64_t *>(wb + pair_bytes);
+    prm.tb = wb + pair_bytes + row_bytes;
+    e = cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(CigarPair),
+                        cudaMemcpyHostToDevice, s);
+    for (size_t c = 0; e == cudaSuccess && c < chunks.size(); ++c) {
+        prm.pairs = d_pairs + chunks[c].first;
+        cigar_kernel<<<(unsigned)(chunks[c].second - chunks[c].first), kThreads, 0, s>>>(prm);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(ws, s);
+    if (e != cudaSuccess)
+        return set_error(SW_ECUDA, (std::string(who) + ": " + cudaGetErrorString(e)).c_str());
+    return SW_OK;
+}
+
+
+// ---- the preparation on the device (sw_traceback_device)
+//
+// The same classification as the host's, as three kernels over results and
+// offsets already on the device: a histogram of the fast-path pairs over
+// (class, span-length bucket) slots with the choice words each slot needs,
+// one block's exclusive scan of the slots (record and word positions, and
+// the class ranges), and a scatter that writes each pair's record at its
+// slot's next position, its choice words at the slot's next word offset.
+// Within a slot pairs land in arbitrary order; each pair's ops depend on its
+// own span alone.
+constexpr int kTbMShift = 3;     // span-length buckets of 8 columns
+constexpr int kTbMBuckets = 512;  // per class; spans of 4,088 columns or more share the last
+constexpr int kTbSlots = kTbClasses * kTbMBuckets;
+constexpr int kTbScanThreads = 1024;
+static_assert(kTbSlots % kTbScanThreads == 0, "whole slots per scan thread");
+
+struct TbDevSummary {
+    unsigned long long err;  // ~(pair << 3 | kind) of the first bad pair (atomicMax), 0: none
+    long long words;         // choice words of the fast path
+    int32_t n_fast, n_general, n_ranges, blocks;
+    TbClassRange ranges[kTbClasses];
+};
+
+struct TbDevArgs {
+    const int64_t *qo, *ro, *co;
+    const int32_t *res;
+    int64_t n;
+    int64_t unit;   // per-cell magnitude bound of the fast path's values
+    int bytes_ok;   // every s - go fits a signed byte
+    uint32_t *slot_count;
+    unsigned long long *slot_words;
+    uint32_t *slot_pos;
+    unsigned long long *slot_wpos;
+    TbPair *records;
+    CigarPair *general;
+    TbDevSummary *sum;
+};
+
+// kind: -1 bad (bad = 1 coordinates outside the pair, 2 too little op room,
+// 3 offsets negative or decreasing, 4 a length above SW_MAX_LEN), 0 nothing
+// to trace (score 0), 1 fast path, 2 general path
+struct TbDevClass {
+    int kind, bad, slot, cls;
+    int32_t N, M, qs, rs;
+    int64_t wpp;
+};
+
+__device__ TbDevClass tb_dev_class(const TbDevArgs &a, int64_t p) {
+    TbDevClass c{};
+    const int64_t q0 = a.qo[p], r0 = a.ro[p];
+    const int64_t qn = a.qo[p + 1] - q0, rm = a.ro[p + 1] - r0;
+    if (q0 < 0 || r0 < 0 || qn < 0 || rm < 0 || qn > SW_MAX_LEN || rm > SW_MAX_LEN) {
+        c.kind = -1;
+        c.bad = (qn > SW_MAX_LEN || rm > SW_MAX_LEN) && qn >= 0 && rm >= 0 && q0 >= 0 && r0 >= 0 ? 4 : 3;
+        return c;
+    }
+    const int64_t n = a.n;
+    const int32_t S = a.res[p], qe = a.res[n + p], re = a.res[2 * n + p], qs = a.res[3 * n + p],
+                  rs = a.res[4 * n + p];
+    if (S <= 0) return c;
+    if (qs < 0 || qs > qe || qe >= qn || rs < 0 || rs > re || re >= rm) {
+        c.kind = -1;
+        c.bad = 1;
+        return c;
+    }
+    c.N = qe - qs + 1;
+    c.M = re - rs + 1;
+    c.qs = qs;
+    c.rs = rs;
+    if (a.co[p + 1] - a.co[p] < (int64_t)c.N + c.M) {
+        c.kind = -1;
+        c.bad = 2;
+        return c;
+    }
+    if (a.bytes_ok && c.N <= kTbMaxRows && ((int64_t)kTbMaxRows + c.M + 2) * a.unit <= ((int64_t)1 << 28)) {
+        c.kind = 1;
+        c.cls = tb_class_of(c.N);
+        const int64_t G = (int64_t)1 << (c.cls / kTbRowOpts);
+        c.wpp = G * (c.M + G - 1);
+        // widest class first, longest span first within a class
+        c.slot = (kTbClasses - 1 - c.cls) * kTbMBuckets +
+                 (kTbMBuckets - 1 - min(c.M >> kTbMShift, kTbMBuckets - 1));
+        return c;
+    }
+    c.kind = 2;
+    return c;
+}
+
+__global__ void tb_dev_classify(const __grid_constant__ TbDevArgs a) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const TbDevClass c = tb_dev_class(a, p);
+        if (c.kind < 0) {
+            atomicMax(&a.sum->err, ~(((unsigned long long)p << 3) | (unsigned long long)c.bad));
+        } else if (c.kind == 1) {
+            atomicAdd(a.slot_count + c.slot, 1u);
+            atomicAdd(a.slot_words + c.slot, (unsigned long long)c.wpp);
+        } else if (c.kind == 2) {
+            const int g = atomicAdd(&a.sum->n_general, 1);
+            CigarPair cp{};
+            cp.q = a.qo[p] + c.qs;
+            cp.r = a.ro[p] + c.rs;
+            cp.N = c.N;
+            cp.M = c.M;
+            cp.id = (int32_t)p;
+            cp.out = a.co[p];
+            a.general[g] = cp;
+        }
+    }
+}
+
+// One block: exclusive scans of the slot counts and words, then the class
+// ranges (classes widest first) and the fill's blocks per class.
+__global__ void __launch_bounds__(kTbScanThreads) tb_dev_scan(const __grid_constant__ TbDevArgs a) {
+    constexpr int per = kTbSlots / kTbScanThreads;
+    __shared__ uint32_t wc[32];
+    __shared__ unsigned long long ww[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, k0 = t * per;
+    uint32_t c = 0;
+    unsigned long long w = 0;
+    for (int i = 0; i < per; ++i) {
+        c += a.slot_count[k0 + i];
+        w += a.slot_words[k0 + i];
+    }
+    uint32_t ic = c;
+    unsigned long long iw = w;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t oc = __shfl_up_sync(0xffffffffu, ic, off);
+        const unsigned long long ow = __shfl_up_sync(0xffffffffu, iw, off);
+        if (lane >= off) {
+            ic += oc;
+            iw += ow;
+        }
+    }
+    if (lane == 31) {
+        wc[warp] = ic;
+        ww[warp] = iw;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = wc[lane];
+        unsigned long long y = ww[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t ox = __shfl_up_sync(0xffffffffu, x, off);
+            const unsigned long long oy = __shfl_up_sync(0xffffffffu, y, off);
+            if (lane >= off) {
+                x += ox;
+                y += oy;
+            }
+        }
+        wc[lane] = x;
+        ww[lane] = y;
+    }
+    __syncthreads();
+    uint32_t bc = (warp ? wc[warp - 1] : 0u) + ic - c;
+    unsigned long long bw = (warp ? ww[warp - 1] : 0ull) + iw - w;
+    for (int i = 0; i < per; ++i) {
+        a.slot_pos[k0 + i] = bc;
+        a.slot_wpos[k0 + i] = bw;
+        bc += a.slot_count[k0 + i];
+        bw += a.slot_words[k0 + i];
+    }
+    __syncthreads();  // every thread's slot positions are visible to thread 0
+    if (t == 0) {
+        const uint32_t total = wc[31];
+        int nr = 0;
+        int64_t blocks = 0;
+        for (int k = 0; k < kTbClasses; ++k) {
+            const uint32_t first = a.slot_pos[k * kTbMBuckets];
+            const uint32_t end = k + 1 < kTbClasses ? a.slot_pos[(k + 1) * kTbMBuckets] : total;
+            if (end > first) {
+                const int cls = kTbClasses - 1 - k;
+                const int per_block = 128 >> (cls / kTbRowOpts);
+                a.sum->ranges[nr] = TbClassRange{cls, (int32_t)first, (int32_t)(end - first),
+                                                 (int32_t)blocks};
+                blocks += (end - first + per_block - 1) / per_block;
+                ++nr;
+            }
+        }
+        a.sum->n_fast = (int32_t)total;
+        a.sum->words = (long long)ww[31];
+        a.sum->n_ranges = nr;
+        a.sum->blocks = (int32_t)blocks;
+    }
+}
+
+__global__ void tb_dev_scatter(const __grid_constant__ TbDevArgs a) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const TbDevClass c = tb_dev_class(a, p);
+        if (c.kind != 1) continue;
+        const uint32_t pos = atomicAdd(a.slot_pos + c.slot, 1u);
+        const unsigned long long wpos = atomicAdd(a.slot_wpos + c.slot, (unsigned long long)c.wpp);
+        TbPair tp;
+        tp.q = a.qo[p] + c.qs;
+        tp.r = a.ro[p] + c.rs;
+        tp.ch = (int64_t)wpos;
+        tp.out = a.co[p];
+        tp.N = c.N;
+        tp.M = c.M;
+        tp.id = (int32_t)p;
+        tp.cls = c.cls;
+        a.records[pos] = tp;
+    }
+}
+
+// Room per pair ((qend - qstart + 1) + (rend - rstart + 1) ops for an
+// aligned pair, 0 otherwise) and its exclusive scan, by one block over tiles
+// of its width; offsets[n] ends as the total.
+constexpr int kCapThreads = 1024;
+__global__ void __launch_bounds__(kCapThreads) cigar_capacity_kernel(const int32_t *res, int64_t n,
+                                                                    int64_t *offsets) {
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += kCapThreads) {
+        const int64_t p = base + t;
+        long long room = 0;
+        if (p < n && res[p] > 0)
+            room = (long long)(res[n + p] - res[3 * n + p] + 1) + (res[2 * n + p] - res[4 * n + p] + 1);
+        room = room > 0 ? room : 0;
+        long long inc = room;
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long o = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += o;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            long long x = wsum[lane];
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long o = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += o;
+            }
+            wsum[lane] = x;
+        }
+        __syncthreads();
+        const long long c0 = carry;
+        if (p < n) offsets[p] = c0 + (warp ? wsum[warp - 1] : 0) + inc - room;
+        __syncthreads();
+        if (t == 0) carry = c0 + wsum[31];
+        __syncthreads();
+    }
+    if (t == 0) offsets[n] = carry;
 }
 
 }  // namespace
@@ -887,92 +1236,160 @@ extern "C" int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q
             cudaFreeAsync(ws, s);
             return rc;
         }
-        TbParams tp;
-        std::memset(&tp, 0, sizeof tp);
-        tp.q = q_seqs;
-        tp.r = r_seqs;
-        tp.choice = d_choice;
-        tp.ops = out_ops;
-        tp.n_ops = out_n_ops;
-        tp.A = alphabet_size;
-        tp.go = gap_open;
-        tp.ge = gap_extend;
-        std::memcpy(tp.mat, score_matrix, (size_t)alphabet_size * alphabet_size);
-        // each thread's profile: one 16-byte entry per residue code
-        const size_t prof_bytes = (size_t)alphabet_size * 128 * 16;
-        tp.pairs = d_fast;
-        tp.n_pairs = (int32_t)n_fast;
-        tp.n_ranges = n_ranges;
-        std::memcpy(tp.ranges, ranges, sizeof ranges);
-        // with the kernel's static shared memory (the score table) the block
-        // can pass the default 48 KB
-        e = cudaFuncSetAttribute(tb_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)prof_bytes);
-        if (e == cudaSuccess) {
-            tb_fill_kernel<<<(unsigned)blocks, 128, prof_bytes, s>>>(tp);
-            e = cudaGetLastError();
-        }
+        e = launch_tb_fill(d_fast, (int32_t)n_fast, d_choice, ranges, n_ranges, blocks, q_seqs,
+                           r_seqs, out_ops, out_n_ops, score_matrix, alphabet_size, gap_open,
+                           gap_extend, s);
         cudaFreeAsync(ws, s);  // stream-ordered: after the kernels that use it
         if (e != cudaSuccess)
             return set_error(SW_ECUDA, (std::string("sw_traceback: ") + cudaGetErrorString(e)).c_str());
     }
 
     // ---- general path: one CTA per pair, chunks whose choice bytes fit the budget
-    if (pairs.empty()) return SW_OK;
-    CigarParams prm;
-    std::memset(&prm, 0, sizeof prm);
-    prm.q = q_seqs;
-    prm.r = r_seqs;
-    prm.ops = out_ops;
-    prm.n_ops = out_n_ops;
-    prm.A = alphabet_size;
-    prm.go = gap_open;
-    prm.ge = gap_extend;
-    std::memcpy(prm.mat, score_matrix, (size_t)alphabet_size * alphabet_size);
-    int64_t biggest = 0;
-    for (const CigarPair &cp : pairs) biggest = std::max(biggest, choice_bytes(cp.N, cp.M));
-    const size_t tb_cap = std::max<size_t>(kScratchBudget, (size_t)biggest);
-    size_t row_cap = 0;
-    for (const CigarPair &cp : pairs) row_cap += 2 * ((size_t)cp.M + 1);
-    // chunks: a chunk's pairs share the choice scratch, so the next chunk runs
-    // after it in stream order; every record is laid out before the upload
-    std::vector<std::pair<size_t, size_t>> chunks;
-    {
-        size_t first = 0;
-        int64_t row_at = 0;
-        while (first < pairs.size()) {
-            size_t last = first;
-            int64_t used = 0;
-            while (last < pairs.size()) {
-                const int64_t b = choice_bytes(pairs[last].N, pairs[last].M);
-                if (last > first && used + b > (int64_t)tb_cap) break;
-                pairs[last].tb = used;
-                pairs[last].row = row_at;
-                row_at += 2 * ((int64_t)pairs[last].M + 1);
-                used += b;
-                ++last;
-            }
-            chunks.emplace_back(first, last);
-            first = last;
-        }
+    return run_general(ctx, pairs, q_seqs, r_seqs, out_ops, out_n_ops, score_matrix, alphabet_size,
+                       gap_open, gap_extend, s, "sw_traceback");
+}
+
+
+extern "C" int sw_cigar_capacity_device(const int32_t *results, int32_t n_pairs, int64_t *offsets,
+                                        void *stream) {
+    if (n_pairs < 0 || !offsets || (n_pairs > 0 && !results))
+        return set_error(SW_EINVAL, "sw_cigar_capacity_device: bad argument");
+    cigar_capacity_kernel<<<1, kCapThreads, 0, (cudaStream_t)stream>>>(results, n_pairs, offsets);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_error(SW_ECUDA, (std::string("sw_cigar_capacity_device: ") + cudaGetErrorString(e)).c_str());
+    return SW_OK;
+}
+
+extern "C" int sw_traceback_device(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
+                                   const uint8_t *r_seqs, const int64_t *r_offsets, int32_t n_pairs,
+                                   const int8_t *score_matrix, int32_t alphabet_size,
+                                   int32_t gap_open, int32_t gap_extend, const int32_t *results,
+                                   const int64_t *cigar_offsets, uint32_t *out_ops,
+                                   int32_t *out_n_ops, void *stream) {
+    const char *who = "sw_traceback_device";
+    if (!ctx) return set_error(SW_EINVAL, "sw_traceback_device: ctx is NULL");
+    if (n_pairs < 0 || (n_pairs > 0 && (!q_offsets || !r_offsets || !results || !cigar_offsets ||
+                                        !out_n_ops || !q_seqs || !r_seqs || !out_ops)))
+        return set_error(SW_EINVAL, "sw_traceback_device: bad argument");
+    if (n_pairs == 0) return SW_OK;
+    std::string msg;
+    int rc = check_batch(nullptr, nullptr, 0, score_matrix, alphabet_size, gap_open, gap_extend,
+                         nullptr, nullptr, nullptr, &msg);
+    if (rc != SW_OK) return set_error(rc, ("sw_traceback_device: " + msg).c_str());
+    int smax = 0;
+    bool bytes_ok = true;
+    for (int k = 0; k < alphabet_size * alphabet_size; ++k) {
+        smax = std::max(smax, std::abs((int)score_matrix[k]));
+        const int v = (int)score_matrix[k] - gap_open;
+        bytes_ok = bytes_ok && v >= -128 && v <= 127;
     }
-    const size_t pair_bytes = (pairs.size() * sizeof(CigarPair) + 255) & ~(size_t)255;
-    const size_t row_bytes = (row_cap * sizeof(int64_t) + 255) & ~(size_t)255;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    const int dev = ctx_device(ctx);
+    if (dev != dev_prev && cudaSetDevice(dev) != cudaSuccess)
+        return set_error(SW_ECUDA, "sw_traceback_device: cudaSetDevice failed");
+    struct Restore {
+        int dev, prev;
+        ~Restore() {
+            if (dev != prev && prev >= 0) cudaSetDevice(prev);
+        }
+    } restore{dev, dev_prev};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = n_pairs;
+    cudaError_t e = cudaMemsetAsync(out_n_ops, 0, (size_t)n * sizeof(int32_t), s);
+    if (e != cudaSuccess) return set_error(SW_ECUDA, "sw_traceback_device: memset failed");
+
+    // planning workspace: summary | slot counts | slot words | slot cursors
+    // (records, words) | fast-path records | general-path records
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_count = up(sizeof(TbDevSummary));
+    const size_t o_words = o_count + up((size_t)kTbSlots * 4);
+    const size_t o_pos = o_words + up((size_t)kTbSlots * 8);
+    const size_t o_wpos = o_pos + up((size_t)kTbSlots * 4);
+    const size_t o_rec = o_wpos + up((size_t)kTbSlots * 8);
+    const size_t o_gen = o_rec + up((size_t)n * sizeof(TbPair));
+    const size_t ws_bytes = o_gen + up((size_t)n * sizeof(CigarPair));
     void *ws = nullptr;
-    if ((rc = ctx_alloc_async(ctx, pair_bytes + row_bytes + tb_cap, s, &ws)) != SW_OK) return rc;
+    if ((rc = ctx_alloc_async(ctx, ws_bytes, s, &ws)) != SW_OK) return rc;
     unsigned char *wb = static_cast<unsigned char *>(ws);
-    CigarPair *d_pairs = reinterpret_cast<CigarPair *>(wb);
-    prm.row = reinterpret_cast<int64_t *>(wb + pair_bytes);
-    prm.tb = wb + pair_bytes + row_bytes;
-    e = cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(CigarPair),
-                        cudaMemcpyHostToDevice, s);
-    for (size_t c = 0; e == cudaSuccess && c < chunks.size(); ++c) {
-        prm.pairs = d_pairs + chunks[c].first;
-        cigar_kernel<<<(unsigned)(chunks[c].second - chunks[c].first), kThreads, 0, s>>>(prm);
+    TbDevArgs a;
+    a.qo = q_offsets;
+    a.ro = r_offsets;
+    a.co = cigar_offsets;
+    a.res = results;
+    a.n = n;
+    a.unit = (int64_t)-gap_open - gap_extend + smax;
+    a.bytes_ok = bytes_ok ? 1 : 0;
+    a.sum = reinterpret_cast<TbDevSummary *>(wb);
+    a.slot_count = reinterpret_cast<uint32_t *>(wb + o_count);
+    a.slot_words = reinterpret_cast<unsigned long long *>(wb + o_words);
+    a.slot_pos = reinterpret_cast<uint32_t *>(wb + o_pos);
+    a.slot_wpos = reinterpret_cast<unsigned long long *>(wb + o_wpos);
+    a.records = reinterpret_cast<TbPair *>(wb + o_rec);
+    a.general = reinterpret_cast<CigarPair *>(wb + o_gen);
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    e = cudaMemsetAsync(wb, 0, o_pos, s);  // summary, slot counts and words
+    if (e == cudaSuccess) {
+        tb_dev_classify<<<grid, 256, 0, s>>>(a);
+        tb_dev_scan<<<1, kTbScanThreads, 0, s>>>(a);
+        tb_dev_scatter<<<grid, 256, 0, s>>>(a);
         e = cudaGetLastError();
     }
-    cudaFreeAsync(ws, s);
-    if (e != cudaSuccess)
-        return set_error(SW_ECUDA, (std::string("sw_traceback: ") + cudaGetErrorString(e)).c_str());
-    return SW_OK;
+    TbDevSummary hs;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, a.sum, sizeof hs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ws, s);
+        return set_error(SW_ECUDA, (std::string("sw_traceback_device: ") + cudaGetErrorString(e)).c_str());
+    }
+    if (hs.err != 0) {
+        cudaFreeAsync(ws, s);
+        const unsigned long long code = ~hs.err;
+        const long long p = (long long)(code >> 3);
+        const int kind = (int)(code & 7);
+        char buf[160];
+        if (kind == 3)
+            snprintf(buf, sizeof buf, "%s: offsets of pair %lld negative or decreasing", who, p);
+        else if (kind == 4)
+            snprintf(buf, sizeof buf, "%s: pair %lld has a length above SW_MAX_LEN", who, p);
+        else if (kind == 1)
+            snprintf(buf, sizeof buf, "%s: pair %lld has coordinates outside it", who, p);
+        else
+            snprintf(buf, sizeof buf, "%s: pair %lld needs more ops of room than its cigar offsets give",
+                     who, p);
+        return set_error(SW_ERANGE, buf);
+    }
+    if (hs.n_fast > 0) {
+        void *cw = nullptr;
+        if ((rc = ctx_alloc_async(ctx, (size_t)hs.words * 8, s, &cw)) != SW_OK) {
+            cudaFreeAsync(ws, s);
+            return rc;
+        }
+        e = launch_tb_fill(a.records, hs.n_fast, static_cast<uint64_t *>(cw), hs.ranges,
+                           hs.n_ranges, hs.blocks, q_seqs, r_seqs, out_ops, out_n_ops, score_matrix,
+                           alphabet_size, gap_open, gap_extend, s);
+        cudaFreeAsync(cw, s);  // stream-ordered: after the kernel that uses it
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ws, s);
+            return set_error(SW_ECUDA, (std::string("sw_traceback_device: ") + cudaGetErrorString(e)).c_str());
+        }
+    }
+    std::vector<CigarPair> pairs;
+    if (hs.n_general > 0) {
+        pairs.resize((size_t)hs.n_general);
+        e = cudaMemcpyAsync(pairs.data(), a.general, pairs.size() * sizeof(CigarPair),
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ws, s);
+            return set_error(SW_ECUDA, (std::string("sw_traceback_device: ") + cudaGetErrorString(e)).c_str());
+        }
+        // in pair order, as the host preparation lists them
+        std::sort(pairs.begin(), pairs.end(),
+                  [](const CigarPair &x, const CigarPair &y) { return x.id < y.id; });
+    }
+    cudaFreeAsync(ws, s);  // stream-ordered: after the fill kernel reads the records
+    return run_general(ctx, pairs, q_seqs, r_seqs, out_ops, out_n_ops, score_matrix, alphabet_size,
+                       gap_open, gap_extend, s, who);
 }
