@@ -287,7 +287,7 @@ int sw_plan_preview(const int64_t *q_offsets, const int64_t *r_offsets, int32_t 
  * batch - offsets and score_matrix on the HOST as for sw_plan_create,
  * q_seqs/r_seqs on the DEVICE, `out` a DEVICE scratch array of 5 x n_pairs
  * int32 that receives the results - once per candidate tuning (bulk
- * lane-group width 2, 4 or 8 with long-pair caps 0.25, 0.5, 1 or none, and
+ * lane-group width 2, 4, 8, 16 or 32 with long-pair caps 0.25, 0.5, 1 or none, and
  * the planner's own choice; for a batch that takes the packed form with
  * 32-bit profile words, each of those also with 32 rows per lane and in the
  * scaled int32 form), then the fastest with two resident blocks per SM

@@ -2,7 +2,7 @@
 //
 // The planner (plan.cpp) picks lane-group widths from a cost model.  The
 // autotuner measures instead: it runs the batch under each candidate tuning
-// - bulk lane-group width G in {2, 4, 8} x long-pair cap in {0.25, 0.5, 1,
+// - bulk lane-group width G in {2, 4, 8, 16, 32} x long-pair cap in {0.25, 0.5, 1,
 // none}, plus the planner's own choice, for each kernel form the batch
 // allows (the packed 16-bit form with 16 or with 32 rows per lane, and the
 // scaled int32 form) - keeps the fastest, sets it on the context and
@@ -41,7 +41,7 @@ uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
 
 // Part of every cache key: a tuning measured on another kernel build is not
 // reused.  Changed whenever the batched kernel's code changes.
-constexpr char kKernelRevision[] = "group-kernel-r14 H+go / transposed reverse / linear / score tables / warp-built profiles / packed 16-bit / half-width tails / paired end-key chain / strip-start cost 18 / branch-free staging / group slots / forms";
+constexpr char kKernelRevision[] = "group-kernel-r14 H+go / transposed reverse / linear / score tables / warp-built profiles / packed 16-bit / half-width tails / paired end-key chain / strip-start cost 18 / branch-free staging / group slots / forms / bulk widths to 32";
 
 std::string batch_key(const char *gpu, int sms, const int64_t *qo, const int64_t *ro, int n_pairs,
                       const int8_t *mat, int A, int go, int ge) {
@@ -220,7 +220,9 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
     std::vector<Cand> cands;
     for (const auto &f : forms) {
         cands.push_back({-1, 0.5, f.first, f.second});
-        for (int lg = kMinLog2G; lg <= 3; ++lg)
+        // bulk widths up to 32 lanes: small batches (and the tail of large
+        // ones) finish sooner on wide groups, which cut a pair's serial sweep
+        for (int lg = kMinLog2G; lg <= 5; ++lg)
             for (double fr : {0.25, 0.5, 1.0, 1e9}) cands.push_back({lg, fr, f.first, f.second});
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -228,11 +228,10 @@ __device__ __forceinline__ uint64_t route_cap(const DevicePlanShape &S, const He
 __device__ __forceinline__ int choose_lg(const DevicePlanShape &S, uint64_t cap, int n, int m,
                                          int route) {
     const int rows = S.rows[route], gn = S.bulk_log2g;
+    // the narrowest width from gn up whose cost stays under the cap, else
+    // the widest (32 lanes)
     int lg = gn;
-    if ((uint64_t)pair_cost(n, m, gn, rows, S.strip_ov) > cap) {
-        for (lg = gn + 1; lg < 5; ++lg)
-            if ((uint64_t)pair_cost(n, m, lg, rows, S.strip_ov) <= cap) break;
-    }
+    while (lg < 5 && (uint64_t)pair_cost(n, m, lg, rows, S.strip_ov) > cap) ++lg;
     if (S.half_tails[route] && lg == gn && gn > kMinLog2G) {
         const int h = rows << gn;
         if ((n + h / 2 - 1) / (h / 2) * (h / 2) < (n + h - 1) / h * h) lg = gn - 1;

@@ -220,11 +220,10 @@ std::vector<PlannedClass> build(const std::vector<PlanPair> &pairs, const Costs 
     std::vector<std::vector<int32_t>> by(6);
     std::vector<double> work(6, 0.0);
     for (const auto &p : pairs) {
+        // the narrowest width from gn up whose cost stays under the cap, else
+        // the widest (32 lanes)
         int lg = gn;
-        if (cost(gn, p.id) > cap) {
-            for (lg = gn + 1; lg < 5; ++lg)
-                if (cost(lg, p.id) <= cap) break;
-        }
+        while (lg < 5 && cost(lg, p.id) > cap) ++lg;
         // a bulk pair whose last strip would be at most half used takes
         // half-width groups: same strips' worth of rows or fewer, less padding
         if (half_tails && lg == gn && gn > kMinLog2G) {

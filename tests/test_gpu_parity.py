@@ -98,7 +98,9 @@ def edge_batch(kind, seed, lens_q, lens_r, plant=True):
     return wl.make_batch("edge-protein", qs, rs, s.astype(np.int8), -11, -1)
 
 
-TUNINGS = [(lg, 1e9) for lg in range(6)] + [(0, 0.05), (1, 0.3), (-1, 0.5)]
+# (the last two: pairs above the cap at the widest bulk widths, where no
+# wider class is left)
+TUNINGS = [(lg, 1e9) for lg in range(6)] + [(0, 0.05), (1, 0.3), (-1, 0.5), (4, 0.05), (5, 0.05)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS, ids=[f"G{1 << t[0] if t[0] >= 0 else 'auto'}-cap{t[1]:g}"

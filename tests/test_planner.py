@@ -118,6 +118,27 @@ def test_long_pairs_go_to_wider_groups(lib):
     assert np.all(lg_nocap == 1)
 
 
+@pytest.mark.parametrize("lg_bulk", [0, 1, 2, 3, 4, 5])
+def test_every_fixed_bulk_width(lib, lg_bulk):
+    """Every bulk width sw_ctx_set_tuning accepts, up to 32 lanes, with pairs
+    above the cap: the bulk keeps its width (0 means the narrowest, 2
+    lanes), a pair above the cap takes a class no narrower than the bulk
+    and at most 32 lanes wide (at the widest bulk width it stays there)."""
+    lens_q = [100] * 600 + [3000, 5000, 8000]
+    lens_r = [400] * 600 + [4000, 4000, 4000]
+    b = _batch(lens_q, lens_r, wl.dna_matrix(), -6, -1, seed=8)
+    bulk = max(lg_bulk, 1)
+    for cap in (0.25, 1.0, 1e9):
+        _, lg, rank = preview(lib, b, narrow_log2g=lg_bulk, cap_fraction=cap, sm_count=1)
+        assert np.all((lg[:600] == bulk) | (lg[:600] == bulk - 1))  # half-width tails
+        assert np.all((lg[600:] >= bulk) & (lg[600:] <= 5))
+        for g in np.unique(lg):  # each class's queue positions are a permutation
+            sel = np.flatnonzero(lg == g)
+            assert np.array_equal(np.sort(rank[sel]), np.arange(len(sel)))
+    _, lg, _ = preview(lib, b, narrow_log2g=lg_bulk, cap_fraction=0.25, sm_count=1)
+    assert list(lg[600:]) == [5, 5, 5]
+
+
 def test_pairs_beyond_the_batched_bounds_take_the_plain_kernel(lib):
     """Scores beyond the scaled int32 key and lengths beyond 65,471 residues
     go to the one-block-per-pair kernel; empty pairs stay on the batched path."""
