@@ -183,3 +183,21 @@ def test_default_plans_take_the_measured_best_widths(lib):
     _, lg, _ = preview(lib, b3, sm_count=sms)
     h = np.bincount(lg[lg >= 0], minlength=6)
     assert h[2] + h[3] >= 0.99 * b3.n_pairs and h[1] == 0, h.tolist()
+
+
+def test_small_batches_take_wide_groups(lib):
+    """Batches too small to fill the GPU: the planner's simulation picks the
+    widths a sweep of fixed tunings on a GB300 measured best (identical
+    outputs under every tuning): 1,000 pairs of the 1k DNA workload on
+    32-lane groups (0.099 ms, against 0.109 at the best of 2, 4 and 8
+    lanes), 4,000 on 16-lane groups (0.148 ms, against 0.207), and a
+    20,000-pair slice of the 100k DNA workload on 16-lane bulk groups with
+    8-lane tails (1.203 ms, against 1.282)."""
+    for n, want in ((1000, {5}), (4000, {4})):
+        b = wl.gen_config(0, n_pairs=n)
+        _, lg, _ = preview(lib, b, sm_count=152)
+        assert set(np.unique(lg).tolist()) == want, np.bincount(lg, minlength=6).tolist()
+    b = wl.gen_config(1, n_pairs=20000)
+    _, lg, _ = preview(lib, b, sm_count=152)
+    h = np.bincount(lg, minlength=6)
+    assert h[4] >= 0.5 * b.n_pairs and h[3] + h[4] == b.n_pairs, h.tolist()
