@@ -565,7 +565,9 @@ int sw_traceback(sw_ctx *ctx, const uint8_t *q_seqs, const int64_t *q_offsets,
  * results are checked on the device: SW_ERANGE names the smallest bad pair
  * (offsets negative or decreasing, a length above SW_MAX_LEN, coordinates
  * outside the pair, or room below its need) and then nothing is enqueued
- * beyond the cleared out_n_ops.  Other errors: SW_EINVAL, SW_ENOMEM,
+ * beyond the cleared out_n_ops.  The call cannot be captured in a CUDA
+ * graph (it waits on the stream): on a stream being captured it returns
+ * SW_EINVAL and enqueues nothing.  Other errors: SW_EINVAL, SW_ENOMEM,
  * SW_ECUDA.
  */
 int sw_cigar_capacity_device(const int32_t *results, int32_t n_pairs, int64_t *offsets,

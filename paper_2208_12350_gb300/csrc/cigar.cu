@@ -1296,6 +1296,15 @@ extern "C" int sw_traceback_device(sw_ctx *ctx, const uint8_t *q_seqs, const int
         }
     } restore{dev, dev_prev};
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        // the call reads a summary back and waits for it: not capturable
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess)
+            return set_error(SW_ECUDA, "sw_traceback_device: cudaStreamIsCapturing failed");
+        if (cs != cudaStreamCaptureStatusNone)
+            return set_error(SW_EINVAL, "sw_traceback_device: the stream is being captured (the "
+                                        "call waits for its classification kernels)");
+    }
     const int64_t n = n_pairs;
     cudaError_t e = cudaMemsetAsync(out_n_ops, 0, (size_t)n * sizeof(int32_t), s);
     if (e != cudaSuccess) return set_error(SW_ECUDA, "sw_traceback_device: memset failed");

@@ -199,3 +199,40 @@ def test_errors_found_on_the_device(gpu_lib, ctx):
     call(res5, off)
     got = (ops.cpu().numpy().view(np.uint32), off, n_ops.cpu().numpy())
     assert_same_cigars(b, res, got)
+
+
+def test_refuses_stream_capture(gpu_lib, ctx):
+    """The call waits for its classification kernels, so on a stream being
+    captured it refuses before enqueueing anything."""
+    import torch
+    dev = torch.device("cuda", 0)
+    b = wl.gen_config(0, n_pairs=16)
+    res = oracle.align_workload(b)
+    res5 = np.ascontiguousarray(res.T)
+    off = gpu_lib.sw_cigar_capacity(res5)
+    q = torch.from_numpy(b.q_seqs).to(dev)
+    r = torch.from_numpy(b.r_seqs).to(dev)
+    qo = torch.from_numpy(b.q_offsets).to(dev)
+    ro = torch.from_numpy(b.r_offsets).to(dev)
+    res_d = torch.from_numpy(res5).to(dev)
+    off_d = torch.from_numpy(off).to(dev)
+    ops = torch.zeros(int(off[-1]) + 1, dtype=torch.int32, device=dev)
+    n_ops = torch.zeros(b.n_pairs, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    caught = None
+    with torch.cuda.graph(g, stream=stream):
+        try:
+            gpu_lib.sw_traceback_device(ctx, q, qo, r, ro, b.matrix, b.gap_open, b.gap_extend,
+                                        res_d, off_d, ops, n_ops, stream)
+        except gpu_lib.SwError as e:
+            caught = e
+        n_ops.add_(0)  # something to capture
+    assert caught is not None and caught.code == gpu_lib.SW_EINVAL
+    # outside the capture the same call works
+    gpu_lib.sw_traceback_device(ctx, q, qo, r, ro, b.matrix, b.gap_open, b.gap_extend, res_d,
+                                off_d, ops, n_ops, stream)
+    stream.synchronize()
+    got = (ops.cpu().numpy().view(np.uint32), off, n_ops.cpu().numpy())
+    assert_same_cigars(b, res, got)
