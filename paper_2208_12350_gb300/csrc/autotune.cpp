@@ -14,6 +14,7 @@
 // fewer (2 instead of 3 for 16 rows per lane).  Steps per staging block are
 // fixed per form (8; 4 measured 9 % slower on 100k DNA pairs).
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cinttypes>
@@ -121,7 +122,10 @@ std::vector<Entry> read_cache(const char *path) {
 }
 
 bool write_cache(const char *path, const std::vector<Entry> &entries, const char *gpu, int sms) {
-    const std::string tmp = std::string(path) + ".tmp";
+    // a temporary file of this process's own, renamed over the cache: several
+    // processes tuning at once (one per GPU) never interleave their lines,
+    // and a reader sees one whole file or the other
+    const std::string tmp = std::string(path) + ".tmp." + std::to_string((long long)getpid());
     std::ofstream f(tmp);
     if (!f) return false;
     f << "{\"gpu\": \"" << gpu << "\", \"sms\": " << sms << ", \"entries\": [\n";
@@ -176,9 +180,11 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
         cache = read_cache(cache_path);
         for (const Entry &e : cache)
             if (e.key == key) {
+                // an entry the context does not accept (a damaged or foreign
+                // file) is measured again, as if it were absent
                 int rc = sw_ctx_set_tuning(ctx, e.log2g, e.frac);
                 if (rc == SW_OK) rc = sw_ctx_set_form(ctx, e.arith, e.rows, e.blocks);
-                if (rc != SW_OK) return rc;
+                if (rc != SW_OK) break;
                 if (chosen_log2g) *chosen_log2g = e.log2g;
                 if (chosen_frac) *chosen_frac = e.frac;
                 if (chosen_ms) *chosen_ms = e.ms;
@@ -279,6 +285,9 @@ extern "C" int sw_autotune_ex(sw_ctx *ctx, const int64_t *q_offsets, const int64
     if (chosen_frac) *chosen_frac = best.frac;
     if (chosen_ms) *chosen_ms = best_ms;
     if (cache_path && *cache_path) {
+        cache.erase(std::remove_if(cache.begin(), cache.end(),
+                                   [&](const Entry &e) { return e.key == key; }),
+                    cache.end());
         cache.push_back({key, best.lg, best.frac, best_ms, best.arith, best.rows, best.blocks});
         if (!write_cache(cache_path, cache, gpu, sms))
             return set_error(SW_EINVAL, "sw_autotune: cannot write the cache file");

@@ -158,3 +158,43 @@ def test_autotune_records_form(gpu_lib, tmp_path):
     finally:
         swgb.sw_ctx_destroy(ctx)
         swgb.sw_ctx_destroy(ctx2)
+
+
+def test_damaged_cache_entry_is_measured_again(gpu_lib, tmp_path):
+    """A cache entry the context rejects (here a lane-group width of 2^99,
+    as a torn write could leave) counts as a miss: the batch is measured,
+    the results stay exact, and the file keeps one valid entry for it.
+    Processes tuning at once write through temporary files of their own,
+    so no other file is left beside the cache."""
+    import torch
+    swgb = gpu_lib
+    b = wl.gen_config(1, n_pairs=2000)
+    dev = torch.device("cuda:0")
+    q = torch.from_numpy(b.q_seqs).to(dev)
+    r = torch.from_numpy(b.r_seqs).to(dev)
+    out = torch.empty((5, b.n_pairs), dtype=torch.int32, device=dev)
+    ctx = swgb.sw_ctx_create(0)
+    cache = tmp_path / "tune.json"
+    try:
+        swgb.sw_autotune(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open, b.gap_extend,
+                         q, r, out, cache_path=str(cache))
+        text = cache.read_text()
+        doc = json.loads(text)
+        key = doc["entries"][0]["key"]
+        bad = text.replace(f'"narrow_log2g": {doc["entries"][0]["narrow_log2g"]},',
+                           '"narrow_log2g": 99,')
+        assert bad != text
+        cache.write_text(bad)
+        out.zero_()
+        again = swgb.sw_autotune(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
+                                 b.gap_extend, q, r, out, cache_path=str(cache))
+        assert -1 <= again["narrow_log2g"] <= 5 and again["ms"] > 0
+        torch.cuda.synchronize()
+        idx = np.arange(0, b.n_pairs, 7)
+        assert np.array_equal(out.cpu().numpy().T[idx], oracle.align_workload(b, idx=idx))
+        doc = json.loads(cache.read_text())
+        mine = [e for e in doc["entries"] if e["key"] == key]
+        assert len(mine) == 1 and -1 <= mine[0]["narrow_log2g"] <= 5
+        assert sorted(p.name for p in tmp_path.iterdir()) == ["tune.json"]
+    finally:
+        swgb.sw_ctx_destroy(ctx)
