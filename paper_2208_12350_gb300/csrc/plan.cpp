@@ -22,8 +22,9 @@
 // half used (n mod Gn R in (0, Gn R / 2]) goes to Gn / 2, which computes
 // fewer padded rows for more strips: measured +1.5 % and +2.3 % on 100k and
 // 200k DNA pairs (the autotuner then preferring Gn = 8 over 4), but -23 % on
-// 20k protein pairs in the int32 form and -28 % in the packed form with the
-// byte profile, so the plan asks for it with 32-bit profile words only.
+// 20k protein pairs in the int32 form and -2.3 % in the packed form with the
+// byte profile (2,006 against 2,054 GCUPS, twice each, the autotuner's
+// choice in both), so the plan asks for it with 32-bit profile words only.
 // Warps start on classes in
 // proportion to class work and then walk the classes cyclically.  Among a
 // few (Gn, cap) candidates the planner keeps the one whose simulated
