@@ -140,8 +140,17 @@ int sw_ctx_sm_count(const sw_ctx *ctx, int32_t *out);
 /* *yes = 1 when the context's device reads host memory through the host's
  * page tables over a coherent link (cudaDevAttrPageableMemoryAccessUses-
  * HostPageTables), so sw_plan_execute_host reads page-locked inputs in
- * place; 0 otherwise. */
+ * place; 0 otherwise (or after sw_ctx_set_host_in_place(ctx, 0)). */
 int sw_ctx_host_in_place(const sw_ctx *ctx, int32_t *yes);
+
+/* enable = 0: host-buffer executions and one-shot calls on this context
+ * copy page-locked host inputs to the device (copy engines) instead of
+ * letting the kernels read them over the host link; 1 (the default where
+ * the device supports it): read them in place.  Results are the same; the
+ * faster transport depends on the link's load (reads in place overlap the
+ * transfer with the alignment, copies keep the kernels on device memory).
+ * Errors: SW_EINVAL. */
+int sw_ctx_set_host_in_place(sw_ctx *ctx, int32_t enable);
 
 /* Synchronise the context's device, return its device status word in
  * *status (0 = no inconsistency detected by any kernel; bit 0 = a reverse

@@ -45,6 +45,7 @@ SIGNATURES = {
     "sw_default_ctx": ([_I32, _PP], ctypes.c_int),
     "sw_ctx_set_guards": ([_P, _I32], ctypes.c_int),
     "sw_ctx_host_in_place": ([_P, ctypes.POINTER(_I32)], ctypes.c_int),
+    "sw_ctx_set_host_in_place": ([_P, _I32], ctypes.c_int),
     "sw_ctx_set_tuning": ([_P, _I32, ctypes.c_double], ctypes.c_int),
     "sw_ctx_set_form": ([_P, _I32, _I32, _I32], ctypes.c_int),
     "sw_ctx_get_tuning": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
@@ -250,6 +251,12 @@ def sw_ctx_host_in_place(ctx: int) -> bool:
     v = _I32()
     _check(load().sw_ctx_host_in_place(ctx, ctypes.byref(v)), "sw_ctx_host_in_place")
     return bool(v.value)
+
+
+def sw_ctx_set_host_in_place(ctx: int, enable: bool) -> None:
+    """Read page-locked host inputs in place (True, the default where the
+    device supports it) or copy them to the device first (False)."""
+    _check(load().sw_ctx_set_host_in_place(ctx, 1 if enable else 0), "sw_ctx_set_host_in_place")
 
 
 def sw_plan_execute_host(plan: int, q_seqs, r_seqs, out_host, stream=None) -> None:

@@ -71,7 +71,9 @@ struct sw_ctx {
     int form_rows = 16;         // packed form with 32-bit profile words: 16 or 32 rows per lane
     int form_blocks = 0;        // resident blocks per SM of the batched kernel (0: as many as fit)
     // the device reads host memory through the host's page tables over a
-    // coherent link (NVLink-C2C on Grace): pinned host inputs are read in place
+    // coherent link (NVLink-C2C on Grace): pinned host inputs are read in
+    // place (host_in_place), unless the caller asked for copies
+    bool host_in_place_ok = false;
     bool host_in_place = false;
     std::mutex mu;
     std::vector<std::pair<sw_plan *, cudaEvent_t>> retired;
@@ -213,7 +215,8 @@ int sw_ctx_create(int32_t device, sw_ctx **out) {
         cudaGetLastError();
         ats = 0;
     }
-    ctx->host_in_place = ats != 0;
+    ctx->host_in_place_ok = ats != 0;
+    ctx->host_in_place = ctx->host_in_place_ok;
     if (cudaMalloc(&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -438,6 +441,13 @@ static const uint8_t *host_view(const sw_ctx *ctx, const uint8_t *h) {
 int sw_ctx_host_in_place(const sw_ctx *ctx, int32_t *yes) {
     if (!ctx || !yes) return fail(SW_EINVAL, "sw_ctx_host_in_place: NULL argument");
     *yes = ctx->host_in_place ? 1 : 0;
+    return SW_OK;
+}
+
+int sw_ctx_set_host_in_place(sw_ctx *ctx, int32_t enable) {
+    if (!ctx || (enable != 0 && enable != 1))
+        return fail(SW_EINVAL, "sw_ctx_set_host_in_place: bad argument");
+    ctx->host_in_place = enable != 0 && ctx->host_in_place_ok;
     return SW_OK;
 }
 

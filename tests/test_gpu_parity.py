@@ -373,3 +373,43 @@ def test_host_buffer_execution_pinned_and_pageable(gpu_lib, ctx):
     finally:
         gpu_lib.sw_plan_destroy(plan)
     assert isinstance(gpu_lib.sw_ctx_host_in_place(ctx), bool)
+
+
+def test_host_input_transport_switch(gpu_lib):
+    """sw_ctx_set_host_in_place: page-locked inputs copied to the device
+    (0) or read in place where the device can (1) give the same outputs, for
+    the plan's host-buffer call and the one-shot call; the setting reads
+    back, and never claims in-place reads a device cannot do."""
+    import torch
+    b = wl.gen_config(2, n_pairs=800)
+    expect = oracle.align_workload(b)
+    ctx = gpu_lib.sw_ctx_create(0)
+    try:
+        able = gpu_lib.sw_ctx_host_in_place(ctx)
+        plan = gpu_lib.sw_plan_create(ctx, b.q_offsets, b.r_offsets, b.matrix, b.gap_open,
+                                      b.gap_extend, gpu_lib.SW_MODE_BATCHED, gpu_lib.SW_PLAN_GRAPH)
+        qh = torch.from_numpy(b.q_seqs).pin_memory()
+        rh = torch.from_numpy(b.r_seqs).pin_memory()
+        qoh = torch.from_numpy(b.q_offsets).pin_memory()
+        roh = torch.from_numpy(b.r_offsets).pin_memory()
+        try:
+            for enable in (False, True, False):
+                gpu_lib.sw_ctx_set_host_in_place(ctx, enable)
+                assert gpu_lib.sw_ctx_host_in_place(ctx) == (enable and able)
+                out = torch.full((5, b.n_pairs), -9, dtype=torch.int32).pin_memory()
+                gpu_lib.sw_plan_execute_host(plan, qh, rh, out)
+                assert_same(out.numpy().T, expect, f"host buffers, in place={enable}")
+                if enable and able:
+                    # (the one-shot call takes host buffers only when it reads
+                    # them in place; otherwise its inputs must be on the device)
+                    dout = torch.full((5, b.n_pairs), -9, dtype=torch.int32, device="cuda")
+                    gpu_lib.sw_align_batch_ex(ctx, qh, qoh, rh, roh, b.matrix, b.gap_open,
+                                              b.gap_extend, gpu_lib.SW_MODE_AUTO, dout)
+                    torch.cuda.synchronize()
+                    assert_same(dout.cpu().numpy().T, expect, "one-shot, inputs in place")
+        finally:
+            gpu_lib.sw_plan_destroy(plan)
+        assert gpu_lib.load().sw_ctx_set_host_in_place(ctx, 2) == gpu_lib.SW_EINVAL
+        assert gpu_lib.sw_ctx_host_in_place(ctx) is False
+    finally:
+        gpu_lib.sw_ctx_destroy(ctx)
